@@ -1,0 +1,302 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused FP64 RK4 ray tracer on the GRIN-fibre workload.
+
+Workload (one "step"): 1,048,576 rays in a parabolic GRIN fibre (n0 = 1.5,
+a = 2) with 16 Gaussian blobs, launched from x = -1 within 10 degrees of +x,
+set on shell (gf_rays_onshell) and traced by 10,000 RK4 steps of dt = 5e-4
+(gf_trace_rk4), FP64.  Metric: ray-steps/s (one RK4 step of one ray), counted
+from the per-ray step counters the kernel writes.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gf|reference]
+
+Multi-GPU (torchrun, one rank per GPU): every rank traces its own independent
+batch of the same size (weak scaling, no data-path collective); timing is the
+max over ranks.  `--impl reference` times the plain FP64 CPU oracle on the
+host cores on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2508_15967_gb300 import workloads as W  # noqa: E402
+
+METRIC = "ray-steps/s FP64 at 1M rays (GRIN fibre + 16 blobs, RK4)"
+UNIT = "ray-steps/s"
+SMS = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gf", "reference"], default="gf")
+    ap.add_argument("--rays", type=int, default=1 << 20)
+    ap.add_argument("--nsteps", type=int, default=10000)
+    ap.add_argument("--precision", choices=["f64", "f32"], default="f64")
+    ap.add_argument("--cpu-rays", type=int, default=4096,
+                    help="rays of the oracle sample (x the full step count)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        rows = [l.split(",") for l in open(self.path).read().strip().splitlines() if l.count(",") >= 8]
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if "Active" == r[5 + j].strip()})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------- oracle leg
+
+def oracle_throughput(wl, n_rays: int) -> dict:
+    """Plain FP64 oracle on the first n_rays rays of the workload (host cores)."""
+    import oracle as O
+    m = O.medium(**wl.medium)
+    k0, _ = O.onshell(m, wl.x0[:n_rays], wl.d[:n_rays])
+    r = O.make_rays(wl.x0[:n_rays], k0)
+    t0 = time.perf_counter()
+    O.trace_rk4(m, r, wl.omega, wl.dt, wl.n_steps)
+    el = time.perf_counter() - t0
+    units = int(r.steps.astype(np.int64).sum())
+    return {"value": units / el, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{n_rays} rays x {wl.n_steps} RK4 steps of the same workload "
+                      f"({units} ray-steps, {el:.1f} s)", "seconds": el}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = W.grin(n=max(a.cpu_rays, 1), n_steps=a.nsteps)
+    for _ in range(a.warmup):
+        oracle_throughput(wl, min(256, a.cpu_rays))
+    vals, secs = [], 0.0
+    for _ in range(a.steps):
+        r = oracle_throughput(wl, a.cpu_rays)
+        vals.append(r["value"])
+        secs += r["seconds"]
+    v = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * secs / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"grin_fibre_16_blobs rays={a.cpu_rays} (sample of {a.rays}) "
+                                   f"rk4_steps={a.nsteps} dt=5e-4", "parallelism": "host cores"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- GPU leg
+
+# Algorithmic FP64 cost of one RK4 ray-step on the GRIN + 16 blob medium; the
+# derivation is in the design doc (flops: add/mul 1, fma 2; exp and 1/x counted
+# separately, not as flops).
+FLOPS_PER_EVAL_BASE = 7 + 8 + 8 + 24
+FLOPS_PER_BLOB = 19
+EVALS_PER_STEP = 4
+FLOPS_PER_STEP_EXTRA = 18
+
+
+def flops_per_ray_step(n_blobs: int) -> int:
+    return EVALS_PER_STEP * (FLOPS_PER_EVAL_BASE + FLOPS_PER_BLOB * n_blobs) + FLOPS_PER_STEP_EXTRA
+
+
+def run_gpu(a):
+    import torch
+    import torch.distributed as dist
+    import paper_2508_15967_gb300 as gf
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    dtype = torch.float64 if a.precision == "f64" else torch.float32
+    wl = W.grin(n=a.rays, n_steps=a.nsteps, shard=rank)
+    m = gf.gf_medium_create(**wl.medium)
+    x0 = torch.from_numpy(np.ascontiguousarray(wl.x0.T)).to("cuda", dtype)
+    dirs = torch.from_numpy(np.ascontiguousarray(wl.d.T)).to("cuda", dtype)
+    rays = gf.Rays.empty(wl.n, dtype)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def reset():
+        rays.y[:3].copy_(x0)
+        rays.t.zero_()
+        rays.status.zero_()
+        rays.steps.zero_()
+        rays.d_max.zero_()
+
+    def step(k_ev=None):
+        reset()
+        gf.gf_rays_onshell(m, rays, dirs, wl.omega)
+        if k_ev:
+            k_ev[0].record(stream)
+        gf.gf_trace_rk4(m, rays, wl.omega, wl.dt, wl.n_steps)
+        if k_ev:
+            k_ev[1].record(stream)
+
+    # measured FMA peaks (informational; the roofline peak is derived below)
+    peak64, _ = gf.gf_bench_fma_peak(gf.GF_F64, 1 << 15, 4)
+    peak32, _ = gf.gf_bench_fma_peak(gf.GF_F32, 1 << 18, 8)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    units_per_step = int(rays.steps.to(torch.int64).sum().item())
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    starts, ends, kev = [ev() for _ in range(a.steps)], [ev() for _ in range(a.steps)], []
+    barrier()
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for k in range(a.steps):
+        flush.zero_()                                  # L2 flush between timed steps
+        starts[k].record(stream)
+        kk = (ev(), ev())
+        step(kk)
+        kev.append(kk)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - w0
+    clk = clocks.stop()
+    units = int(rays.steps.to(torch.int64).sum().item())
+    assert units == units_per_step, "step counts changed between steps"
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    kern_ms = [s.elapsed_time(e) for s, e in kev]
+    t_dev = sum(step_ms) / 1e3
+    t_max = torch.tensor([t_dev], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    t_max = t_max.item()
+    value = world * units * a.steps / t_max
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    e2e = None
+    if not a.no_e2e:
+        x0_h = torch.from_numpy(np.ascontiguousarray(wl.x0.T)).to(dtype).pin_memory()
+        d_h = torch.from_numpy(np.ascontiguousarray(wl.d.T)).to(dtype).pin_memory()
+        out = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in
+               dict(y=rays.y, t=rays.t, status=rays.status, steps=rays.steps,
+                    d_res=rays.d_res, d_max=rays.d_max).items()}
+        h2d = x0_h.numel() * x0_h.element_size() + d_h.numel() * d_h.element_size()
+        d2h = sum(v.numel() * v.element_size() for v in out.values())
+        barrier()
+        torch.cuda.synchronize()
+        e0 = time.perf_counter()
+        for _ in range(a.steps):
+            gf.trace_host(m, x0_h, d_h, wl.omega, wl.dt, wl.n_steps, rays, dirs, out)
+        torch.cuda.synchronize()
+        barrier()
+        te = torch.tensor([time.perf_counter() - e0], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * units * a.steps / te.item(), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    n_blobs = wl.medium["blobs"].shape[0]
+    fl_step = flops_per_ray_step(n_blobs)
+    k_sec = statistics.mean(kern_ms) / 1e3
+    achieved = fl_step * units / k_sec / 1e12
+    sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+    # FP64 non-tensor peak from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flops
+    peak = SMS * 2 * 2 * sm_mhz * 1e6 / 1e12 if dtype == torch.float64 else SMS * 128 * 2 * sm_mhz * 1e6 / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": 1e3 * t_max / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if dtype == torch.float64 else "f32",
+        "data": "synthetic",
+        "config": {"workload": f"grin_fibre_16_blobs rays={wl.n} rk4_steps={wl.n_steps} dt={wl.dt}",
+                   "rays_per_gpu": wl.n, "rk4_steps": wl.n_steps, "parallelism": f"ray shards x{world}",
+                   "l2": "256 MiB buffer written between timed steps"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "rk4_kernel<double, GRIN>", "kernel_ms": 1e3 * k_sec,
+                     "flops_per_ray_step": fl_step,
+                     "peak_basis": f"152 SM x 2 DFMA/clk x 2 flop x {sm_mhz:.0f} MHz (sampled)",
+                     "fma_peak_measured_tflops": {"f64": peak64, "f32": peak32}},
+        "clocks": clk, "gpu_launches": 2 * a.steps, "e2e": e2e, "wall_s": wall,
+    }
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cb = oracle_throughput(W.grin(n=a.cpu_rays, n_steps=a.nsteps), a.cpu_rays)
+        cb.pop("seconds")
+        line["cpu_baseline"] = cb
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gpu(a)
+
+
+if __name__ == "__main__":
+    main()

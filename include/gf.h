@@ -1,0 +1,190 @@
+/*
+ * gf.h -- C ABI of the GB300 Hamiltonian ray-tracing library (libgf.so).
+ *
+ * The library advances many independent rays of a wave whose dispersion
+ * relation is D(x, k, w) = 0 (arXiv 2508.15967, Sec. 4).  Along a ray D is
+ * constant (Eq. 1) and the equations actually integrated come from implicit
+ * differentiation (Eqs. 2-3):
+ *
+ *     dx/dt =  dw/dk = -D_k / D_w,        dk/dt = -dw/dx = D_x / D_w.
+ *
+ * Supported media (D and its gradients are hand-derived and fused on device):
+ *   GF_MED_HOMOG      D = |k|^2 - w^2 n_h^2
+ *   GF_MED_LUNEBURG   D = |k|^2 - w^2 n^2(x),  n^2 = 2 - |x|^2 for |x|^2 <= 1, else 1
+ *   GF_MED_GRIN       D = |k|^2 - w^2 n^2(x),  n^2 = n0^2 (1 - a^2 (y^2 + z^2))
+ *   GF_MED_QUADRATIC  D = |k|^2 - w^2 (2 - |x|^2)        (Luneburg law, no kink)
+ *   GF_MED_SPLINE     D = k^T M(x) k - w^2 eps(x), M (symmetric 3x3) and eps from
+ *                     a periodic tricubic B-spline grid on [-1, 1)^3
+ * Every isotropic medium may add Gaussian blobs to n^2:
+ *   n^2 += sum_j A_j exp(-|x - c_j|^2 / (2 w_j^2)).
+ *
+ * Conventions for every entry point:
+ *   - Device pointers are caller-owned CUDA global memory on the current
+ *     device (for example torch tensors); the library never frees them.
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and returns without synchronising, unless stated.
+ *   - The return value is a gf_status; GF_OK on success.  On failure a
+ *     description is available from gf_last_error() (thread-local).  Argument
+ *     errors are detected on the host before anything is enqueued.
+ *   - Per-ray outcomes (exit, cut-off, ...) are ray statuses, not call errors.
+ *   - Nothing traps: device-side failures are reported through statuses.
+ *
+ * Ray state layout (struct gf_rays): structure of arrays, component c of ray
+ * i at y[c * ld + i] with c = 0..5 = (x, y, z, kx, ky, kz).  A sub-range of a
+ * larger ray set is addressed by offsetting every pointer and keeping ld.
+ */
+#ifndef GF_H
+#define GF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GF_OK = 0,
+    GF_ERR_INVALID_ARG = 1,   /* a NULL required pointer, a bad size or value       */
+    GF_ERR_CUDA = 2,          /* a CUDA runtime call failed (text in gf_last_error) */
+    GF_ERR_OOM = 3,           /* device memory allocation failed                    */
+    GF_ERR_UNSUPPORTED = 4,   /* valid request this build does not provide          */
+    GF_ERR_TIMEOUT = 5        /* a bounded device-side wait gave up                 */
+} gf_status;
+
+typedef enum { GF_F32 = 0, GF_F64 = 1 } gf_precision;
+
+typedef enum {
+    GF_MED_HOMOG = 0,
+    GF_MED_LUNEBURG = 1,
+    GF_MED_GRIN = 2,
+    GF_MED_QUADRATIC = 3,
+    GF_MED_SPLINE = 4
+} gf_medium_kind;
+
+/* Ray status codes, stored per ray (int32). */
+enum {
+    GF_RAY_ACTIVE = 0,          /* still propagating; another call continues it        */
+    GF_RAY_EXITED = 1,          /* a step ended outside the termination sphere          */
+    GF_RAY_CUTOFF = 2,          /* reached n^2 <= 0 (eps <= 0), i.e. D_w = 0: cut-off  */
+    GF_RAY_NONFINITE = 3,       /* an update was inf/nan; the state before it is kept  */
+    GF_RAY_MAX_STEPS = 4,       /* adaptive stepping used its step budget              */
+    GF_RAY_STEP_UNDERFLOW = 5,  /* adaptive step fell below 1e-14 max(1, |t|)          */
+    GF_RAY_DONE = 6             /* adaptive stepping reached t_max                     */
+};
+
+#define GF_MAX_BLOBS 64         /* blobs per medium                                   */
+
+/* Host-side description of a medium, read only during gf_medium_create. */
+typedef struct {
+    int32_t kind;               /* gf_medium_kind                                        */
+    int32_t n_blobs;            /* 0..GF_MAX_BLOBS; isotropic media only                  */
+    int32_t grid_n;             /* GF_MED_SPLINE: nodes per axis (>= 4)                   */
+    int32_t reserved;           /* must be 0                                              */
+    double n_h;                 /* GF_MED_HOMOG: refractive index (> 0)                   */
+    double n0, a;               /* GF_MED_GRIN: axis index and gradient constant          */
+    const double *blobs;        /* host, n_blobs rows (A, cx, cy, cz, w), w > 0           */
+    const float *grid;          /* host, grid_n^3 nodes x 8 floats, x fastest, node
+                                   (ix, iy, iz) at (-1 + ix h, ...), h = 2 / grid_n, holding
+                                   (M11, M12, M13, M22, M23, M33, eps, unused); the values
+                                   are B-spline control coefficients (no prefilter)       */
+} gf_medium_desc;
+
+typedef struct gf_medium_s *gf_medium;
+
+/* Ray buffers, all device memory, caller-owned. */
+typedef struct {
+    int64_t n;                  /* number of rays (0 allowed: the call does nothing)     */
+    int64_t ld;                 /* stride between the 6 state rows, >= n                  */
+    void *y;                    /* 6 x ld: double for GF_F64, float for GF_F32            */
+    double *t;                  /* n: time of each ray                                    */
+    int32_t *status;            /* n: GF_RAY_*; only GF_RAY_ACTIVE rays are advanced      */
+    int32_t *steps;             /* n: steps taken, incremented by every accepted step     */
+    double *d_res;              /* n or NULL: |D| at the final state                      */
+    double *d_max;              /* n or NULL: running max of |D| over every state visited */
+} gf_rays;
+
+/* Adaptive step control for gf_trace_dopri5. */
+typedef struct {
+    double rtol, atol;          /* error tolerances (> 0)                                */
+    double h0;                  /* first trial step (> 0)                                */
+    double t_max;               /* stop (GF_RAY_DONE) at this time                       */
+    double radius;              /* stop (GF_RAY_EXITED) outside |x| = radius; <= 0: none */
+    double fac_min, fac_max;    /* step-ratio clamps, 0 < fac_min < 1 < fac_max          */
+    double safety;              /* controller safety factor, (0, 1]                      */
+    int64_t max_steps;          /* accepted-step budget per ray (> 0)                    */
+} gf_step_ctl;
+
+/* Text of the last error on this thread ("" if none).  Never NULL. */
+const char *gf_last_error(void);
+
+/* Library version as an integer, major * 10000 + minor * 100 + patch. */
+int32_t gf_version(void);
+
+/*
+ * gf_medium_create -- copy a medium description to the current device.
+ * Paper: the dispersion relation and its spatial dependence through the
+ * medium (Sec. 4); the spline grid is the counterpart of the paper's
+ * argument-dependent coefficient nodes used for spline interpolation (Sec. 2.1).
+ * desc: host description (read during the call only).  out: receives a handle
+ * owned by the caller until gf_medium_destroy.  Synchronous (blocking copy).
+ * Errors: GF_ERR_INVALID_ARG (unknown kind, n_blobs out of range, non-positive
+ * width or index, missing grid, reserved != 0), GF_ERR_OOM, GF_ERR_CUDA.
+ */
+gf_status gf_medium_create(const gf_medium_desc *desc, gf_medium *out);
+
+/* gf_medium_destroy -- free the device copy of a medium (NULL: no-op).  Blocks
+ * until the device is done with it. */
+gf_status gf_medium_destroy(gf_medium m);
+
+/*
+ * gf_medium_set_amplitudes -- replace the blob amplitudes A_j (the parameters
+ * theta of the adjoint problem) from n_blobs device doubles, stream-ordered.
+ * Errors: GF_ERR_INVALID_ARG (NULL, medium without blobs), GF_ERR_CUDA.
+ */
+gf_status gf_medium_set_amplitudes(gf_medium m, const double *amplitudes, void *stream);
+
+/*
+ * gf_rays_onshell -- set k = s d with s > 0 so that D(x, s d, w) = 0 at every
+ * ray's current position x (rows 0..2 of rays->y).
+ * Paper: initial conditions fix w and x and solve D = 0 for the remaining
+ * wave-vector freedom (Sec. 4, to |D| < 1e-15).  Along a fixed direction both
+ * media are quadratic in s, so s = w sqrt(eps / q) in closed form, with
+ * q = d.d (isotropic) or d^T M d (spline), eps = n^2 or eps.
+ * dir: device, 3 rows of rays->ld elements (same type as y), need not be unit.
+ * Writes rows 3..5 of y; status = GF_RAY_CUTOFF and k = 0 where eps <= 0 or
+ * q <= 0, else GF_RAY_ACTIVE.  Leaves t, steps, d_res, d_max untouched.
+ * Errors: GF_ERR_INVALID_ARG, GF_ERR_CUDA (launch failure).
+ */
+gf_status gf_rays_onshell(gf_medium m, gf_precision prec, const gf_rays *rays, const void *dir,
+                          double omega, void *stream);
+
+/*
+ * gf_trace_rk4 -- advance every active ray by up to n_steps classic RK4 steps
+ * of fixed size dt of the ray equations (Eqs. 2-3), fused into one kernel with
+ * the ray state held in registers (Sec. 4: one kernel with inputs x, k, t, w
+ * and outputs the updated x, k, t and the dispersion residual).
+ * Per step: K1 = f(y), K2 = f(y + dt/2 K1), K3 = f(y + dt/2 K2),
+ * K4 = f(y + dt K3), y <- y + dt/6 (K1 + 2 K2 + 2 K3 + K4), t = t_0 + n dt.
+ * A ray stops early with GF_RAY_CUTOFF (a stage point with eps <= 0; state
+ * kept before that step), GF_RAY_NONFINITE, or GF_RAY_EXITED (a step ending
+ * with |x| > radius, radius > 0).  d_max (if given) becomes max(d_max, |D|)
+ * over the states visited; d_res (if given) = |D| at the final state.
+ * omega > 0; dt > 0; n_steps >= 0.
+ * ckpt (GF_F64 only, may be NULL): device doubles [n_ckpt][6][rays->n] with
+ * n_ckpt = ceil(n_steps / checkpoint_every); slot j receives the state before
+ * step j * checkpoint_every of this call (rays that stopped earlier leave
+ * their later slots unwritten).
+ * prec: GF_F64 computes in double; GF_F32 in float with Kahan-compensated
+ * state updates, t kept in double.
+ * Errors: GF_ERR_INVALID_ARG, GF_ERR_UNSUPPORTED (ckpt with GF_F32),
+ * GF_ERR_CUDA.
+ */
+gf_status gf_trace_rk4(gf_medium m, gf_precision prec, const gf_rays *rays, double omega,
+                       double dt, int64_t n_steps, double radius, int64_t checkpoint_every,
+                       double *ckpt, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GF_H */

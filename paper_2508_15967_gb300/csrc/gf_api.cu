@@ -1,0 +1,304 @@
+// gf_api.cu -- host side of the C ABI declared in include/gf.h: error
+// reporting, argument validation, medium objects and the RK4 / on-shell
+// entry points.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "gf_internal.cuh"
+
+struct gf_medium_s {
+    gf::MediumParams p{};
+    int device = -1;
+    double *d_blobs64 = nullptr;
+    float *d_blobs32 = nullptr;
+    float4 *d_grid = nullptr;
+};
+
+namespace gf {
+
+static thread_local std::string g_err;
+
+void set_error(const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+gf_status cuda_status(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return GF_OK;
+    set_error("%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+    if (e == cudaErrorMemoryAllocation) return GF_ERR_OOM;
+    return GF_ERR_CUDA;
+}
+
+// A pointer the kernels may dereference: device or managed memory, on any
+// device visible to the current context.  Host and unregistered pointers
+// are rejected before any launch.
+gf_status check_device_ptr(const void *p, const char *name)
+{
+    if (p == nullptr) {
+        set_error("%s is NULL", name);
+        return GF_ERR_INVALID_ARG;
+    }
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("%s: cudaPointerGetAttributes failed: %s", name, cudaGetErrorString(e));
+        return GF_ERR_INVALID_ARG;
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) {
+        set_error("%s is not device memory", name);
+        return GF_ERR_INVALID_ARG;
+    }
+    return GF_OK;
+}
+
+gf_status check_rays(const gf_rays *r, bool need_state)
+{
+    if (r == nullptr) {
+        set_error("rays is NULL");
+        return GF_ERR_INVALID_ARG;
+    }
+    if (r->n < 0 || r->ld < r->n || r->n > (int64_t)INT32_MAX * 64) {
+        set_error("rays: need 0 <= n <= ld (n=%lld, ld=%lld)", (long long)r->n, (long long)r->ld);
+        return GF_ERR_INVALID_ARG;
+    }
+    if (r->n == 0) return GF_OK;
+    gf_status s;
+    if ((s = check_device_ptr(r->y, "rays.y")) != GF_OK) return s;
+    if ((s = check_device_ptr(r->status, "rays.status")) != GF_OK) return s;
+    if (need_state) {
+        if ((s = check_device_ptr(r->t, "rays.t")) != GF_OK) return s;
+        if ((s = check_device_ptr(r->steps, "rays.steps")) != GF_OK) return s;
+        if (r->d_res && (s = check_device_ptr(r->d_res, "rays.d_res")) != GF_OK) return s;
+        if (r->d_max && (s = check_device_ptr(r->d_max, "rays.d_max")) != GF_OK) return s;
+    }
+    return GF_OK;
+}
+
+const MediumParams &params_of(gf_medium m) { return m->p; }
+int device_of(gf_medium m) { return m->device; }
+
+static gf_status check_medium(gf_medium m)
+{
+    if (m == nullptr) {
+        set_error("medium is NULL");
+        return GF_ERR_INVALID_ARG;
+    }
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != m->device) {
+        set_error("medium lives on device %d, current device is %d", m->device, dev);
+        return GF_ERR_INVALID_ARG;
+    }
+    return GF_OK;
+}
+
+static void free_medium(gf_medium m)
+{
+    if (m->d_blobs64) cudaFree(m->d_blobs64);
+    if (m->d_blobs32) cudaFree(m->d_blobs32);
+    if (m->d_grid) cudaFree(m->d_grid);
+    delete m;
+}
+
+__global__ void set_amplitudes_kernel(double *b64, float *b32, const double *A, int nb)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < nb) {
+        double a = A[j];
+        b64[kBlobStride * j] = a;
+        b32[kBlobStride * j] = (float)a;
+    }
+}
+
+}  // namespace gf
+
+using namespace gf;
+
+extern "C" {
+
+const char *gf_last_error(void) { return g_err.c_str(); }
+
+int32_t gf_version(void) { return 100; }
+
+gf_status gf_medium_create(const gf_medium_desc *d, gf_medium *out)
+{
+    if (d == nullptr || out == nullptr) {
+        set_error("gf_medium_create: desc and out must be non-NULL");
+        return GF_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (d->kind < GF_MED_HOMOG || d->kind > GF_MED_SPLINE || d->reserved != 0) {
+        set_error("gf_medium_create: unknown kind %d or reserved != 0", d->kind);
+        return GF_ERR_INVALID_ARG;
+    }
+    if (d->n_blobs < 0 || d->n_blobs > GF_MAX_BLOBS || (d->n_blobs > 0 && d->blobs == nullptr)) {
+        set_error("gf_medium_create: n_blobs must be in [0, %d] with a table", GF_MAX_BLOBS);
+        return GF_ERR_INVALID_ARG;
+    }
+    if (d->kind == GF_MED_SPLINE && d->n_blobs != 0) {
+        set_error("gf_medium_create: blobs are only defined for isotropic media");
+        return GF_ERR_INVALID_ARG;
+    }
+    if (d->kind == GF_MED_HOMOG && !(d->n_h > 0 && std::isfinite(d->n_h))) {
+        set_error("gf_medium_create: n_h must be a positive finite number");
+        return GF_ERR_INVALID_ARG;
+    }
+    if (d->kind == GF_MED_GRIN && !(std::isfinite(d->n0) && std::isfinite(d->a) && d->n0 > 0)) {
+        set_error("gf_medium_create: GRIN needs finite n0 > 0 and a");
+        return GF_ERR_INVALID_ARG;
+    }
+    if (d->kind == GF_MED_SPLINE && (d->grid == nullptr || d->grid_n < 4 || d->grid_n > 2048)) {
+        set_error("gf_medium_create: spline needs a grid with 4 <= grid_n <= 2048");
+        return GF_ERR_INVALID_ARG;
+    }
+    std::vector<double> t64(kBlobStride * (size_t)d->n_blobs);
+    std::vector<float> t32(t64.size());
+    for (int j = 0; j < d->n_blobs; ++j) {
+        const double *b = d->blobs + 5 * j;
+        double w = b[4];
+        bool fin = std::isfinite(b[0]) && std::isfinite(b[1]) && std::isfinite(b[2]) && std::isfinite(b[3]);
+        if (!(w > 0) || !std::isfinite(w) || !fin) {
+            set_error("gf_medium_create: blob %d has a non-finite value or width <= 0", j);
+            return GF_ERR_INVALID_ARG;
+        }
+        double row[kBlobStride] = {b[0], b[1], b[2], b[3], -1.0 / (2.0 * w * w)};
+        for (int c = 0; c < kBlobStride; ++c) {
+            t64[kBlobStride * j + c] = row[c];
+            t32[kBlobStride * j + c] = (float)row[c];
+        }
+    }
+    gf_medium m = new gf_medium_s();
+    cudaGetDevice(&m->device);
+    MediumParams &p = m->p;
+    p.kind = d->kind;
+    p.n_blobs = d->n_blobs;
+    p.grid_n = d->grid_n;
+    p.n_h2 = d->n_h * d->n_h;
+    p.n02 = d->n0 * d->n0;
+    p.n02a2 = d->n0 * d->n0 * d->a * d->a;
+    gf_status s = GF_OK;
+    size_t nb = t64.size() ? t64.size() : 1;
+    if ((s = cuda_status(cudaMalloc(&m->d_blobs64, nb * sizeof(double)), "cudaMalloc(blobs)")) != GF_OK ||
+        (s = cuda_status(cudaMalloc(&m->d_blobs32, nb * sizeof(float)), "cudaMalloc(blobs)")) != GF_OK) {
+        free_medium(m);
+        return s;
+    }
+    if (!t64.empty()) {
+        if ((s = cuda_status(cudaMemcpy(m->d_blobs64, t64.data(), t64.size() * sizeof(double),
+                                        cudaMemcpyHostToDevice), "cudaMemcpy(blobs)")) != GF_OK ||
+            (s = cuda_status(cudaMemcpy(m->d_blobs32, t32.data(), t32.size() * sizeof(float),
+                                        cudaMemcpyHostToDevice), "cudaMemcpy(blobs)")) != GF_OK) {
+            free_medium(m);
+            return s;
+        }
+    }
+    p.blobs64 = m->d_blobs64;
+    p.blobs32 = m->d_blobs32;
+    if (d->kind == GF_MED_SPLINE) {
+        size_t nodes = (size_t)d->grid_n * d->grid_n * d->grid_n;
+        for (size_t i = 0; i < nodes * 8; ++i)
+            if (!std::isfinite(d->grid[i])) {
+                set_error("gf_medium_create: grid value %zu is not finite", i);
+                free_medium(m);
+                return GF_ERR_INVALID_ARG;
+            }
+        if ((s = cuda_status(cudaMalloc(&m->d_grid, nodes * 8 * sizeof(float)), "cudaMalloc(grid)")) != GF_OK ||
+            (s = cuda_status(cudaMemcpy(m->d_grid, d->grid, nodes * 8 * sizeof(float),
+                                        cudaMemcpyHostToDevice), "cudaMemcpy(grid)")) != GF_OK) {
+            free_medium(m);
+            return s;
+        }
+        p.grid = m->d_grid;
+    }
+    *out = m;
+    return GF_OK;
+}
+
+gf_status gf_medium_destroy(gf_medium m)
+{
+    if (m == nullptr) return GF_OK;
+    free_medium(m);
+    return GF_OK;
+}
+
+gf_status gf_medium_set_amplitudes(gf_medium m, const double *amplitudes, void *stream)
+{
+    gf_status s;
+    if ((s = check_medium(m)) != GF_OK) return s;
+    if (m->p.n_blobs == 0) {
+        set_error("gf_medium_set_amplitudes: medium has no blobs");
+        return GF_ERR_INVALID_ARG;
+    }
+    if ((s = check_device_ptr(amplitudes, "amplitudes")) != GF_OK) return s;
+    set_amplitudes_kernel<<<1, GF_MAX_BLOBS, 0, (cudaStream_t)stream>>>(m->d_blobs64, m->d_blobs32,
+                                                                        amplitudes, m->p.n_blobs);
+    return cuda_status(cudaGetLastError(), "gf_medium_set_amplitudes launch");
+}
+
+gf_status gf_rays_onshell(gf_medium m, gf_precision prec, const gf_rays *rays, const void *dir,
+                          double omega, void *stream)
+{
+    gf_status s;
+    if ((s = check_medium(m)) != GF_OK) return s;
+    if (prec != GF_F32 && prec != GF_F64) {
+        set_error("gf_rays_onshell: unknown precision %d", (int)prec);
+        return GF_ERR_INVALID_ARG;
+    }
+    if (!(omega > 0) || !std::isfinite(omega)) {
+        set_error("gf_rays_onshell: omega must be positive and finite");
+        return GF_ERR_INVALID_ARG;
+    }
+    if ((s = check_rays(rays, false)) != GF_OK) return s;
+    if (rays->n == 0) return GF_OK;
+    if ((s = check_device_ptr(dir, "dir")) != GF_OK) return s;
+    return cuda_status(launch_onshell(m->p, prec, *rays, dir, omega, (cudaStream_t)stream),
+                       "gf_rays_onshell launch");
+}
+
+gf_status gf_trace_rk4(gf_medium m, gf_precision prec, const gf_rays *rays, double omega, double dt,
+                       int64_t n_steps, double radius, int64_t checkpoint_every, double *ckpt,
+                       void *stream)
+{
+    gf_status s;
+    if ((s = check_medium(m)) != GF_OK) return s;
+    if (prec != GF_F32 && prec != GF_F64) {
+        set_error("gf_trace_rk4: unknown precision %d", (int)prec);
+        return GF_ERR_INVALID_ARG;
+    }
+    if (!(omega > 0) || !std::isfinite(omega) || !(dt > 0) || !std::isfinite(dt) || n_steps < 0 ||
+        !std::isfinite(radius)) {
+        set_error("gf_trace_rk4: need omega > 0, dt > 0, n_steps >= 0, finite radius");
+        return GF_ERR_INVALID_ARG;
+    }
+    if ((s = check_rays(rays, true)) != GF_OK) return s;
+    if (ckpt != nullptr) {
+        if (prec != GF_F64) {
+            set_error("gf_trace_rk4: checkpoints are only produced by the FP64 path");
+            return GF_ERR_UNSUPPORTED;
+        }
+        if (checkpoint_every <= 0) {
+            set_error("gf_trace_rk4: checkpoint_every must be > 0 with a checkpoint buffer");
+            return GF_ERR_INVALID_ARG;
+        }
+        if (rays->n > 0 && (s = check_device_ptr(ckpt, "ckpt")) != GF_OK) return s;
+    }
+    if (rays->n == 0 || n_steps == 0) {
+        if (rays->n == 0) return GF_OK;
+    }
+    return cuda_status(launch_rk4(m->p, prec, *rays, omega, dt, n_steps, radius,
+                                  ckpt ? checkpoint_every : 1, ckpt, (cudaStream_t)stream),
+                       "gf_trace_rk4 launch");
+}
+
+}  // extern "C"

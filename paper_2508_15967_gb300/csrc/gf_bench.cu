@@ -1,0 +1,66 @@
+// gf_bench.cu -- FMA-throughput microbenchmark behind gf_bench_fma_peak.
+#include "gf_internal.cuh"
+#include "../../include/gf_bench.h"
+
+namespace gf {
+
+template <typename R>
+__global__ void __launch_bounds__(256) fma_peak_kernel(R *out, int64_t iters, R a, R b)
+{
+    R x[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[c] = (R)(threadIdx.x + c) * (R)1e-3;
+    for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) x[c] = fma(x[c], a, b);
+    }
+    R s = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s += x[c];
+    if (s == (R)-1) out[blockIdx.x] = s;   // never true; keeps the chains live
+}
+
+template <typename R>
+static gf_status run_peak(int64_t iters, int bps, double *tflops, double *ms)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = sms * bps;
+    R *out = nullptr;
+    gf_status s;
+    if ((s = cuda_status(cudaMalloc(&out, sizeof(R) * blocks), "cudaMalloc")) != GF_OK) return s;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    fma_peak_kernel<R><<<blocks, 256>>>(out, iters / 16 + 1, (R)0.9999999, (R)1e-7);  // warm-up
+    cudaEventRecord(e0);
+    fma_peak_kernel<R><<<blocks, 256>>>(out, iters, (R)0.9999999, (R)1e-7);
+    cudaEventRecord(e1);
+    cudaError_t err = cudaEventSynchronize(e1);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if ((s = cuda_status(err == cudaSuccess ? cudaGetLastError() : err, "fma_peak_kernel")) != GF_OK)
+        return s;
+    *ms = t;
+    *tflops = 2.0 * 8.0 * (double)iters * blocks * 256.0 / (t * 1e-3) / 1e12;
+    return GF_OK;
+}
+
+}  // namespace gf
+
+extern "C" gf_status gf_bench_fma_peak(gf_precision prec, int64_t iters, int32_t blocks_per_sm,
+                                       double *out_tflops, double *out_ms)
+{
+    if (iters <= 0 || blocks_per_sm <= 0 || out_tflops == nullptr || out_ms == nullptr) {
+        gf::set_error("gf_bench_fma_peak: need iters > 0, blocks_per_sm > 0 and outputs");
+        return GF_ERR_INVALID_ARG;
+    }
+    if (prec == GF_F64) return gf::run_peak<double>(iters, blocks_per_sm, out_tflops, out_ms);
+    if (prec == GF_F32) return gf::run_peak<float>(iters, blocks_per_sm, out_tflops, out_ms);
+    gf::set_error("gf_bench_fma_peak: unknown precision");
+    return GF_ERR_INVALID_ARG;
+}

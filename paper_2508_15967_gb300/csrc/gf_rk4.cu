@@ -1,0 +1,227 @@
+// gf_rk4.cu -- fused fixed-step RK4 ray-tracing kernel and the on-shell
+// initialisation kernel.
+//
+// One thread owns one ray for the whole call: the state is loaded once,
+// advanced n_steps times in registers (four fused D / grad D evaluations per
+// step) and stored once -- the load-once / store-once kernel shape of the
+// paper's generated RK4 ray update (Sec. 2.2, Sec. 4).  The blob table is
+// staged in shared memory and read as warp-wide broadcasts.
+#include "gf_internal.cuh"
+
+namespace gf {
+
+constexpr int kRk4Block = 128;
+
+template <typename R>
+__device__ __forceinline__ bool finite6(const R *y)
+{
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) ok = ok && isfinite(y[c]);
+    return ok;
+}
+
+// State update y <- y + inc.  FP64: plain add.  FP32: Kahan-compensated
+// (Kahan 1965) so that 10^4 small increments to |x| ~ 1 do not drift.
+template <typename R>
+struct Accum {
+    __device__ __forceinline__ void add(R *y, const R *inc, R *out) const
+    {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) out[c] = y[c] + inc[c];
+    }
+    __device__ __forceinline__ void commit(R *y, const R *out) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) y[c] = out[c];
+    }
+};
+
+template <>
+struct Accum<float> {
+    float comp[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float pend[6];
+    __device__ __forceinline__ void add(float *y, const float *inc, float *out)
+    {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            float yk = __fsub_rn(inc[c], comp[c]);
+            float s = __fadd_rn(y[c], yk);
+            pend[c] = __fsub_rn(__fsub_rn(s, y[c]), yk);
+            out[c] = s;
+        }
+    }
+    __device__ __forceinline__ void commit(float *y, const float *out)
+    {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            y[c] = out[c];
+            comp[c] = pend[c];
+        }
+    }
+};
+
+template <typename R, int KIND>
+__global__ void __launch_bounds__(kRk4Block) rk4_kernel(const MediumParams m, const RaysView<R> r,
+                                                        const R omega, const R dt, const double dt64,
+                                                        const int64_t n_steps, const R radius2,
+                                                        const int64_t every, double *__restrict__ ckpt)
+{
+    __shared__ R sb[kBlobStride * GF_MAX_BLOBS];
+    if constexpr (KIND != K_SPLINE) stage_blobs<R>(m, sb);
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= r.n) return;
+    int st = r.status[i];
+    if (st != GF_RAY_ACTIVE) return;
+
+    const Rhs<R, KIND> f{m, sb, m.n_blobs, omega};
+    R y[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) y[c] = r.y[c * r.ld + i];
+    R dm = r.d_max ? (R)r.d_max[i] : (R)0;
+    const R h2 = dt * (R)0.5, h6 = dt / (R)6;
+    Accum<R> acc_state;
+    int64_t s = 0;
+    for (; s < n_steps; ++s) {
+        if (ckpt != nullptr && s % every == 0) {
+            double *slot = ckpt + (s / every) * 6 * r.n;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) slot[c * r.n + i] = (double)y[c];
+        }
+        R K[6], acc[6], Y[6], D;
+        bool ok = f(y, K, D);
+        dm = fmax(dm, fabs(D));
+        if (!ok) { st = GF_RAY_CUTOFF; break; }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) { acc[c] = K[c]; Y[c] = y[c] + h2 * K[c]; }
+        if (!f(Y, K, D)) { st = GF_RAY_CUTOFF; break; }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) { acc[c] += (R)2 * K[c]; Y[c] = y[c] + h2 * K[c]; }
+        if (!f(Y, K, D)) { st = GF_RAY_CUTOFF; break; }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) { acc[c] += (R)2 * K[c]; Y[c] = y[c] + dt * K[c]; }
+        if (!f(Y, K, D)) { st = GF_RAY_CUTOFF; break; }
+        R inc[6], yn[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) inc[c] = h6 * (acc[c] + K[c]);
+        acc_state.add(y, inc, yn);
+        if (!finite6(yn)) { st = GF_RAY_NONFINITE; break; }
+        acc_state.commit(y, yn);
+        if (radius2 > (R)0 && y[0] * y[0] + y[1] * y[1] + y[2] * y[2] > radius2) {
+            st = GF_RAY_EXITED;
+            ++s;
+            break;
+        }
+    }
+    // s = number of steps applied in this call
+    {
+        R K[6], D;
+        f(y, K, D);
+        dm = fmax(dm, fabs(D));
+        if (r.d_res) r.d_res[i] = (double)fabs(D);
+        if (r.d_max) r.d_max[i] = (double)dm;
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) r.y[c * r.ld + i] = y[c];
+    if (s > 0) r.t[i] = __dadd_rn(r.t[i], __dmul_rn((double)s, dt64));
+    r.steps[i] += (int32_t)s;
+    r.status[i] = st;
+}
+
+// k = s d with D(x, s d, w) = 0, s = w sqrt(eps / q).
+template <typename R, int KIND>
+__global__ void __launch_bounds__(kRk4Block) onshell_kernel(const MediumParams m, const RaysView<R> r,
+                                                            const R *__restrict__ dir, const R omega)
+{
+    __shared__ R sb[kBlobStride * GF_MAX_BLOBS];
+    if constexpr (KIND != K_SPLINE) stage_blobs<R>(m, sb);
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= r.n) return;
+    R x[3] = {r.y[i], r.y[r.ld + i], r.y[2 * r.ld + i]};
+    R d[3] = {dir[i], dir[r.ld + i], dir[2 * r.ld + i]};
+    R eps, q;
+    if constexpr (KIND == K_SPLINE) {
+        R val[7], grad[7][3];
+        spline_fields<R>(m, x, val, grad);
+        eps = val[6];
+        R Md0 = val[0] * d[0] + val[1] * d[1] + val[2] * d[2];
+        R Md1 = val[1] * d[0] + val[3] * d[1] + val[4] * d[2];
+        R Md2 = val[2] * d[0] + val[4] * d[1] + val[5] * d[2];
+        q = d[0] * Md0 + d[1] * Md1 + d[2] * Md2;
+    } else {
+        R g[3];
+        iso_index<R, KIND>(m, sb, m.n_blobs, x, eps, g);
+        q = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    }
+    if (!(eps > (R)0) || !(q > (R)0)) {
+        r.status[i] = GF_RAY_CUTOFF;
+        for (int c = 0; c < 3; ++c) r.y[(3 + c) * r.ld + i] = (R)0;
+        return;
+    }
+    R s = omega * sqrt(eps / q);
+    r.status[i] = GF_RAY_ACTIVE;
+    for (int c = 0; c < 3; ++c) r.y[(3 + c) * r.ld + i] = s * d[c];
+}
+
+template <typename R>
+static RaysView<R> view(const gf_rays &r)
+{
+    return RaysView<R>{r.n, r.ld, (R *)r.y, r.t, r.status, r.steps, r.d_res, r.d_max};
+}
+
+template <typename R, int KIND>
+static cudaError_t rk4_launch(const MediumParams &m, const gf_rays &r, double omega, double dt,
+                              int64_t n_steps, double radius, int64_t every, double *ckpt,
+                              cudaStream_t s)
+{
+    const int64_t blocks = (r.n + kRk4Block - 1) / kRk4Block;
+    const R r2 = radius > 0 ? (R)(radius * radius) : (R)0;
+    rk4_kernel<R, KIND><<<(unsigned)blocks, kRk4Block, 0, s>>>(m, view<R>(r), (R)omega, (R)dt, dt,
+                                                               n_steps, r2, every, ckpt);
+    return cudaGetLastError();
+}
+
+template <typename R, int KIND>
+static cudaError_t onshell_launch(const MediumParams &m, const gf_rays &r, const void *dir, double omega,
+                                  cudaStream_t s)
+{
+    const int64_t blocks = (r.n + kRk4Block - 1) / kRk4Block;
+    onshell_kernel<R, KIND><<<(unsigned)blocks, kRk4Block, 0, s>>>(m, view<R>(r), (const R *)dir, (R)omega);
+    return cudaGetLastError();
+}
+
+#define GF_KIND_SWITCH(KIND_VAR, FN, R, ...)                                      \
+    switch (KIND_VAR) {                                                            \
+    case K_HOMOG: return FN<R, K_HOMOG>(__VA_ARGS__);                             \
+    case K_LUNEBURG: return FN<R, K_LUNEBURG>(__VA_ARGS__);                       \
+    case K_GRIN: return FN<R, K_GRIN>(__VA_ARGS__);                               \
+    case K_QUADRATIC: return FN<R, K_QUADRATIC>(__VA_ARGS__);                     \
+    case K_SPLINE: return FN<R, K_SPLINE>(__VA_ARGS__);                           \
+    default: return cudaErrorInvalidValue;                                         \
+    }
+
+cudaError_t launch_rk4(const MediumParams &m, gf_precision prec, const gf_rays &r, double omega,
+                       double dt, int64_t n_steps, double radius, int64_t every, double *ckpt,
+                       cudaStream_t s)
+{
+    if (r.n == 0) return cudaSuccess;
+    if (prec == GF_F64) {
+        GF_KIND_SWITCH(m.kind, rk4_launch, double, m, r, omega, dt, n_steps, radius, every, ckpt, s)
+    } else {
+        GF_KIND_SWITCH(m.kind, rk4_launch, float, m, r, omega, dt, n_steps, radius, every, ckpt, s)
+    }
+}
+
+cudaError_t launch_onshell(const MediumParams &m, gf_precision prec, const gf_rays &r, const void *dir,
+                           double omega, cudaStream_t s)
+{
+    if (r.n == 0) return cudaSuccess;
+    if (prec == GF_F64) {
+        GF_KIND_SWITCH(m.kind, onshell_launch, double, m, r, dir, omega, s)
+    } else {
+        GF_KIND_SWITCH(m.kind, onshell_launch, float, m, r, dir, omega, s)
+    }
+}
+
+}  // namespace gf

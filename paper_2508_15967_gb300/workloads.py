@@ -94,13 +94,11 @@ def fourier_field(rng: np.random.Generator, axis: np.ndarray, n_modes: int = 32,
     amp = rng.standard_normal(n_modes) / math.sqrt(n_modes)
     ph = rng.uniform(0.0, 2.0 * math.pi, n_modes)
     g = axis.size
-    out = np.zeros((g, g, g))
-    X = axis[None, None, :]
-    Y = axis[None, :, None]
-    Z = axis[:, None, None]
-    for m in range(n_modes):
-        out += amp[m] * np.cos(math.pi * (kap[m, 0] * X + kap[m, 1] * Y + kap[m, 2] * Z) + ph[m])
-    return out
+    # separable evaluation: cos(pi kappa.x + phi) = Re(e^{i phi} e^{i pi kx x} e^{i pi ky y} e^{i pi kz z})
+    E = [np.exp(1j * math.pi * kap[:, c, None] * axis[None, :]) for c in range(3)]   # (m, g) each
+    T = (amp * np.exp(1j * ph))[:, None, None] * E[2][:, :, None] * E[1][:, None, :]  # (m, z, y)
+    out = (T.reshape(n_modes, g * g).T @ E[0]).real                                   # (z*y, x)
+    return out.reshape(g, g, g)
 
 
 def aniso_grid(rng: np.random.Generator, g: int = 128, n_modes: int = 32):
@@ -162,16 +160,18 @@ def luneburg(n: int = 1024, n_steps: int = 2000, dt: float = 1e-3) -> Workload:
     return Workload("luneburg", dict(kind="luneburg"), x0, d, 1.0, dt, n_steps)
 
 
-def grin(n: int = 1 << 20, n_steps: int = 10000, dt: float = 5e-4, n_blobs: int = 16) -> Workload:
+def grin(n: int = 1 << 20, n_steps: int = 10000, dt: float = 5e-4, n_blobs: int = 16,
+         shard: int = 0) -> Workload:
     """Parabolic GRIN fibre n0 = 1.5, a = 2, plus Gaussian blobs.
 
     Launch points (-1, y0, z0) with (y0, z0) uniform in a disk of radius 0.05;
     directions uniform in solid angle within 10 degrees of +x.  The blob table
-    is drawn first so that it does not depend on n.
+    is drawn first so that it does not depend on n.  ``shard`` > 0 draws an
+    independent batch of rays in the same medium (one per GPU).
     """
     rng = rng_for(GRIN)
     blobs = blob_table(rng, n_blobs, 0.01)
-    rr = rng_for(GRIN, 7)
+    rr = rng_for(GRIN, 7 + 1000 * shard)
     x0, _ = plane_disk_rays(rr, n, 0.05)
     d = cone_directions(rr, n, 10.0)
     med = dict(kind="grin", n0=1.5, a=2.0, blobs=blobs)

@@ -1,0 +1,239 @@
+"""GPU parity of the fused RK4 kernels against the FP64 oracle, through the C ABI.
+
+Tolerances: FP64 endpoints <= 1e-9 relative (per-ray norm of rel_err), FP32
+<= 1e-4 relative against the oracle fed the same FP32-rounded inputs; ray
+statuses and step counts bit-exact; t bit-exact (both compute t0 + n dt).
+Sizes span several 128-ray blocks and a ragged tail.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_2508_15967_gb300 as gf
+from paper_2508_15967_gb300 import workloads as W
+from tests import _closed_forms as CF
+from tests._parity import (assert_parity, conditioning_mask, gpu_rk4, oracle_rk4, rel_err)
+
+pytestmark = pytest.mark.gpu
+
+
+def _onshell(spec, x0, d):
+    k0, st = O.onshell(O.medium(**spec), x0, d)
+    assert (st == 0).all()
+    return k0
+
+
+def _f32(a):
+    return np.asarray(a, np.float32).astype(np.float64)
+
+
+def test_luneburg_workload_full_size():
+    """The Luneburg lens workload exactly as specified: 1024 rays, dt 1e-3, 2000 steps."""
+    wl = W.luneburg()
+    k0 = _onshell(wl.medium, wl.x0, wl.d)
+    g = gpu_rk4(wl.medium, wl.x0, k0, 1.0, wl.dt, wl.n_steps)
+    o, _ = oracle_rk4(wl.medium, wl.x0, k0, 1.0, wl.dt, wl.n_steps)
+    assert_parity(g, o, 1e-9)
+
+
+def test_grin_f64_parity_ragged():
+    """GRIN + 16 blobs, 1000 rays (7 full blocks + a tail of 104), 10,000 steps."""
+    wl = W.grin(n=1000)
+    k0 = _onshell(wl.medium, wl.x0, wl.d)
+    g = gpu_rk4(wl.medium, wl.x0, k0, 1.0, wl.dt, wl.n_steps)
+    o, _ = oracle_rk4(wl.medium, wl.x0, k0, 1.0, wl.dt, wl.n_steps)
+    assert_parity(g, o, 1e-9)
+    assert g.dmax.max() <= 1e-8
+
+
+def test_grin_f32_parity():
+    """FP32 path (Kahan-compensated state) against the FP64 oracle on the same
+    FP32-rounded launch states, 10,000 steps."""
+    wl = W.grin(n=700)
+    k0 = _onshell(wl.medium, wl.x0, wl.d)
+    x0f, k0f = _f32(wl.x0), _f32(k0)
+    g = gpu_rk4(wl.medium, x0f, k0f, 1.0, wl.dt, wl.n_steps, dtype=torch.float32)
+    o, _ = oracle_rk4(wl.medium, x0f, k0f, 1.0, wl.dt, wl.n_steps)
+    assert_parity(g, o, 1e-4, diag_atol=1e-5)
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-9), (torch.float32, 1e-4)])
+def test_spline_parity(dtype, tol):
+    """Anisotropic 128^3 tricubic medium, 257 rays (2 blocks + 1), 4000 steps."""
+    wl = W.aniso(n=257)
+    k0 = _onshell(wl.medium, wl.x0, wl.d)
+    x0, k0 = (wl.x0, k0) if dtype == torch.float64 else (_f32(wl.x0), _f32(k0))
+    g = gpu_rk4(wl.medium, x0, k0, 1.0, wl.dt, wl.n_steps, dtype=dtype)
+    o, _ = oracle_rk4(wl.medium, x0, k0, 1.0, wl.dt, wl.n_steps)
+    mask = conditioning_mask(wl.medium, x0, k0, 1.0, wl.dt, wl.n_steps, o.y) \
+        if dtype == torch.float64 else None
+    assert_parity(g, o, tol, cond_mask=mask, diag_atol=1e-12 if dtype == torch.float64 else 1e-5)
+
+
+def test_homogeneous_exact_and_quadratic_closed_form():
+    """Straight rays to 1e-13; quadratic-law ellipses vs the closed form (O(dt^4))."""
+    spec = dict(kind="homog", n_h=1.3)
+    rng = np.random.default_rng(3)
+    x0 = rng.uniform(-1, 1, (300, 3))
+    d = W.sphere_directions(rng, 300)
+    k0 = _onshell(spec, x0, d)
+    g = gpu_rk4(spec, x0, k0, 1.0, 1e-2, 400)
+    x_ex, _ = CF.straight(x0, k0, 1.3, 4.0)
+    np.testing.assert_allclose(g.y[:, :3], x_ex, atol=1e-13)
+    assert np.array_equal(g.y[:, 3:], k0)
+    spec = dict(kind="quadratic")
+    p = W.sphere_directions(rng, 200) * 0.8
+    k0 = _onshell(spec, p, W.sphere_directions(rng, 200))
+    g = gpu_rk4(spec, p, k0, 1.0, 2e-3, 1000)
+    for i in range(0, 200, 17):
+        x_ex, k_ex = CF.quadratic(p[i], k0[i], 2.0)
+        assert np.abs(g.y[i, :3] - x_ex).max() < 1e-10
+    o, _ = oracle_rk4(spec, p, k0, 1.0, 2e-3, 1000)
+    assert_parity(g, o, 1e-12)
+
+
+def test_status_edge_cases():
+    """Cut-off, exit, non-finite, inactive rays, zero steps and zero rays."""
+    grin = dict(kind="grin", n0=1.5, a=2.0)
+    x0 = np.array([[0.0, 0.45, 0.0], [0.0, 0.0, 0.0]])
+    k0 = _onshell(grin, x0, np.array([[0.2, 1.0, 0.0], [1.0, 0.0, 0.0]]))
+    g = gpu_rk4(grin, x0, k0, 1.0, 1e-2, 1000)
+    o, _ = oracle_rk4(grin, x0, k0, 1.0, 1e-2, 1000)
+    assert g.status.tolist() == [gf.GF_RAY_CUTOFF, gf.GF_RAY_ACTIVE]
+    assert_parity(g, o, 1e-9)
+    homog = dict(kind="homog", n_h=1.0)
+    x0 = np.zeros((4, 3))
+    k0 = np.array([[1.0, 0, 0], [0, 1.0, 0], [1.5e308, 0, 0], [0, 0, 1.0]])
+    status = np.array([0, 0, 0, gf.GF_RAY_EXITED], np.int32)
+    g = gpu_rk4(homog, x0, k0, 1.0, 0.01, 1000, radius=0.505, status=status)
+    o, _ = oracle_rk4(homog, x0, k0, 1.0, 0.01, 1000, radius=0.505, status=status)
+    assert g.status.tolist() == [gf.GF_RAY_EXITED, gf.GF_RAY_EXITED, gf.GF_RAY_NONFINITE, gf.GF_RAY_EXITED]
+    assert g.steps.tolist() == [51, 51, 0, 0]
+    assert np.array_equal(g.y[3], np.concatenate([x0[3], k0[3]]))        # inactive: untouched
+    assert_parity(g, o, 1e-12)
+    g = gpu_rk4(homog, x0[:2], k0[:2], 1.0, 0.01, 0)                       # zero steps
+    assert (g.steps == 0).all() and (g.t == 0).all() and (g.dres >= 0).all()
+    m = gf.gf_medium_create("homog", n_h=1.0)
+    empty = gf.Rays.empty(0)
+    gf.gf_trace_rk4(m, empty, 1.0, 0.01, 10)                               # zero rays: no-op
+
+
+def test_resume_and_subranges_are_bitwise_identical():
+    """A trace split over two calls, or over disjoint sub-ranges addressed by
+    offset pointers with the full stride (how a caller shards rays), equals one
+    call bit for bit."""
+    wl = W.grin(n=777, n_steps=600)
+    k0 = _onshell(wl.medium, wl.x0, wl.d)
+    m = gf.gf_medium_create(**wl.medium)
+    whole = gf.Rays.from_numpy(wl.x0, k0)
+    gf.gf_trace_rk4(m, whole, 1.0, wl.dt, 600)
+    split = gf.Rays.from_numpy(wl.x0, k0)
+    gf.gf_trace_rk4(m, split, 1.0, wl.dt, 250)
+    gf.gf_trace_rk4(m, split, 1.0, wl.dt, 350)
+    parts = gf.Rays.from_numpy(wl.x0, k0)
+    ld = parts.y.stride(0)
+    for lo, hi in [(0, 300), (300, 301), (301, 777)]:
+        sub = gf.GfRays(hi - lo, ld, parts.y.data_ptr() + 8 * lo, parts.t.data_ptr() + 8 * lo,
+                        parts.status.data_ptr() + 4 * lo, parts.steps.data_ptr() + 4 * lo,
+                        parts.d_res.data_ptr() + 8 * lo, parts.d_max.data_ptr() + 8 * lo)
+        st = gf.lib().gf_trace_rk4(m.handle, gf.GF_F64, C.byref(sub), 1.0, wl.dt, 600, 0.0, 0, None,
+                                   torch.cuda.current_stream().cuda_stream)
+        assert st == gf.GF_OK
+    torch.cuda.synchronize()
+    assert torch.equal(whole.y, split.y) and torch.equal(whole.y, parts.y)
+    assert torch.equal(whole.steps, split.steps) and torch.equal(whole.d_max, parts.d_max)
+
+
+def test_checkpoints_match_oracle():
+    wl = W.grin(n=300, n_steps=200)
+    k0 = _onshell(wl.medium, wl.x0, wl.d)
+    g = gpu_rk4(wl.medium, wl.x0, k0, 1.0, wl.dt, 200, ckpt_every=64)
+    o, ck = oracle_rk4(wl.medium, wl.x0, k0, 1.0, wl.dt, 200, every=64)
+    assert g.ckpt.shape == (4, 6, 300)
+    for j in range(4):
+        e = rel_err(g.ckpt[j].T, ck[:, j])
+        assert e.max() <= 1e-12
+    assert np.array_equal(g.ckpt[0].T, np.concatenate([wl.x0, k0], 1))
+
+
+@pytest.mark.parametrize("name", ["luneburg", "grin", "aniso", "homog"])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_onshell_matches_oracle(name, dtype):
+    if name == "luneburg":
+        wl = W.adjoint(n=333)
+        spec, x0 = wl.medium, wl.x0 + np.array([0.3, 0, 0])
+    elif name == "grin":
+        wl = W.grin(n=333)
+        spec, x0 = wl.medium, wl.x0
+    elif name == "aniso":
+        wl = W.aniso(n=333, g=32)
+        spec, x0 = wl.medium, wl.x0
+    else:
+        spec, x0 = dict(kind="homog", n_h=1.7), np.random.default_rng(0).uniform(-1, 1, (333, 3))
+    d = W.sphere_directions(np.random.default_rng(1), 333)
+    if dtype == torch.float32:
+        x0, d = _f32(x0), _f32(d)
+    k_o, st_o = O.onshell(O.medium(**spec), x0, d)
+    m = gf.gf_medium_create(**spec)
+    rays = gf.Rays.from_numpy(x0, None, dtype)
+    dirs = torch.zeros_like(rays.y[:3])
+    dirs.copy_(torch.from_numpy(d.T.copy()).to(dtype))
+    gf.gf_rays_onshell(m, rays, dirs, 1.0)
+    torch.cuda.synchronize()
+    k_g = rays.state()[:, 3:]
+    tol = 1e-15 if dtype == torch.float64 else 2e-6
+    np.testing.assert_allclose(k_g, k_o, rtol=tol, atol=tol)
+    assert np.array_equal(rays.status.cpu().numpy(), st_o)
+
+
+def test_set_amplitudes_changes_the_medium():
+    wl = W.adjoint(n=256, n_steps=300)
+    k0 = _onshell(wl.medium, wl.x0, wl.d)
+    theta = wl.extra["theta_star"]
+    blobs2 = wl.medium["blobs"].copy()
+    blobs2[:, 0] = theta
+    m = gf.gf_medium_create(**wl.medium)
+    gf.gf_medium_set_amplitudes(m, torch.tensor(theta, device="cuda"))
+    rays = gf.Rays.from_numpy(wl.x0, k0)
+    gf.gf_trace_rk4(m, rays, 1.0, wl.dt, 300)
+    spec2 = dict(wl.medium, blobs=blobs2)
+    o, _ = oracle_rk4(spec2, wl.x0, k0, 1.0, wl.dt, 300)
+    from tests._parity import GpuResult
+    assert_parity(GpuResult(rays), o, 1e-9)
+
+
+def test_host_pointer_is_rejected_before_launch():
+    m = gf.gf_medium_create("homog", n_h=1.0)
+    host = np.zeros((6, 4))
+    t = np.zeros(4)
+    st = np.zeros(4, np.int32)
+    r = gf.GfRays(4, 4, host.ctypes.data, t.ctypes.data, st.ctypes.data, st.ctypes.data, None, None)
+    s = gf.lib().gf_trace_rk4(m.handle, gf.GF_F64, C.byref(r), 1.0, 0.01, 10, 0.0, 0, None, None)
+    assert s == gf.GF_ERR_INVALID_ARG
+    assert b"device memory" in gf.lib().gf_last_error()
+
+
+def test_grin_full_size_sampled_parity():
+    """The full GRIN workload (1,048,576 rays, 10,000 steps) in one launch, as
+    the benchmark runs it, with 192 seeded sampled rays checked against the
+    oracle, and |D| drift <= 1e-8 on every ray."""
+    wl = W.grin()
+    m = gf.gf_medium_create(**wl.medium)
+    rays = gf.Rays.from_numpy(wl.x0, None)
+    dirs = torch.from_numpy(wl.d.T.copy()).cuda()
+    gf.gf_rays_onshell(m, rays, dirs, 1.0)
+    gf.gf_trace_rk4(m, rays, 1.0, wl.dt, wl.n_steps)
+    torch.cuda.synchronize()
+    idx = np.sort(np.random.default_rng(99).choice(wl.n, 192, replace=False))
+    k0, _ = O.onshell(O.medium(**wl.medium), wl.x0[idx], wl.d[idx])
+    o, _ = oracle_rk4(wl.medium, wl.x0[idx], k0, 1.0, wl.dt, wl.n_steps)
+    g = rays.state()[idx]
+    assert rel_err(g, o.y).max() <= 1e-9
+    assert (rays.status == 0).all()
+    assert rays.d_max.max().item() <= 1e-8
