@@ -36,6 +36,7 @@
 #ifndef GF_H
 #define GF_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -182,6 +183,115 @@ gf_status gf_rays_onshell(gf_medium m, gf_precision prec, const gf_rays *rays, c
 gf_status gf_trace_rk4(gf_medium m, gf_precision prec, const gf_rays *rays, double omega,
                        double dt, int64_t n_steps, double radius, int64_t checkpoint_every,
                        double *ckpt, void *stream);
+
+/* ------------------------------------------------------------------ adjoint */
+
+/*
+ * gf_adjoint_scratch_bytes -- bytes of device scratch gf_trace_adjoint needs
+ * for n rays, the medium's blob count and segments of checkpoint_every steps:
+ * 8 * (ceil(n/64) * n_blobs + checkpoint_every * 4 * (10 + n_blobs) * n) + 256.
+ * Returns 0 for invalid arguments.
+ */
+size_t gf_adjoint_scratch_bytes(gf_medium m, int64_t n, int64_t checkpoint_every);
+
+/*
+ * gf_trace_adjoint -- gradient of a scalar loss L(y_N) with respect to the blob
+ * amplitudes theta_j = A_j of an isotropic medium, by the discrete adjoint of
+ * the fixed-step RK4 trace of gf_trace_rk4 (the ray equations of Eqs. 2-3
+ * under the RK4 update of Sec. 4; the paper differentiates its expressions
+ * symbolically, Sec. 2.1, here the reverse sweep is hand-derived).
+ * For every step, backwards, with stage points Y_i and lambda = dL/dy_{n+1}:
+ * Kbar_i = dt b_i lambda + dt a_{i+1} Ybar_{i+1}, Ybar_i = J_f(Y_i)^T Kbar_i,
+ * thetabar += (df/dtheta)(Y_i)^T Kbar_i, lambda <- lambda + sum_i Ybar_i.
+ * Inputs (device): ckpt [n_ckpt][6][n] doubles written by gf_trace_rk4 with
+ * the same checkpoint_every (n_ckpt = ceil(n_steps / checkpoint_every));
+ * steps_done [n] int32, the steps that forward call applied to each ray (a
+ * ray that stopped early is differentiated through the steps it took; stop
+ * decisions are held fixed); lambda [6][ld] doubles, dL/dy_N.  Outputs
+ * (device): dL_dtheta [n_blobs] doubles, overwritten; dL_dy0 [6][ld] or NULL.
+ * scratch: device, >= gf_adjoint_scratch_bytes(m, n, checkpoint_every) bytes,
+ * contents overwritten.  The medium must hold the amplitudes of the forward
+ * trace.  Deterministic (fixed-order reductions).
+ * Errors: GF_ERR_INVALID_ARG (no blobs, spline medium, bad sizes, small
+ * scratch, non-device pointers), GF_ERR_CUDA.
+ */
+gf_status gf_trace_adjoint(gf_medium m, int64_t n, double omega, double dt, int64_t n_steps,
+                           int64_t checkpoint_every, const double *ckpt, const int32_t *steps_done,
+                           const double *lambda, int64_t ld, double *dL_dtheta, double *dL_dy0,
+                           void *scratch, size_t scratch_bytes, void *stream);
+
+/* ------------------------------------------------------------ batched DOPRI5 */
+
+/* A batch of media whose rays are stored contiguously per medium. */
+typedef struct gf_batch_s *gf_batch;
+
+typedef enum {
+    GF_SCHED_PERSISTENT = 0,    /* one persistent work-stealing launch (CUDA graph)     */
+    GF_SCHED_PER_MEDIUM = 1     /* one launch per medium (CUDA graph of n_media launches) */
+} gf_schedule;
+
+/* Launch shape of the persistent schedule (see gf_dopri5_autotune). */
+typedef struct {
+    int32_t block;              /* threads per block: 64, 128 or 256                     */
+    int32_t rays_per_thread;    /* ray slots interleaved per thread: 1 or 2              */
+    int32_t compaction;         /* attempted steps between refills of finished lanes     */
+    int32_t chunk;              /* rays per work item popped from the queue (>= 1)       */
+} gf_tune;
+
+#define GF_MAX_BATCH_BLOBS 16   /* blobs per medium in a batch                         */
+
+/*
+ * gf_batch_create -- gather n_media isotropic media of one kind, each with at
+ * most GF_MAX_BATCH_BLOBS blobs, into one device table; the rays of medium j
+ * are rays [offsets[j], offsets[j+1]) of the ray buffers later passed to
+ * gf_trace_dopri5.  offsets: host, n_media + 1 non-decreasing int64, offsets[0]
+ * >= 0.  The media may be destroyed afterwards (the batch holds copies).
+ * Synchronous.  Errors: GF_ERR_INVALID_ARG (NULL, n_media < 1, mixed kinds,
+ * spline media, too many blobs, bad offsets), GF_ERR_OOM, GF_ERR_CUDA.
+ */
+gf_status gf_batch_create(const gf_medium *media, int32_t n_media, const int64_t *offsets,
+                          gf_batch *out);
+
+/* gf_batch_destroy -- free a batch and its cached CUDA graphs (NULL: no-op). */
+gf_status gf_batch_destroy(gf_batch b);
+
+/*
+ * gf_trace_dopri5 -- trace every active ray of the batch with adaptive
+ * Dormand-Prince 5(4) steps until it stops: GF_RAY_EXITED (an accepted step
+ * ending outside |x| = ctl->radius; no event location), GF_RAY_DONE (t reached
+ * ctl->t_max, the last step shortened to land on it), GF_RAY_MAX_STEPS,
+ * GF_RAY_STEP_UNDERFLOW, GF_RAY_CUTOFF or GF_RAY_NONFINITE.
+ * Paper: the ray equations of Eqs. 2-3 (the paper integrates them with RK4;
+ * the embedded 5(4) pair, its error norm and step controller follow Dormand &
+ * Prince 1980 and Hairer-Norsett-Wanner I, Sec. II.4): err = RMS over the 6
+ * components of e_i / (atol + rtol max(|y_i|, |y_new,i|)), accept iff err <= 1,
+ * h <- h min(fac_max, max(fac_min, safety err^(-1/5))), no growth on the step
+ * after a rejection.  rays->steps counts accepted steps; rejects (device, n,
+ * may be NULL) counts rejected ones.  Every ray starts from h = ctl->h0.
+ * Results of a ray do not depend on the schedule: both schedules return bit-
+ * identical buffers.  sched selects the launch structure; tune (may be NULL:
+ * defaults, or the last gf_dopri5_autotune result of this batch) shapes the
+ * persistent launch.  The first call with a given argument set captures a
+ * CUDA graph on a private stream and later calls replay it on `stream`.
+ * Needs rays->n >= offsets[n_media] (GF_F64 rays only).
+ * Errors: GF_ERR_INVALID_ARG, GF_ERR_UNSUPPORTED (GF_F32 rays), GF_ERR_CUDA.
+ */
+gf_status gf_trace_dopri5(gf_batch b, const gf_rays *rays, int32_t *rejects, double omega,
+                          const gf_step_ctl *ctl, gf_schedule sched, const gf_tune *tune,
+                          void *stream);
+
+/*
+ * gf_dopri5_autotune -- time the persistent schedule for block size x rays per
+ * thread x compaction interval x chunk on a prefix of the batch's media (about
+ * an eighth of its rays, at least 65,536 when available), on scratch copies
+ * of `rays` (which are not modified), and return the fastest shape in *out.
+ * The result is remembered by the batch and, when cache_path is non-NULL,
+ * stored in / read from that file keyed by GPU name, SM count, medium kind,
+ * blob count and tolerances.  Synchronous; allocates scratch device memory.
+ * Errors: as gf_trace_dopri5, plus GF_ERR_OOM.
+ */
+gf_status gf_dopri5_autotune(gf_batch b, const gf_rays *rays, double omega, const gf_step_ctl *ctl,
+                             const char *cache_path, gf_tune *out);
 
 #ifdef __cplusplus
 }

@@ -27,6 +27,25 @@ extern "C" {
 gf_status gf_bench_fma_peak(gf_precision prec, int64_t iters, int32_t blocks_per_sm,
                             double *out_tflops, double *out_ms);
 
+/*
+ * gf_bench_set_counters -- from the next launch on, gf_trace_rk4 kernels add
+ * their work to counters[0] (right-hand-side evaluations) and counters[1]
+ * (blob terms actually evaluated, i.e. not skipped as negligible), two device
+ * unsigned 64-bit words owned by the caller; NULL turns counting off.  The
+ * setting is process-wide and not thread-safe (a measurement aid).
+ * Errors: GF_ERR_INVALID_ARG (not device memory).
+ */
+gf_status gf_bench_set_counters(unsigned long long *counters);
+
+/*
+ * gf_bench_exp -- evaluate the library's table-driven exponential (used for
+ * every Gaussian-blob term; defined for a <= 0, returning 0 for a <= -708)
+ * and CUDA's exp on n device doubles `in`, writing out_lib and out_cuda (device,
+ * n each), so that tests can bound its error.  Stream-ordered on `stream`.
+ * Errors: GF_ERR_INVALID_ARG (n < 0, non-device pointers), GF_ERR_CUDA.
+ */
+gf_status gf_bench_exp(const double *in, double *out_lib, double *out_cuda, int64_t n, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

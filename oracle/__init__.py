@@ -66,6 +66,7 @@ def lib():
         _lib.or_index_hess.argtypes = [P, I64, P, P]
         _lib.or_onshell.argtypes = [P, I64, P, P, D, P, P]
         _lib.or_trace_rk4.argtypes = [P, I64, P, P, P, P, P, P, D, D, I64, D, I64, P]
+        _lib.or_trace_rk4_kink.argtypes = [P, I64, P, P, P, P, P, P, D, D, I64, D, P]
         _lib.or_trace_dopri5.argtypes = [P, I64, P, P, P, P, P, P, P, P, D, P]
         _lib.or_tangent_rk4.argtypes = [P, I64, P, P, P, P, P, D, D, I64, D]
         _lib.or_loss_grad.argtypes = [I64, C.c_int, P, P, P, P]
@@ -174,6 +175,17 @@ def trace_rk4(m: Medium, rays: Rays, omega: float, dt: float, n_steps: int,
                        _p(rays.steps), _p(rays.dres), _p(rays.dmax), omega, dt, n_steps,
                        radius, checkpoint_every, _p(ck))
     return ck
+
+
+def trace_rk4_kink(m: Medium, rays: Rays, omega: float, dt: float, n_steps: int,
+                   radius: float = 0.0) -> np.ndarray:
+    """trace_rk4 that also returns, per ray, min over stage points of ||x|^2 - 1|."""
+    s = m.struct()
+    kink = np.full(rays.n, np.inf)
+    lib().or_trace_rk4_kink(C.byref(s), rays.n, _p(rays.y), _p(rays.t), _p(rays.status),
+                            _p(rays.steps), _p(rays.dres), _p(rays.dmax), omega, dt, n_steps,
+                            radius, _p(kink))
+    return kink
 
 
 def dopri5_tableau() -> np.ndarray:

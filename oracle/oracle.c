@@ -353,9 +353,16 @@ void or_onshell(const or_medium *m, int64_t n, const double *x0, const double *d
  * Residual bookkeeping: dmax <- max(dmax, |D(y_n)|) over every state visited
  * (the stage-1 evaluation of each step and the final state); dres = |D(final)|.
  * ckpt (may be NULL): state before step j*every stored at ckpt[j*6 .. j*6+5]. */
+static double or_kink(const double *Y)
+{
+    return fabs(Y[0] * Y[0] + Y[1] * Y[1] + Y[2] * Y[2] - 1.0);
+}
+
+/* kink (may be NULL): min over every stage point of ||x|^2 - 1|, the distance
+ * in |x|^2 from the Luneburg surface where grad n^2 jumps. */
 static void or_rk4_ray(const or_medium *m, double *y, double *t, int32_t *status, int32_t *steps,
                        double *dres, double *dmax, double w, double dt, int64_t n_steps,
-                       double radius, int64_t every, double *ckpt)
+                       double radius, int64_t every, double *ckpt, double *kink)
 {
     double K1[6], K2[6], K3[6], K4[6], Y[6], yn[6], D;
     double t0 = *t, dm = *dmax;
@@ -366,15 +373,19 @@ static void or_rk4_ray(const or_medium *m, double *y, double *t, int32_t *status
         if (ckpt && every > 0 && s % every == 0)
             for (i = 0; i < 6; i++) ckpt[6 * (s / every) + i] = y[i];
         st = or_rhs(m, y, w, K1, &D);
+        if (kink && or_kink(y) < *kink) *kink = or_kink(y);
         if (fabs(D) > dm) dm = fabs(D);
         if (st != OR_ACTIVE) { *status = st; break; }
         for (i = 0; i < 6; i++) Y[i] = y[i] + (dt / 2.0) * K1[i];
+        if (kink && or_kink(Y) < *kink) *kink = or_kink(Y);
         st = or_rhs(m, Y, w, K2, NULL);
         if (st != OR_ACTIVE) { *status = st; break; }
         for (i = 0; i < 6; i++) Y[i] = y[i] + (dt / 2.0) * K2[i];
+        if (kink && or_kink(Y) < *kink) *kink = or_kink(Y);
         st = or_rhs(m, Y, w, K3, NULL);
         if (st != OR_ACTIVE) { *status = st; break; }
         for (i = 0; i < 6; i++) Y[i] = y[i] + dt * K3[i];
+        if (kink && or_kink(Y) < *kink) *kink = or_kink(Y);
         st = or_rhs(m, Y, w, K4, NULL);
         if (st != OR_ACTIVE) { *status = st; break; }
         for (i = 0; i < 6; i++)
@@ -407,7 +418,20 @@ void or_trace_rk4(const or_medium *m, int64_t n, double *y, double *t, int32_t *
 #pragma omp parallel for schedule(dynamic, 16)
     for (r = 0; r < n; r++)
         or_rk4_ray(m, y + 6 * r, t + r, status + r, steps + r, dres + r, dmax + r, w, dt,
-                   n_steps, radius, every, ckpt ? ckpt + 6 * nck * r : NULL);
+                   n_steps, radius, every, ckpt ? ckpt + 6 * nck * r : NULL, NULL);
+}
+
+/* As or_trace_rk4 without checkpoints, also returning kink[r] (initialise to a
+ * large value): the minimum over all stage points of ||x|^2 - 1|. */
+void or_trace_rk4_kink(const or_medium *m, int64_t n, double *y, double *t, int32_t *status,
+                       int32_t *steps, double *dres, double *dmax, double w, double dt,
+                       int64_t n_steps, double radius, double *kink)
+{
+    int64_t r;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (r = 0; r < n; r++)
+        or_rk4_ray(m, y + 6 * r, t + r, status + r, steps + r, dres + r, dmax + r, w, dt,
+                   n_steps, radius, 0, NULL, kink + r);
 }
 
 /* -------------------------------------------------------- public: DOPRI5 */

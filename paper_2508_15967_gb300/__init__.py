@@ -44,6 +44,18 @@ class GfStepCtl(C.Structure):
                 ("fac_max", C.c_double), ("safety", C.c_double), ("max_steps", C.c_int64)]
 
 
+class GfTune(C.Structure):
+    _fields_ = [("block", C.c_int32), ("rays_per_thread", C.c_int32), ("compaction", C.c_int32),
+                ("chunk", C.c_int32)]
+
+    def as_tuple(self):
+        return (self.block, self.rays_per_thread, self.compaction, self.chunk)
+
+
+GF_SCHED_PERSISTENT, GF_SCHED_PER_MEDIUM = 0, 1
+GF_MAX_BATCH_BLOBS = 16
+
+
 class GfError(RuntimeError):
     def __init__(self, fn: str, status: int, msg: str):
         super().__init__(f"{fn} failed with status {status}: {msg}")
@@ -71,6 +83,14 @@ def lib() -> C.CDLL:
             "gf_rays_onshell": ([P, I32, P, P, D, P], I32),
             "gf_trace_rk4": ([P, I32, P, D, D, I64, D, I64, P, P], I32),
             "gf_bench_fma_peak": ([I32, I64, I32, P, P], I32),
+            "gf_bench_set_counters": ([P], I32),
+            "gf_bench_exp": ([P, P, P, I64, P], I32),
+            "gf_adjoint_scratch_bytes": ([P, I64, I64], C.c_size_t),
+            "gf_trace_adjoint": ([P, I64, D, D, I64, I64, P, P, P, I64, P, P, P, C.c_size_t, P], I32),
+            "gf_batch_create": ([P, I32, P, P], I32),
+            "gf_batch_destroy": ([P], I32),
+            "gf_trace_dopri5": ([P, P, P, D, P, I32, P, P], I32),
+            "gf_dopri5_autotune": ([P, P, D, P, C.c_char_p, P], I32),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(L, name)
@@ -215,6 +235,133 @@ def gf_trace_rk4(m: Medium, rays: Rays, omega: float, dt: float, n_steps: int, r
                                               _ptr(ckpt), _stream(stream)))
 
 
+# --------------------------------------------------------------------------- adjoint
+
+def gf_adjoint_scratch_bytes(m: Medium, n: int, checkpoint_every: int) -> int:
+    return int(lib().gf_adjoint_scratch_bytes(m.handle, n, checkpoint_every))
+
+
+def gf_trace_adjoint(m: Medium, n: int, omega: float, dt: float, n_steps: int, checkpoint_every: int,
+                     ckpt: torch.Tensor, steps_done: torch.Tensor, lam: torch.Tensor,
+                     dtheta: torch.Tensor, dy0: torch.Tensor | None = None,
+                     scratch: torch.Tensor | None = None, stream=None) -> None:
+    """dL/dtheta (and dL/dy0) of the RK4 trace from its checkpoints (see gf.h)."""
+    need = gf_adjoint_scratch_bytes(m, n, checkpoint_every)
+    if scratch is None:
+        scratch = torch.empty(max(need, 1), dtype=torch.uint8, device=dtheta.device)
+    if lam.stride(1) != 1 or (dy0 is not None and dy0.stride(0) != lam.stride(0)):
+        raise ValueError("lam and dy0 must be (6, ld) with unit inner stride and the same ld")
+    _check("gf_trace_adjoint", lib().gf_trace_adjoint(
+        m.handle, n, omega, dt, int(n_steps), int(checkpoint_every), _ptr(ckpt), _ptr(steps_done),
+        _ptr(lam), lam.stride(0), _ptr(dtheta), _ptr(dy0), _ptr(scratch), scratch.numel(),
+        _stream(stream)))
+
+
+class TraceRK4(torch.autograd.Function):
+    """y_N = RK4 trace of y0 through a medium whose blob amplitudes are theta.
+
+    forward: gf_medium_set_amplitudes + gf_trace_rk4 with checkpoints every
+    `checkpoint_every` steps; backward: gf_trace_adjoint.  y0 and the output
+    are (6, n) float64 device tensors (rows x y z kx ky kz)."""
+
+    @staticmethod
+    def forward(ctx, theta, y0, medium, omega, dt, n_steps, checkpoint_every):
+        gf_medium_set_amplitudes(medium, theta)
+        n = y0.shape[1]
+        rays = Rays.empty(n, torch.float64, y0.device, diagnostics=False)
+        rays.y.copy_(y0.detach())
+        n_ckpt = max(1, -(-int(n_steps) // int(checkpoint_every)))
+        ckpt = torch.empty((n_ckpt, 6, n), dtype=torch.float64, device=y0.device)
+        gf_trace_rk4(medium, rays, omega, dt, n_steps, 0.0, checkpoint_every, ckpt)
+        ctx.save_for_backward(theta.detach(), ckpt, rays.steps)
+        ctx.medium, ctx.omega, ctx.dt, ctx.n_steps, ctx.every = medium, omega, dt, n_steps, checkpoint_every
+        return rays.y
+
+    @staticmethod
+    def backward(ctx, grad_y):
+        theta, ckpt, steps = ctx.saved_tensors
+        m = ctx.medium
+        gf_medium_set_amplitudes(m, theta)
+        lam = grad_y.to(torch.float64).contiguous()
+        n = lam.shape[1]
+        dtheta = torch.empty(m.n_blobs, dtype=torch.float64, device=lam.device)
+        dy0 = torch.empty_like(lam) if ctx.needs_input_grad[1] else None
+        gf_trace_adjoint(m, n, ctx.omega, ctx.dt, ctx.n_steps, ctx.every, ckpt, steps, lam, dtheta, dy0)
+        return dtheta, dy0, None, None, None, None, None
+
+
+def trace_rk4_autograd(medium: Medium, theta: torch.Tensor, y0: torch.Tensor, omega: float, dt: float,
+                       n_steps: int, checkpoint_every: int = 64) -> torch.Tensor:
+    """Differentiable RK4 trace: returns y_N (6, n); gradients flow to theta and y0."""
+    return TraceRK4.apply(theta, y0, medium, omega, dt, n_steps, checkpoint_every)
+
+
+# --------------------------------------------------------------------------- batched DOPRI5
+
+class Batch:
+    """Handle of a device-resident batch of media (owns it)."""
+
+    def __init__(self, handle: int, n_media: int, offsets: np.ndarray):
+        self.handle = handle
+        self.n_media = n_media
+        self.offsets = offsets
+
+    def close(self) -> None:
+        if self.handle:
+            lib().gf_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gf_batch_create(media: list, offsets) -> Batch:
+    """Gather media (rays of medium j at [offsets[j], offsets[j+1])) into a batch."""
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    if off.shape[0] != len(media) + 1:
+        raise ValueError("offsets must have len(media) + 1 entries")
+    arr = (C.c_void_p * len(media))(*[m.handle for m in media])
+    h = C.c_void_p()
+    _check("gf_batch_create", lib().gf_batch_create(arr, len(media), off.ctypes.data, C.byref(h)))
+    return Batch(h.value, len(media), off)
+
+
+def gf_batch_destroy(b: Batch) -> None:
+    b.close()
+
+
+def step_ctl(rtol=1e-9, atol=1e-9, h0=1e-3, t_max=10.0, radius=1.5, fac_min=0.2, fac_max=10.0,
+             safety=0.9, max_steps=100000) -> GfStepCtl:
+    return GfStepCtl(rtol, atol, h0, t_max, radius, fac_min, fac_max, safety, max_steps)
+
+
+def gf_trace_dopri5(b: Batch, rays: Rays, rejects: torch.Tensor | None = None, omega: float = 1.0,
+                    ctl: GfStepCtl | None = None, sched: int = GF_SCHED_PERSISTENT,
+                    tune: GfTune | tuple | None = None, stream=None) -> None:
+    """Adaptive DOPRI5 over every active ray of the batch, in place (see gf.h)."""
+    s = rays.struct()
+    c = ctl if ctl is not None else step_ctl()
+    t = GfTune(*tune) if isinstance(tune, tuple) else tune
+    _check("gf_trace_dopri5", lib().gf_trace_dopri5(b.handle, C.byref(s), _ptr(rejects), omega,
+                                                    C.byref(c), sched,
+                                                    None if t is None else C.byref(t), _stream(stream)))
+
+
+def gf_dopri5_autotune(b: Batch, rays: Rays, omega: float = 1.0, ctl: GfStepCtl | None = None,
+                       cache_path: str | None = None) -> GfTune:
+    """Pick block x rays/thread x compaction x chunk for the persistent schedule."""
+    s = rays.struct()
+    c = ctl if ctl is not None else step_ctl()
+    out = GfTune()
+    _check("gf_dopri5_autotune", lib().gf_dopri5_autotune(
+        b.handle, C.byref(s), omega, C.byref(c), None if cache_path is None else cache_path.encode(),
+        C.byref(out)))
+    return out
+
+
 def trace_host(m: Medium, x0_host: torch.Tensor, dir_host: torch.Tensor, omega: float, dt: float,
                n_steps: int, rays: Rays | None = None, dirs: torch.Tensor | None = None,
                out: dict | None = None, radius: float = 0.0) -> dict:
@@ -251,6 +398,19 @@ def gf_bench_fma_peak(precision: int, iters: int = 1 << 16, blocks_per_sm: int =
     _check("gf_bench_fma_peak", lib().gf_bench_fma_peak(precision, iters, blocks_per_sm,
                                                         C.byref(tf), C.byref(ms)))
     return tf.value, ms.value
+
+
+def gf_bench_set_counters(counters: torch.Tensor | None) -> None:
+    """Route RK4 work counts (evaluations, blob terms) into a 2-element int64 device tensor."""
+    _check("gf_bench_set_counters", lib().gf_bench_set_counters(_ptr(counters)))
+
+
+def gf_bench_exp(a: torch.Tensor):
+    """(library exp, CUDA exp) of a float64 device tensor."""
+    a = a.contiguous()
+    o1, o2 = torch.empty_like(a), torch.empty_like(a)
+    _check("gf_bench_exp", lib().gf_bench_exp(_ptr(a), _ptr(o1), _ptr(o2), a.numel(), _stream(None)))
+    return o1, o2
 
 
 def medium_from_workload(spec: dict) -> Medium:

@@ -1,0 +1,262 @@
+// gf_adjoint.cu -- discrete adjoint of the fixed-step RK4 ray trace with
+// respect to the blob amplitudes theta_j = A_j of an isotropic medium.
+//
+// For one RK4 step with stage points Y_1 = y, Y_i = y + a_i dt K_{i-1},
+// K_i = f(Y_i), y' = y + dt sum_i b_i K_i (a = 0, 1/2, 1/2, 1; b = 1/6, 1/3,
+// 1/3, 1/6) and lambda = dL/dy', the reverse sweep is, for i = 4 .. 1,
+//     Kbar_i = dt b_i lambda + dt a_{i+1} Ybar_{i+1}      (no second term at i = 4)
+//     Ybar_i = J_f(Y_i)^T Kbar_i,    thetabar += (df/dtheta)(Y_i)^T Kbar_i
+// and then lambda <- lambda + sum_i Ybar_i.
+//
+// For f = (a k, b grad n^2) with a = 1/(w n^2), b = w/(2 n^2), u = 1/n^2 and
+// g = grad n^2, H = Hess n^2, G_j = exp(s_j |x - c_j|^2), s_j = -1/(2 w_j^2):
+//     xbar = b H Kbar_k + C g,   kbar = a Kbar_x,
+//     C = -u (a k.Kbar_x + b g.Kbar_k),
+//     thetabar_j += G_j (C + 2 b s_j (x - c_j).Kbar_k),
+//     H Kbar_k = H_base Kbar_k + sum_j A_j G_j 2 s_j (2 s_j ((x - c_j).Kbar_k)(x - c_j) + Kbar_k).
+//
+// Checkpoints of the forward trace every E steps bound the memory: each
+// segment is recomputed forward from its checkpoint, storing for every step
+// and stage Y_i, n^2, g and all G_j in scratch, then swept in reverse without
+// re-evaluating any exponential.  Per-thread thetabar columns live in shared
+// memory and are reduced block -> grid in a fixed order (deterministic).
+#include <cmath>
+
+#include "gf_internal.cuh"
+
+namespace gf {
+
+constexpr int kAdjBlock = 64;
+constexpr int kStageVals = 10;   // Y (6), n^2, g (3)
+
+struct AdjScratch {
+    double *partials;   // n_blocks x nb
+    double *stage;      // every x 4 x kStageVals x n
+    double *G;          // every x 4 x nb x n
+};
+
+template <int KIND>
+__device__ __forceinline__ void base_index(const MediumParams &m, const double *x, double &n2, double *g)
+{
+    EvalCtx<double> cx;
+    iso_index<double, KIND>(m, nullptr, 0, x, n2, g, cx);
+}
+
+// H_base v for the base index law (Luneburg inside / quadratic: -2 I; GRIN:
+// diag(0, -2c, -2c); homogeneous and Luneburg outside: 0).
+template <int KIND>
+__device__ __forceinline__ void base_hess_vec(const MediumParams &m, const double *x, const double *v,
+                                              double *out)
+{
+    if constexpr (KIND == K_LUNEBURG) {
+        const double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+        const double h = r2 <= 1.0 ? -2.0 : 0.0;
+        out[0] = h * v[0];
+        out[1] = h * v[1];
+        out[2] = h * v[2];
+    } else if constexpr (KIND == K_QUADRATIC) {
+        out[0] = -2.0 * v[0];
+        out[1] = -2.0 * v[1];
+        out[2] = -2.0 * v[2];
+    } else if constexpr (KIND == K_GRIN) {
+        out[0] = 0.0;
+        out[1] = -2.0 * m.n02a2 * v[1];
+        out[2] = -2.0 * m.n02a2 * v[2];
+    } else {
+        out[0] = out[1] = out[2] = 0.0;
+    }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kAdjBlock) adjoint_kernel(
+    const MediumParams m, const int64_t n, const double omega, const double dt, const int64_t n_steps,
+    const int64_t every, const double *__restrict__ ckpt, const int32_t *__restrict__ steps_done,
+    const double *__restrict__ lambda, const int64_t ld, double *__restrict__ dy0, const AdjScratch S)
+{
+    __shared__ double sb[kBlobStride * GF_MAX_BLOBS];
+    __shared__ double sT[64];
+    extern __shared__ double tb[];   // thetabar columns: tb[j * blockDim + tid]
+    const int nb = m.n_blobs;
+    stage_blobs<double>(m, sb);
+    stage_exp_table(sT);
+    for (int j = 0; j < nb; ++j) tb[j * blockDim.x + threadIdx.x] = 0.0;
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        double *acc_t = tb + threadIdx.x;
+        const int B = blockDim.x;
+        const int sd = steps_done[i];
+        double lam[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) lam[c] = lambda[c * ld + i];
+        const double aa[4] = {0.0, 0.5 * dt, 0.5 * dt, dt};
+        const double bb[4] = {dt / 6.0, dt / 3.0, dt / 3.0, dt / 6.0};
+        const int64_t nseg = (n_steps + every - 1) / every;
+        for (int64_t seg = nseg - 1; seg >= 0; --seg) {
+            const int64_t s0 = seg * every;
+            if (s0 >= sd) continue;
+            const int ns = (int)min(every, (int64_t)sd - s0);
+            double y[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) y[c] = ckpt[(seg * 6 + c) * n + i];
+            // ---- forward recompute of the segment, storing every stage
+            for (int s = 0; s < ns; ++s) {
+                double K[6], acc[6];
+#pragma unroll
+                for (int st = 0; st < 4; ++st) {
+                    double Y[6];
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) Y[c] = st == 0 ? y[c] : y[c] + aa[st] * K[c];
+                    double n2, g[3];
+                    base_index<KIND>(m, Y, n2, g);
+                    double *Gs = S.G + ((int64_t)(s * 4 + st) * nb) * n + i;
+                    for (int j = 0; j < nb; ++j) {
+                        const double *b = sb + kBlobStride * j;
+                        const double dx = Y[0] - b[1], dy = Y[1] - b[2], dz = Y[2] - b[3];
+                        const double arg = (dx * dx + dy * dy + dz * dz) * b[4];
+                        double G = 0.0;   // negligible terms (see kBlobCull) are stored as 0
+                        if (arg >= kBlobCull) {
+                            G = exp_tang(arg, sT);
+                            const double AG = b[0] * G;
+                            n2 += AG;
+                            const double cc = b[5] * AG;
+                            g[0] += cc * dx;
+                            g[1] += cc * dy;
+                            g[2] += cc * dz;
+                        }
+                        Gs[(int64_t)j * n] = G;
+                    }
+                    double *Ss = S.stage + ((int64_t)(s * 4 + st) * kStageVals) * n + i;
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) Ss[c * n] = Y[c];
+                    Ss[6 * n] = n2;
+                    Ss[7 * n] = g[0];
+                    Ss[8 * n] = g[1];
+                    Ss[9 * n] = g[2];
+                    const double inv = 1.0 / n2;
+                    const double a = inv / omega, bq = 0.5 * omega * inv;
+                    K[0] = a * Y[3];
+                    K[1] = a * Y[4];
+                    K[2] = a * Y[5];
+                    K[3] = bq * g[0];
+                    K[4] = bq * g[1];
+                    K[5] = bq * g[2];
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) acc[c] = st == 0 ? K[c] : (st == 3 ? acc[c] + K[c] : acc[c] + 2.0 * K[c]);
+                }
+#pragma unroll
+                for (int c = 0; c < 6; ++c) y[c] = y[c] + (dt / 6.0) * acc[c];
+            }
+            // ---- reverse sweep over the segment
+            for (int s = ns - 1; s >= 0; --s) {
+                double ybar_next[6] = {0, 0, 0, 0, 0, 0}, ysum[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+                for (int st = 3; st >= 0; --st) {
+                    double Kb[6];
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) Kb[c] = bb[st] * lam[c] + (st < 3 ? aa[st + 1] * ybar_next[c] : 0.0);
+                    const double *Ss = S.stage + ((int64_t)(s * 4 + st) * kStageVals) * n + i;
+                    double Y[6];
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) Y[c] = Ss[c * n];
+                    const double n2 = Ss[6 * n], g0 = Ss[7 * n], g1 = Ss[8 * n], g2 = Ss[9 * n];
+                    const double u = 1.0 / n2;
+                    const double a = u / omega, bq = 0.5 * omega * u;
+                    const double C = -u * (a * (Y[3] * Kb[0] + Y[4] * Kb[1] + Y[5] * Kb[2]) +
+                                           bq * (g0 * Kb[3] + g1 * Kb[4] + g2 * Kb[5]));
+                    double HK[3];
+                    base_hess_vec<KIND>(m, Y, Kb + 3, HK);
+                    const double *Gs = S.G + ((int64_t)(s * 4 + st) * nb) * n + i;
+                    for (int j = 0; j < nb; ++j) {
+                        const double *b = sb + kBlobStride * j;
+                        const double dx = Y[0] - b[1], dy = Y[1] - b[2], dz = Y[2] - b[3];
+                        const double G = Gs[(int64_t)j * n];
+                        const double dK = dx * Kb[3] + dy * Kb[4] + dz * Kb[5];
+                        const double s2 = b[5];
+                        acc_t[j * B] += G * (C + bq * s2 * dK);
+                        const double t = s2 * b[0] * G;
+                        const double w = s2 * dK;
+                        HK[0] += t * (w * dx + Kb[3]);
+                        HK[1] += t * (w * dy + Kb[4]);
+                        HK[2] += t * (w * dz + Kb[5]);
+                    }
+                    double yb[6];
+                    yb[0] = bq * HK[0] + C * g0;
+                    yb[1] = bq * HK[1] + C * g1;
+                    yb[2] = bq * HK[2] + C * g2;
+                    yb[3] = a * Kb[0];
+                    yb[4] = a * Kb[1];
+                    yb[5] = a * Kb[2];
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) {
+                        ysum[c] += yb[c];
+                        ybar_next[c] = yb[c];
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < 6; ++c) lam[c] += ysum[c];
+            }
+        }
+        if (dy0 != nullptr) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) dy0[c * ld + i] = lam[c];
+        }
+    }
+    __syncthreads();
+    // block reduction of the thetabar columns, fixed order
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+        double sum = 0.0;
+        for (int t = 0; t < (int)blockDim.x; ++t) sum += tb[j * blockDim.x + t];
+        S.partials[(int64_t)blockIdx.x * nb + j] = sum;
+    }
+}
+
+__global__ void adjoint_reduce_kernel(const double *__restrict__ partials, int64_t n_blocks, int nb,
+                                      double *__restrict__ out)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nb) return;
+    double sum = 0.0;
+    for (int64_t b = 0; b < n_blocks; ++b) sum += partials[b * nb + j];
+    out[j] = sum;
+}
+
+size_t adjoint_scratch_bytes(int nb, int64_t n, int64_t every)
+{
+    const int64_t blocks = (n + kAdjBlock - 1) / kAdjBlock;
+    return sizeof(double) * ((size_t)blocks * nb + (size_t)every * 4 * (kStageVals + nb) * (size_t)n) + 256;
+}
+
+cudaError_t launch_adjoint(const MediumParams &m, int64_t n, double omega, double dt, int64_t n_steps,
+                           int64_t every, const double *ckpt, const int32_t *steps_done, const double *lambda,
+                           int64_t ld, double *dtheta, double *dy0, void *scratch, cudaStream_t s)
+{
+    const int nb = m.n_blobs;
+    const int64_t blocks = (n + kAdjBlock - 1) / kAdjBlock;
+    char *base = (char *)(((uintptr_t)scratch + 255) & ~(uintptr_t)255);
+    AdjScratch S;
+    S.partials = (double *)base;
+    S.stage = S.partials + blocks * nb;
+    S.G = S.stage + every * 4 * kStageVals * n;
+    const size_t smem = (size_t)nb * kAdjBlock * sizeof(double);
+#define GF_ADJ(K)                                                                                         \
+    case K:                                                                                               \
+        adjoint_kernel<K><<<(unsigned)blocks, kAdjBlock, smem, s>>>(m, n, omega, dt, n_steps, every,      \
+                                                                    ckpt, steps_done, lambda, ld, dy0, S); \
+        break;
+    switch (m.kind) {
+        GF_ADJ(K_HOMOG)
+        GF_ADJ(K_LUNEBURG)
+        GF_ADJ(K_GRIN)
+        GF_ADJ(K_QUADRATIC)
+    default:
+        return cudaErrorInvalidValue;
+    }
+#undef GF_ADJ
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    adjoint_reduce_kernel<<<(nb + 63) / 64, 64, 0, s>>>(S.partials, blocks, nb, dtheta);
+    return cudaGetLastError();
+}
+
+}  // namespace gf

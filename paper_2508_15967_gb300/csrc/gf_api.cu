@@ -85,7 +85,11 @@ gf_status check_rays(const gf_rays *r, bool need_state)
     return GF_OK;
 }
 
+static unsigned long long *g_work_counters = nullptr;
+unsigned long long *work_counters() { return g_work_counters; }
+
 const MediumParams &params_of(gf_medium m) { return m->p; }
+const double *medium_device_blobs(gf_medium m) { return m->d_blobs64; }
 int device_of(gf_medium m) { return m->device; }
 
 static gf_status check_medium(gf_medium m)
@@ -172,7 +176,8 @@ gf_status gf_medium_create(const gf_medium_desc *d, gf_medium *out)
             set_error("gf_medium_create: blob %d has a non-finite value or width <= 0", j);
             return GF_ERR_INVALID_ARG;
         }
-        double row[kBlobStride] = {b[0], b[1], b[2], b[3], -1.0 / (2.0 * w * w)};
+        const double sj = -1.0 / (2.0 * w * w);
+        double row[kBlobStride] = {b[0], b[1], b[2], b[3], sj, 2.0 * sj};
         for (int c = 0; c < kBlobStride; ++c) {
             t64[kBlobStride * j + c] = row[c];
             t32[kBlobStride * j + c] = (float)row[c];
@@ -299,6 +304,56 @@ gf_status gf_trace_rk4(gf_medium m, gf_precision prec, const gf_rays *rays, doub
     return cuda_status(launch_rk4(m->p, prec, *rays, omega, dt, n_steps, radius,
                                   ckpt ? checkpoint_every : 1, ckpt, (cudaStream_t)stream),
                        "gf_trace_rk4 launch");
+}
+
+gf_status gf_bench_set_counters(unsigned long long *counters)
+{
+    if (counters && check_device_ptr(counters, "counters") != GF_OK) return GF_ERR_INVALID_ARG;
+    g_work_counters = counters;
+    return GF_OK;
+}
+
+size_t gf_adjoint_scratch_bytes(gf_medium m, int64_t n, int64_t checkpoint_every)
+{
+    if (m == nullptr || n < 0 || checkpoint_every < 1 || m->p.n_blobs < 1) return 0;
+    return adjoint_scratch_bytes(m->p.n_blobs, n, checkpoint_every);
+}
+
+gf_status gf_trace_adjoint(gf_medium m, int64_t n, double omega, double dt, int64_t n_steps,
+                           int64_t checkpoint_every, const double *ckpt, const int32_t *steps_done,
+                           const double *lambda, int64_t ld, double *dL_dtheta, double *dL_dy0,
+                           void *scratch, size_t scratch_bytes, void *stream)
+{
+    gf_status s;
+    if ((s = check_medium(m)) != GF_OK) return s;
+    if (m->p.kind == GF_MED_SPLINE || m->p.n_blobs < 1) {
+        set_error("gf_trace_adjoint: needs an isotropic medium with at least one blob");
+        return GF_ERR_INVALID_ARG;
+    }
+    if (n < 0 || ld < n || n_steps < 0 || checkpoint_every < 1 || checkpoint_every > 4096 ||
+        !(omega > 0) || !std::isfinite(omega) || !(dt > 0) || !std::isfinite(dt)) {
+        set_error("gf_trace_adjoint: need n >= 0, ld >= n, n_steps >= 0, 1 <= checkpoint_every <= 4096, "
+                  "omega > 0, dt > 0");
+        return GF_ERR_INVALID_ARG;
+    }
+    if ((s = check_device_ptr(dL_dtheta, "dL_dtheta")) != GF_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n == 0) {
+        return cuda_status(cudaMemsetAsync(dL_dtheta, 0, sizeof(double) * m->p.n_blobs, st),
+                           "gf_trace_adjoint memset");
+    }
+    if ((s = check_device_ptr(ckpt, "ckpt")) != GF_OK || (s = check_device_ptr(steps_done, "steps_done")) != GF_OK ||
+        (s = check_device_ptr(lambda, "lambda")) != GF_OK || (s = check_device_ptr(scratch, "scratch")) != GF_OK)
+        return s;
+    if (dL_dy0 && (s = check_device_ptr(dL_dy0, "dL_dy0")) != GF_OK) return s;
+    const size_t need = adjoint_scratch_bytes(m->p.n_blobs, n, checkpoint_every);
+    if (scratch_bytes < need) {
+        set_error("gf_trace_adjoint: scratch has %zu bytes, needs %zu", scratch_bytes, need);
+        return GF_ERR_INVALID_ARG;
+    }
+    return cuda_status(launch_adjoint(m->p, n, omega, dt, n_steps, checkpoint_every, ckpt, steps_done, lambda,
+                                      ld, dL_dtheta, dL_dy0, scratch, st),
+                       "gf_trace_adjoint launch");
 }
 
 }  // extern "C"

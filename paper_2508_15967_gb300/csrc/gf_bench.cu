@@ -50,7 +50,34 @@ static gf_status run_peak(int64_t iters, int bps, double *tflops, double *ms)
     return GF_OK;
 }
 
+__global__ void exp_check_kernel(const double *in, double *out_lib, double *out_cuda, int64_t n)
+{
+    __shared__ double sT[64];
+    stage_exp_table(sT);
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out_lib[i] = exp_tang(in[i], sT);
+    out_cuda[i] = exp(in[i]);
+}
+
 }  // namespace gf
+
+extern "C" gf_status gf_bench_exp(const double *in, double *out_lib, double *out_cuda, int64_t n,
+                                  void *stream)
+{
+    if (n < 0) {
+        gf::set_error("gf_bench_exp: n < 0");
+        return GF_ERR_INVALID_ARG;
+    }
+    if (n == 0) return GF_OK;
+    gf_status s;
+    if ((s = gf::check_device_ptr(in, "in")) != GF_OK || (s = gf::check_device_ptr(out_lib, "out_lib")) != GF_OK ||
+        (s = gf::check_device_ptr(out_cuda, "out_cuda")) != GF_OK)
+        return s;
+    gf::exp_check_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(in, out_lib, out_cuda, n);
+    return gf::cuda_status(cudaGetLastError(), "gf_bench_exp launch");
+}
 
 extern "C" gf_status gf_bench_fma_peak(gf_precision prec, int64_t iters, int32_t blocks_per_sm,
                                        double *out_tflops, double *out_ms)

@@ -1,0 +1,865 @@
+// gf_dopri5.cu -- batched adaptive Dormand-Prince 5(4) ray tracing over many
+// media: a persistent work-stealing kernel with warp-level refill of finished
+// lanes, a one-launch-per-medium baseline that runs the same per-ray code, the
+// CUDA-graph capture of both schedules, and the launch-shape autotuner.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "gf_internal.cuh"
+
+namespace gf {
+
+// Dormand & Prince (1980) RK5(4)7M coefficients; e = b - b* (5th minus 4th order).
+namespace dp {
+constexpr double a21 = 1.0 / 5.0;
+constexpr double a31 = 3.0 / 40.0, a32 = 9.0 / 40.0;
+constexpr double a41 = 44.0 / 45.0, a42 = -56.0 / 15.0, a43 = 32.0 / 9.0;
+constexpr double a51 = 19372.0 / 6561.0, a52 = -25360.0 / 2187.0, a53 = 64448.0 / 6561.0,
+                 a54 = -212.0 / 729.0;
+constexpr double a61 = 9017.0 / 3168.0, a62 = -355.0 / 33.0, a63 = 46732.0 / 5247.0,
+                 a64 = 49.0 / 176.0, a65 = -5103.0 / 18656.0;
+constexpr double a71 = 35.0 / 384.0, a73 = 500.0 / 1113.0, a74 = 125.0 / 192.0,
+                 a75 = -2187.0 / 6784.0, a76 = 11.0 / 84.0;
+constexpr double e1 = 35.0 / 384.0 - 5179.0 / 57600.0, e3 = 500.0 / 1113.0 - 7571.0 / 16695.0,
+                 e4 = 125.0 / 192.0 - 393.0 / 640.0, e5 = -2187.0 / 6784.0 - (-92097.0 / 339200.0),
+                 e6 = 11.0 / 84.0 - 187.0 / 2100.0, e7 = 0.0 - 1.0 / 40.0;
+}  // namespace dp
+
+struct Ctl {
+    double rtol, atol, h0, t_max, r2, fac_min, fac_max, safety;
+    int64_t max_steps, max_attempts;
+    Omega<double> om;
+};
+
+// Device view of a batch.
+struct BatchView {
+    int32_t n_media, nb_max, n_items, pad;
+    const double *blobs;        // n_media x nb_max x kBlobStride
+    const int32_t *nb;          // n_media
+    const double *base;         // n_media x 3: n_h2, n02, n02a2
+    const int32_t *item_medium; // n_items
+    const int64_t *item_begin;  // n_items
+    const int64_t *item_end;    // n_items
+};
+
+struct Lane {
+    double y[6], K1[6];
+    double t, h, fmax, dm;
+    int64_t ray;
+    int32_t steps, rejects, status, attempts, nb;
+    MediumParams mp;
+};
+
+template <int KIND>
+struct LaneRhs {
+    const Lane &L;
+    const double *sm;
+    int stride;
+    const Omega<double> &om;
+    const double *T;
+    template <bool WANT_D = true>
+    __device__ __forceinline__ bool eval(const double *y, double *f, double &D) const
+    {
+        EvalCtx<double> cx;
+        cx.T = T;
+        return rhs_iso<double, KIND, WANT_D>(L.mp, sm, L.nb, om, y, f, D, cx, stride);
+    }
+};
+
+// Load ray `ray` of medium `med` into lane L and its per-thread shared-memory
+// blob slot (field f of blob j at sm[(5 j + f) * stride]).  Returns false if
+// the ray is not active.
+template <int KIND>
+__device__ __forceinline__ bool lane_load(Lane &L, const BatchView &B, const RaysView<double> &r,
+                                          int med, int64_t ray, double *sm, int stride, const double *T,
+                                          const Ctl &c)
+{
+    L.status = r.status[ray];
+    if (L.status != GF_RAY_ACTIVE) return false;
+    L.ray = ray;
+    L.nb = B.nb[med];
+    L.mp.kind = KIND;
+    L.mp.n_h2 = B.base[3 * med];
+    L.mp.n02 = B.base[3 * med + 1];
+    L.mp.n02a2 = B.base[3 * med + 2];
+    const double *src = B.blobs + (int64_t)med * B.nb_max * kBlobStride;
+    for (int j = 0; j < L.nb * kBlobStride; ++j) sm[j * stride] = src[j];
+#pragma unroll
+    for (int c2 = 0; c2 < 6; ++c2) L.y[c2] = r.y[c2 * r.ld + ray];
+    L.t = r.t[ray];
+    L.steps = r.steps[ray];
+    L.rejects = 0;
+    L.attempts = 0;
+    L.dm = r.d_max ? r.d_max[ray] : 0.0;
+    L.h = c.h0;
+    L.fmax = c.fac_max;
+    double D;
+    const LaneRhs<KIND> f{L, sm, stride, c.om, T};
+    bool ok = f.eval(L.y, L.K1, D);
+    L.dm = fmax(L.dm, fabs(D));
+    if (!ok) L.status = GF_RAY_CUTOFF;
+    return true;
+}
+
+// Final residual and store of a lane whose ray stopped.
+template <int KIND>
+__device__ __forceinline__ void lane_store(const Lane &L, const RaysView<double> &r, int32_t *rejects,
+                                           const double *sm, int stride, const double *T, const Ctl &c)
+{
+    double K[6], D;
+    const LaneRhs<KIND> f{L, sm, stride, c.om, T};
+    f.eval(L.y, K, D);
+    const double dm = fmax(L.dm, fabs(D));
+    const int64_t i = L.ray;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) r.y[c * r.ld + i] = L.y[c];
+    r.t[i] = L.t;
+    r.status[i] = L.status;
+    r.steps[i] = L.steps;
+    if (rejects) rejects[i] = L.rejects;
+    if (r.d_res) r.d_res[i] = fabs(D);
+    if (r.d_max) r.d_max[i] = dm;
+}
+
+// One attempted DOPRI5 step of an active lane (the step-size controller of
+// Hairer-Norsett-Wanner I, Sec. II.4).  Leaves L.status != ACTIVE when the ray stops.
+template <int KIND>
+__device__ __forceinline__ void lane_attempt(Lane &L, const double *sm, int stride, const double *T,
+                                             const Ctl &c)
+{
+    using namespace dp;
+    if (L.steps >= c.max_steps || L.attempts >= c.max_attempts) { L.status = GF_RAY_MAX_STEPS; return; }
+    if (L.t >= c.t_max) { L.status = GF_RAY_DONE; return; }
+    ++L.attempts;
+    double hs = L.h;
+    bool last = false;
+    if (L.t + hs >= c.t_max) { hs = c.t_max - L.t; last = true; }
+    if (hs < 1e-14 * fmax(1.0, fabs(L.t))) { L.status = GF_RAY_STEP_UNDERFLOW; return; }
+    const LaneRhs<KIND> f{L, sm, stride, c.om, T};
+    const double *y = L.y, *K1 = L.K1;
+    double K2[6], K3[6], K4[6], K5[6], K6[6], K7[6], Y[6], D;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) Y[i] = y[i] + hs * (a21 * K1[i]);
+    if (!f.template eval<false>(Y, K2, D)) { L.status = GF_RAY_CUTOFF; return; }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) Y[i] = y[i] + hs * (a31 * K1[i] + a32 * K2[i]);
+    if (!f.template eval<false>(Y, K3, D)) { L.status = GF_RAY_CUTOFF; return; }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) Y[i] = y[i] + hs * (a41 * K1[i] + a42 * K2[i] + a43 * K3[i]);
+    if (!f.template eval<false>(Y, K4, D)) { L.status = GF_RAY_CUTOFF; return; }
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        Y[i] = y[i] + hs * (a51 * K1[i] + a52 * K2[i] + a53 * K3[i] + a54 * K4[i]);
+    if (!f.template eval<false>(Y, K5, D)) { L.status = GF_RAY_CUTOFF; return; }
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        Y[i] = y[i] + hs * (a61 * K1[i] + a62 * K2[i] + a63 * K3[i] + a64 * K4[i] + a65 * K5[i]);
+    if (!f.template eval<false>(Y, K6, D)) { L.status = GF_RAY_CUTOFF; return; }
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        Y[i] = y[i] + hs * (a71 * K1[i] + a73 * K3[i] + a74 * K4[i] + a75 * K5[i] + a76 * K6[i]);
+    if (!f.template eval<true>(Y, K7, D)) { L.status = GF_RAY_CUTOFF; return; }
+    bool fin = true;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) fin = fin && isfinite(Y[i]) && isfinite(K7[i]);
+    if (!fin) { L.status = GF_RAY_NONFINITE; return; }
+    double err = 0.0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        double e = hs * (e1 * K1[i] + e3 * K3[i] + e4 * K4[i] + e5 * K5[i] + e6 * K6[i] + e7 * K7[i]);
+        double sc = c.atol + c.rtol * fmax(fabs(y[i]), fabs(Y[i]));
+        double q = e / sc;
+        err += q * q;
+    }
+    err = sqrt(err / 6.0);
+    const double fac = err > 0.0 ? c.safety * pow(err, -0.2) : L.fmax;
+    if (err <= 1.0) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            L.y[i] = Y[i];
+            L.K1[i] = K7[i];
+        }
+        L.t = last ? c.t_max : L.t + hs;
+        ++L.steps;
+        L.dm = fmax(L.dm, fabs(D));
+        L.h = hs * fmin(L.fmax, fmax(c.fac_min, fac));
+        L.fmax = c.fac_max;
+        if (c.r2 > 0.0 && Y[0] * Y[0] + Y[1] * Y[1] + Y[2] * Y[2] > c.r2) L.status = GF_RAY_EXITED;
+    } else {
+        ++L.rejects;
+        L.h = hs * fmin(L.fmax, fmax(c.fac_min, fac));
+        L.fmax = 1.0;
+    }
+}
+
+// ------------------------------------------------------- one launch per medium
+
+template <int KIND>
+__global__ void __launch_bounds__(128) dopri5_medium_kernel(const BatchView B, const int med,
+                                                            const int64_t lo, const int64_t hi,
+                                                            const RaysView<double> r, int32_t *rejects,
+                                                            const Ctl c)
+{
+    extern __shared__ double sm_dyn[];
+    __shared__ double sT[64];
+    stage_exp_table(sT);
+    __syncthreads();
+    const int stride = blockDim.x;
+    double *sm = sm_dyn + threadIdx.x;
+    const int64_t ray = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ray >= hi) return;
+    Lane L;
+    if (!lane_load<KIND>(L, B, r, med, ray, sm, stride, sT, c)) return;
+    while (L.status == GF_RAY_ACTIVE) lane_attempt<KIND>(L, sm, stride, sT, c);
+    lane_store<KIND>(L, r, rejects, sm, stride, sT, c);
+}
+
+// ------------------------------------------------------------- persistent
+
+// Warps pop work items (a range of rays of one medium) from a global counter.
+// Every `compaction` attempted steps the warp ballots its finished lanes and
+// refills them with the next rays of its current item, popping new items as
+// items run dry; lanes may hold rays of different media (each lane has its own
+// blob slot in shared memory).  RPT ray slots per thread are interleaved.
+template <int KIND, int RPT>
+__global__ void dopri5_persistent_kernel(const BatchView B, const RaysView<double> r,
+                                         int32_t *rejects, const Ctl c,
+                                         const int compaction, int *__restrict__ head)
+{
+    extern __shared__ double sm_dyn[];
+    __shared__ double sT[64];
+    stage_exp_table(sT);
+    __syncthreads();
+    const int stride = blockDim.x * RPT;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    Lane L[RPT];
+    bool active[RPT];
+#pragma unroll
+    for (int s = 0; s < RPT; ++s) active[s] = false;
+    int64_t cur = 0, end = 0;
+    int cur_med = 0;
+    bool exhausted = false;
+    for (;;) {
+#pragma unroll
+        for (int s = 0; s < RPT; ++s) {
+            double *sm = sm_dyn + s * blockDim.x + threadIdx.x;
+            unsigned freem = __ballot_sync(0xffffffffu, !active[s]);
+            while (freem != 0u && !exhausted) {
+                if (cur >= end) {
+                    int item = 0;
+                    if (lane == 0) item = atomicAdd(head, 1);
+                    item = __shfl_sync(0xffffffffu, item, 0);
+                    if (item >= B.n_items) {
+                        exhausted = true;
+                        break;
+                    }
+                    cur = B.item_begin[item];
+                    end = B.item_end[item];
+                    cur_med = B.item_medium[item];
+                }
+                const int nfree = __popc(freem);
+                const int take = (int)min((int64_t)nfree, end - cur);
+                const int rank = __popc(freem & lt_mask);
+                if (!active[s] && rank < take) {
+                    if (lane_load<KIND>(L[s], B, r, cur_med, cur + rank, sm, stride, sT, c)) {
+                        if (L[s].status == GF_RAY_ACTIVE)
+                            active[s] = true;
+                        else
+                            lane_store<KIND>(L[s], r, rejects, sm, stride, sT, c);
+                    }
+                }
+                cur += take;
+                freem = __ballot_sync(0xffffffffu, !active[s]);
+            }
+        }
+        bool any = false;
+#pragma unroll
+        for (int s = 0; s < RPT; ++s) any = any || active[s];
+        if (!__any_sync(0xffffffffu, any)) break;
+        for (int it = 0; it < compaction; ++it) {
+#pragma unroll
+            for (int s = 0; s < RPT; ++s) {
+                if (active[s]) {
+                    double *sm = sm_dyn + s * blockDim.x + threadIdx.x;
+                    lane_attempt<KIND>(L[s], sm, stride, sT, c);
+                    if (L[s].status != GF_RAY_ACTIVE) {
+                        lane_store<KIND>(L[s], r, rejects, sm, stride, sT, c);
+                        active[s] = false;
+                    }
+                }
+            }
+        }
+    }
+}
+
+}  // namespace gf
+
+// ------------------------------------------------------------------- host side
+
+using namespace gf;
+
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    std::string key;
+};
+
+struct gf_batch_s {
+    int device = -1;
+    int kind = 0, n_media = 0, nb_max = 0;
+    std::vector<int64_t> offsets;
+    double *d_blobs = nullptr, *d_base = nullptr;
+    int32_t *d_nb = nullptr;
+    int *d_head = nullptr;
+    // work items for the current chunk size
+    int chunk = 0, n_items = 0;
+    int32_t *d_item_medium = nullptr;
+    int64_t *d_item_begin = nullptr, *d_item_end = nullptr;
+    cudaStream_t capture = nullptr;
+    GraphCache graphs[2];
+    bool tuned = false;
+    gf_tune tune{};
+    std::vector<int> media_kind_nb;  // per medium blob count (host)
+};
+
+namespace gf {
+const double *medium_device_blobs(gf_medium m);
+}
+
+static void batch_free(gf_batch b)
+{
+    cudaFree(b->d_blobs);
+    cudaFree(b->d_base);
+    cudaFree(b->d_nb);
+    cudaFree(b->d_head);
+    cudaFree(b->d_item_medium);
+    cudaFree(b->d_item_begin);
+    cudaFree(b->d_item_end);
+    for (auto &g : b->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (b->capture) cudaStreamDestroy(b->capture);
+    delete b;
+}
+
+static gf_status build_items(gf_batch b, int chunk)
+{
+    if (b->chunk == chunk && b->d_item_medium) return GF_OK;
+    std::vector<int32_t> med;
+    std::vector<int64_t> beg, end;
+    for (int m = 0; m < b->n_media; ++m)
+        for (int64_t lo = b->offsets[m]; lo < b->offsets[m + 1]; lo += chunk) {
+            med.push_back(m);
+            beg.push_back(lo);
+            end.push_back(std::min(lo + chunk, b->offsets[m + 1]));
+        }
+    cudaFree(b->d_item_medium);
+    cudaFree(b->d_item_begin);
+    cudaFree(b->d_item_end);
+    b->d_item_medium = nullptr;
+    b->d_item_begin = b->d_item_end = nullptr;
+    size_t n = std::max<size_t>(med.size(), 1);
+    gf_status s;
+    if ((s = cuda_status(cudaMalloc(&b->d_item_medium, n * sizeof(int32_t)), "cudaMalloc(items)")) != GF_OK ||
+        (s = cuda_status(cudaMalloc(&b->d_item_begin, n * sizeof(int64_t)), "cudaMalloc(items)")) != GF_OK ||
+        (s = cuda_status(cudaMalloc(&b->d_item_end, n * sizeof(int64_t)), "cudaMalloc(items)")) != GF_OK)
+        return s;
+    if (!med.empty()) {
+        cudaMemcpy(b->d_item_medium, med.data(), med.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+        cudaMemcpy(b->d_item_begin, beg.data(), beg.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+        if ((s = cuda_status(cudaMemcpy(b->d_item_end, end.data(), end.size() * sizeof(int64_t),
+                                        cudaMemcpyHostToDevice), "cudaMemcpy(items)")) != GF_OK)
+            return s;
+    }
+    b->chunk = chunk;
+    b->n_items = (int)med.size();
+    for (auto &g : b->graphs) g.key.clear();
+    return GF_OK;
+}
+
+static BatchView view_of(gf_batch b)
+{
+    return BatchView{b->n_media, b->nb_max, b->n_items, 0, b->d_blobs, b->d_nb, b->d_base,
+                     b->d_item_medium, b->d_item_begin, b->d_item_end};
+}
+
+static Ctl ctl_of(const gf_step_ctl *c, double omega)
+{
+    Ctl k;
+    k.om = make_omega<double>(omega);
+    k.rtol = c->rtol;
+    k.atol = c->atol;
+    k.h0 = c->h0;
+    k.t_max = c->t_max;
+    k.r2 = c->radius > 0 ? c->radius * c->radius : 0.0;
+    k.fac_min = c->fac_min;
+    k.fac_max = c->fac_max;
+    k.safety = c->safety;
+    k.max_steps = c->max_steps;
+    // rejections shrink h geometrically to h_min, so attempts are bounded; this
+    // cap only guards against a controller that never converges
+    k.max_attempts = 4 * c->max_steps + 100000;
+    return k;
+}
+
+static gf_status check_ctl(const gf_step_ctl *c)
+{
+    if (c == nullptr || !(c->rtol > 0) || !(c->atol > 0) || !(c->h0 > 0) || !std::isfinite(c->t_max) ||
+        !std::isfinite(c->radius) || !(c->fac_min > 0 && c->fac_min < 1) || !(c->fac_max > 1) ||
+        !std::isfinite(c->fac_max) || !(c->safety > 0 && c->safety <= 1) || c->max_steps <= 0 ||
+        c->max_steps > INT32_MAX / 8) {
+        set_error("gf_step_ctl: need rtol, atol, h0 > 0, 0 < fac_min < 1 < fac_max, 0 < safety <= 1, "
+                  "finite t_max and radius, 0 < max_steps < 2^28");
+        return GF_ERR_INVALID_ARG;
+    }
+    return GF_OK;
+}
+
+static gf_status check_tune(const gf_tune *t)
+{
+    if (!(t->block == 64 || t->block == 128 || t->block == 256) ||
+        !(t->rays_per_thread == 1 || t->rays_per_thread == 2) || t->compaction < 1 ||
+        t->compaction > 1024 || t->chunk < 1) {
+        set_error("gf_tune: block in {64,128,256}, rays_per_thread in {1,2}, 1 <= compaction <= 1024, chunk >= 1");
+        return GF_ERR_INVALID_ARG;
+    }
+    return GF_OK;
+}
+
+static const gf_tune kDefaultTune = {128, 1, 4, 64};
+
+// Launch shape resolved outside any stream capture (function attributes and
+// occupancy queries are not stream work).
+struct LaunchPlan {
+    int grid = 0, block = 128, rpt = 1;
+    size_t smem = 0;
+};
+
+template <int KIND, int RPT>
+static cudaError_t plan_persistent_rpt(gf_batch b, const gf_tune &t, LaunchPlan &p)
+{
+    auto k = dopri5_persistent_kernel<KIND, RPT>;
+    p.block = t.block;
+    p.rpt = RPT;
+    p.smem = (size_t)b->nb_max * kBlobStride * sizeof(double) * t.block * RPT;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem)) != cudaSuccess)
+        return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, t.block, p.smem)) != cudaSuccess)
+        return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    p.grid = sms * per_sm;
+    return cudaSuccess;
+}
+
+template <int KIND>
+static cudaError_t plan(gf_batch b, gf_schedule sched, const gf_tune &t, LaunchPlan &p)
+{
+    if (sched == GF_SCHED_PERSISTENT)
+        return t.rays_per_thread == 1 ? plan_persistent_rpt<KIND, 1>(b, t, p)
+                                      : plan_persistent_rpt<KIND, 2>(b, t, p);
+    p.block = 128;
+    p.smem = (size_t)b->nb_max * kBlobStride * sizeof(double) * p.block;
+    return cudaFuncSetAttribute(dopri5_medium_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)p.smem);
+}
+
+template <int KIND>
+static cudaError_t launch(gf_batch b, gf_schedule sched, const gf_tune &t, const LaunchPlan &p,
+                          const RaysView<double> &r, int32_t *rejects, double omega, const Ctl &c,
+                          cudaStream_t s)
+{
+    const BatchView B = view_of(b);
+    if (sched == GF_SCHED_PERSISTENT) {
+        cudaError_t e = cudaMemsetAsync(b->d_head, 0, sizeof(int), s);
+        if (e != cudaSuccess) return e;
+        if (p.rpt == 1)
+            dopri5_persistent_kernel<KIND, 1><<<p.grid, p.block, p.smem, s>>>(B, r, rejects, c,
+                                                                             t.compaction, b->d_head);
+        else
+            dopri5_persistent_kernel<KIND, 2><<<p.grid, p.block, p.smem, s>>>(B, r, rejects, c,
+                                                                             t.compaction, b->d_head);
+        return cudaGetLastError();
+    }
+    for (int m = 0; m < b->n_media; ++m) {
+        const int64_t lo = b->offsets[m], hi = b->offsets[m + 1];
+        if (hi <= lo) continue;
+        const unsigned blocks = (unsigned)((hi - lo + p.block - 1) / p.block);
+        dopri5_medium_kernel<KIND><<<blocks, p.block, p.smem, s>>>(B, m, lo, hi, r, rejects, c);
+    }
+    return cudaGetLastError();
+}
+
+#define GF_D5_DISPATCH(FN, ...)                          \
+    switch (b->kind) {                                   \
+    case K_HOMOG: return FN<K_HOMOG>(__VA_ARGS__);       \
+    case K_LUNEBURG: return FN<K_LUNEBURG>(__VA_ARGS__); \
+    case K_GRIN: return FN<K_GRIN>(__VA_ARGS__);         \
+    case K_QUADRATIC: return FN<K_QUADRATIC>(__VA_ARGS__); \
+    default: return cudaErrorInvalidValue;               \
+    }
+
+static cudaError_t plan_any(gf_batch b, gf_schedule sched, const gf_tune &t, LaunchPlan &p)
+{
+    GF_D5_DISPATCH(plan, b, sched, t, p)
+}
+
+static cudaError_t enqueue(gf_batch b, gf_schedule sched, const gf_tune &t, const LaunchPlan &p,
+                           const RaysView<double> &r, int32_t *rejects, double omega, const Ctl &c,
+                           cudaStream_t s)
+{
+    GF_D5_DISPATCH(launch, b, sched, t, p, r, rejects, omega, c, s)
+}
+
+static std::string graph_key(gf_schedule sched, const gf_tune &t, const gf_rays *rays, int32_t *rejects,
+                             double omega, const gf_step_ctl *c)
+{
+    char buf[512];
+    snprintf(buf, sizeof buf, "%d|%d,%d,%d,%d|%lld,%lld,%p,%p,%p,%p,%p,%p,%p|%p|%.17g|%.17g,%.17g,%.17g,%.17g,%.17g,%.17g,%.17g,%.17g,%lld",
+             (int)sched, t.block, t.rays_per_thread, t.compaction, t.chunk, (long long)rays->n,
+             (long long)rays->ld, rays->y, (void *)rays->t, (void *)rays->status, (void *)rays->steps,
+             (void *)rays->d_res, (void *)rays->d_max, (void *)rejects, (void *)rejects, omega, c->rtol,
+             c->atol, c->h0, c->t_max, c->radius, c->fac_min, c->fac_max, c->safety,
+             (long long)c->max_steps);
+    return buf;
+}
+
+static gf_status run_dopri5(gf_batch b, const gf_rays *rays, int32_t *rejects, double omega,
+                            const gf_step_ctl *ctl, gf_schedule sched, const gf_tune &t,
+                            cudaStream_t stream, bool use_graph)
+{
+    gf_status s;
+    if (sched == GF_SCHED_PERSISTENT && (s = build_items(b, t.chunk)) != GF_OK) return s;
+    const RaysView<double> r{rays->n, rays->ld, (double *)rays->y, rays->t, rays->status, rays->steps,
+                             rays->d_res, rays->d_max};
+    const Ctl c = ctl_of(ctl, omega);
+    LaunchPlan p;
+    if ((s = cuda_status(plan_any(b, sched, t, p), "gf_trace_dopri5 launch plan")) != GF_OK) return s;
+    if (!use_graph)
+        return cuda_status(enqueue(b, sched, t, p, r, rejects, omega, c, stream), "gf_trace_dopri5 launch");
+    GraphCache &g = b->graphs[sched];
+    const std::string key = graph_key(sched, t, rays, rejects, omega, ctl);
+    if (g.exec == nullptr || g.key != key) {
+        if (g.exec) {
+            cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+        }
+        if (b->capture == nullptr &&
+            (s = cuda_status(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking),
+                             "cudaStreamCreate")) != GF_OK)
+            return s;
+        cudaGraph_t graph = nullptr;
+        if ((s = cuda_status(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal),
+                             "cudaStreamBeginCapture")) != GF_OK)
+            return s;
+        cudaError_t le = enqueue(b, sched, t, p, r, rejects, omega, c, b->capture);
+        cudaError_t ce = cudaStreamEndCapture(b->capture, &graph);
+        if (le != cudaSuccess || ce != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_status(le != cudaSuccess ? le : ce, "gf_trace_dopri5 capture");
+        }
+        cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if ((s = cuda_status(ie, "cudaGraphInstantiate")) != GF_OK) return s;
+        g.key = key;
+    }
+    return cuda_status(cudaGraphLaunch(g.exec, stream), "cudaGraphLaunch");
+}
+
+static gf_status check_batch_rays(gf_batch b, const gf_rays *rays, int32_t *rejects)
+{
+    gf_status s;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != b->device) {
+        set_error("batch lives on device %d, current device is %d", b->device, dev);
+        return GF_ERR_INVALID_ARG;
+    }
+    if ((s = check_rays(rays, true)) != GF_OK) return s;
+    if (rays->n < b->offsets.back()) {
+        set_error("gf_trace_dopri5: rays.n = %lld < offsets[n_media] = %lld", (long long)rays->n,
+                  (long long)b->offsets.back());
+        return GF_ERR_INVALID_ARG;
+    }
+    if (rejects && rays->n > 0 && (s = check_device_ptr(rejects, "rejects")) != GF_OK) return s;
+    return GF_OK;
+}
+
+// ---------------------------------------------------------------- autotune
+
+static std::string tune_key(gf_batch b, const gf_step_ctl *c)
+{
+    cudaDeviceProp p;
+    cudaGetDeviceProperties(&p, b->device);
+    char buf[400];
+    snprintf(buf, sizeof buf, "%s|sm%d|kind%d|nb%d|f64|rtol%.3g|atol%.3g", p.name, p.multiProcessorCount,
+             b->kind, b->nb_max, c->rtol, c->atol);
+    return buf;
+}
+
+static bool cache_lookup(const char *path, const std::string &key, gf_tune *out)
+{
+    if (!path) return false;
+    FILE *f = fopen(path, "r");
+    if (!f) return false;
+    char line[1024];
+    bool found = false;
+    while (fgets(line, sizeof line, f)) {
+        // line format: <key>\t<block> <rpt> <compaction> <chunk>
+        char *tab = strchr(line, '\t');
+        if (!tab) continue;
+        *tab = 0;
+        gf_tune t;
+        if (key == line && sscanf(tab + 1, "%d %d %d %d", &t.block, &t.rays_per_thread, &t.compaction,
+                                  &t.chunk) == 4 && check_tune(&t) == GF_OK) {
+            *out = t;
+            found = true;
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+static void cache_store(const char *path, const std::string &key, const gf_tune &t)
+{
+    if (!path) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s\t%d %d %d %d\n", key.c_str(), t.block, t.rays_per_thread, t.compaction, t.chunk);
+    fclose(f);
+}
+
+extern "C" {
+
+gf_status gf_batch_create(const gf_medium *media, int32_t n_media, const int64_t *offsets, gf_batch *out)
+{
+    if (out == nullptr || media == nullptr || offsets == nullptr || n_media < 1) {
+        set_error("gf_batch_create: need media, n_media >= 1, offsets and out");
+        return GF_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    int kind = -1, nb_max = 0;
+    for (int m = 0; m < n_media; ++m) {
+        if (media[m] == nullptr || device_of(media[m]) != dev) {
+            set_error("gf_batch_create: medium %d is NULL or on another device", m);
+            return GF_ERR_INVALID_ARG;
+        }
+        const MediumParams &p = params_of(media[m]);
+        if (p.kind == K_SPLINE || (kind >= 0 && p.kind != kind)) {
+            set_error("gf_batch_create: media must be isotropic and of one kind (medium %d)", m);
+            return GF_ERR_INVALID_ARG;
+        }
+        if (p.n_blobs > GF_MAX_BATCH_BLOBS) {
+            set_error("gf_batch_create: medium %d has %d blobs > %d", m, p.n_blobs, GF_MAX_BATCH_BLOBS);
+            return GF_ERR_INVALID_ARG;
+        }
+        kind = p.kind;
+        nb_max = std::max(nb_max, (int)p.n_blobs);
+        if (offsets[m] < 0 || offsets[m + 1] < offsets[m]) {
+            set_error("gf_batch_create: offsets must be >= 0 and non-decreasing (at %d)", m);
+            return GF_ERR_INVALID_ARG;
+        }
+    }
+    gf_batch b = new gf_batch_s();
+    b->device = dev;
+    b->kind = kind;
+    b->n_media = n_media;
+    b->nb_max = std::max(nb_max, 1);
+    b->offsets.assign(offsets, offsets + n_media + 1);
+    std::vector<double> base(3 * (size_t)n_media);
+    std::vector<int32_t> nb(n_media);
+    gf_status s = GF_OK;
+    const size_t row = (size_t)b->nb_max * kBlobStride;
+    if ((s = cuda_status(cudaMalloc(&b->d_blobs, row * n_media * sizeof(double)), "cudaMalloc(batch)")) != GF_OK ||
+        (s = cuda_status(cudaMalloc(&b->d_base, base.size() * sizeof(double)), "cudaMalloc(batch)")) != GF_OK ||
+        (s = cuda_status(cudaMalloc(&b->d_nb, nb.size() * sizeof(int32_t)), "cudaMalloc(batch)")) != GF_OK ||
+        (s = cuda_status(cudaMalloc(&b->d_head, sizeof(int)), "cudaMalloc(batch)")) != GF_OK) {
+        batch_free(b);
+        return s;
+    }
+    for (int m = 0; m < n_media; ++m) {
+        const MediumParams &p = params_of(media[m]);
+        base[3 * m] = p.n_h2;
+        base[3 * m + 1] = p.n02;
+        base[3 * m + 2] = p.n02a2;
+        nb[m] = p.n_blobs;
+        if (p.n_blobs > 0 &&
+            (s = cuda_status(cudaMemcpy(b->d_blobs + row * m, medium_device_blobs(media[m]),
+                                        p.n_blobs * kBlobStride * sizeof(double), cudaMemcpyDeviceToDevice),
+                             "cudaMemcpy(batch blobs)")) != GF_OK) {
+            batch_free(b);
+            return s;
+        }
+    }
+    if ((s = cuda_status(cudaMemcpy(b->d_base, base.data(), base.size() * sizeof(double),
+                                    cudaMemcpyHostToDevice), "cudaMemcpy(batch)")) != GF_OK ||
+        (s = cuda_status(cudaMemcpy(b->d_nb, nb.data(), nb.size() * sizeof(int32_t), cudaMemcpyHostToDevice),
+                         "cudaMemcpy(batch)")) != GF_OK) {
+        batch_free(b);
+        return s;
+    }
+    *out = b;
+    return GF_OK;
+}
+
+gf_status gf_batch_destroy(gf_batch b)
+{
+    if (b == nullptr) return GF_OK;
+    cudaDeviceSynchronize();
+    batch_free(b);
+    return GF_OK;
+}
+
+gf_status gf_trace_dopri5(gf_batch b, const gf_rays *rays, int32_t *rejects, double omega,
+                          const gf_step_ctl *ctl, gf_schedule sched, const gf_tune *tune, void *stream)
+{
+    gf_status s;
+    if (b == nullptr) {
+        set_error("gf_trace_dopri5: batch is NULL");
+        return GF_ERR_INVALID_ARG;
+    }
+    if (sched != GF_SCHED_PERSISTENT && sched != GF_SCHED_PER_MEDIUM) {
+        set_error("gf_trace_dopri5: unknown schedule %d", (int)sched);
+        return GF_ERR_INVALID_ARG;
+    }
+    if (!(omega > 0) || !std::isfinite(omega)) {
+        set_error("gf_trace_dopri5: omega must be positive and finite");
+        return GF_ERR_INVALID_ARG;
+    }
+    if ((s = check_ctl(ctl)) != GF_OK) return s;
+    if ((s = check_batch_rays(b, rays, rejects)) != GF_OK) return s;
+    const gf_tune t = tune ? *tune : (b->tuned ? b->tune : kDefaultTune);
+    if ((s = check_tune(&t)) != GF_OK) return s;
+    if (rays->n == 0 || b->offsets.back() == b->offsets.front()) return GF_OK;
+    return run_dopri5(b, rays, rejects, omega, ctl, sched, t, (cudaStream_t)stream, true);
+}
+
+gf_status gf_dopri5_autotune(gf_batch b, const gf_rays *rays, double omega, const gf_step_ctl *ctl,
+                             const char *cache_path, gf_tune *out)
+{
+    gf_status s;
+    if (b == nullptr || out == nullptr) {
+        set_error("gf_dopri5_autotune: batch and out must be non-NULL");
+        return GF_ERR_INVALID_ARG;
+    }
+    if ((s = check_ctl(ctl)) != GF_OK) return s;
+    if ((s = check_batch_rays(b, rays, nullptr)) != GF_OK) return s;
+    const std::string key = tune_key(b, ctl);
+    if (cache_lookup(cache_path, key, out)) {
+        b->tune = *out;
+        b->tuned = true;
+        return GF_OK;
+    }
+    // prefix of media holding ~1/8 of the rays (>= 65,536 when available)
+    const int64_t total = b->offsets.back() - b->offsets.front();
+    const int64_t want = std::max<int64_t>(total / 8, std::min<int64_t>(total, 65536));
+    int m_end = 0;
+    while (m_end < b->n_media && b->offsets[m_end + 1] - b->offsets.front() < want) ++m_end;
+    m_end = std::min(b->n_media, m_end + 1);
+    const int64_t lo = b->offsets.front(), hi = b->offsets[m_end], n = hi - lo;
+    // scratch copies of the sample rays
+    double *y = nullptr, *t = nullptr, *dres = nullptr, *dmax = nullptr;
+    int32_t *st = nullptr, *steps = nullptr;
+    auto release = [&]() {
+        cudaFree(y); cudaFree(t); cudaFree(dres); cudaFree(dmax); cudaFree(st); cudaFree(steps);
+    };
+    if ((s = cuda_status(cudaMalloc(&y, 6 * n * sizeof(double)), "cudaMalloc(tune)")) != GF_OK ||
+        (s = cuda_status(cudaMalloc(&t, n * sizeof(double)), "cudaMalloc(tune)")) != GF_OK ||
+        (s = cuda_status(cudaMalloc(&dres, n * sizeof(double)), "cudaMalloc(tune)")) != GF_OK ||
+        (s = cuda_status(cudaMalloc(&dmax, n * sizeof(double)), "cudaMalloc(tune)")) != GF_OK ||
+        (s = cuda_status(cudaMalloc(&st, n * sizeof(int32_t)), "cudaMalloc(tune)")) != GF_OK ||
+        (s = cuda_status(cudaMalloc(&steps, n * sizeof(int32_t)), "cudaMalloc(tune)")) != GF_OK) {
+        release();
+        return s;
+    }
+    // a sub-batch view over media [0, m_end) with offsets shifted to the scratch rays
+    gf_batch_s sub;
+    sub.device = b->device;
+    sub.kind = b->kind;
+    sub.n_media = m_end;
+    sub.nb_max = b->nb_max;
+    sub.offsets.assign(b->offsets.begin(), b->offsets.begin() + m_end + 1);
+    for (auto &o : sub.offsets) o -= lo;
+    sub.d_blobs = b->d_blobs;
+    sub.d_base = b->d_base;
+    sub.d_nb = b->d_nb;
+    if ((s = cuda_status(cudaMalloc(&sub.d_head, sizeof(int)), "cudaMalloc(tune)")) != GF_OK) {
+        release();
+        return s;
+    }
+    const gf_rays scratch{n, n, y, t, st, steps, dres, dmax};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const double *src_y = (const double *)rays->y;
+    auto reset = [&]() {
+        for (int c = 0; c < 6; ++c)
+            cudaMemcpy(y + c * n, src_y + c * rays->ld + lo, n * sizeof(double), cudaMemcpyDeviceToDevice);
+        cudaMemcpy(t, rays->t + lo, n * sizeof(double), cudaMemcpyDeviceToDevice);
+        cudaMemcpy(st, rays->status + lo, n * sizeof(int32_t), cudaMemcpyDeviceToDevice);
+        cudaMemcpy(steps, rays->steps + lo, n * sizeof(int32_t), cudaMemcpyDeviceToDevice);
+        cudaMemset(dmax, 0, n * sizeof(double));
+    };
+    static const int blocks[] = {64, 128, 256};
+    static const int rpts[] = {1, 2};
+    static const int comps[] = {1, 4, 16};
+    static const int chunks[] = {32, 256};
+    gf_tune best = kDefaultTune;
+    float best_ms = 1e30f;
+    for (int bl : blocks)
+        for (int rp : rpts)
+            for (int cp : comps)
+                for (int ch : chunks) {
+                    gf_tune cand{bl, rp, cp, ch};
+                    if ((size_t)b->nb_max * kBlobStride * sizeof(double) * bl * rp > 200 * 1024) continue;
+                    reset();
+                    cudaEventRecord(e0);
+                    gf_status rs = run_dopri5(&sub, &scratch, nullptr, omega, ctl, GF_SCHED_PERSISTENT,
+                                              cand, nullptr, false);
+                    cudaEventRecord(e1);
+                    cudaError_t se = cudaEventSynchronize(e1);
+                    if (rs != GF_OK || se != cudaSuccess) {
+                        cudaGetLastError();
+                        continue;  // e.g. a shape that does not fit; try the next
+                    }
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        best = cand;
+                    }
+                }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sub.d_head);
+    cudaFree(sub.d_item_medium);
+    cudaFree(sub.d_item_begin);
+    cudaFree(sub.d_item_end);
+    sub.d_blobs = nullptr;
+    sub.d_base = nullptr;
+    sub.d_nb = nullptr;
+    sub.d_head = nullptr;
+    sub.d_item_medium = nullptr;
+    sub.d_item_begin = sub.d_item_end = nullptr;
+    release();
+    if (best_ms >= 1e29f) {
+        set_error("gf_dopri5_autotune: no launch shape ran");
+        return GF_ERR_CUDA;
+    }
+    *out = best;
+    b->tune = best;
+    b->tuned = true;
+    cache_store(cache_path, key, best);
+    return GF_OK;
+}
+
+}  // extern "C"

@@ -15,7 +15,7 @@ namespace gf {
 enum : int { K_HOMOG = GF_MED_HOMOG, K_LUNEBURG = GF_MED_LUNEBURG, K_GRIN = GF_MED_GRIN,
              K_QUADRATIC = GF_MED_QUADRATIC, K_SPLINE = GF_MED_SPLINE };
 
-constexpr int kBlobStride = 5;   // device blob row: A, cx, cy, cz, s = -1 / (2 w^2)
+constexpr int kBlobStride = 6;   // device blob row: A, cx, cy, cz, s = -1 / (2 w^2), 2 s
 
 // Medium as the kernels see it (passed by value as a kernel argument).
 struct MediumParams {
@@ -44,16 +44,70 @@ gf_status cuda_status(cudaError_t e, const char *what);
 gf_status check_rays(const gf_rays *r, bool need_state);
 gf_status check_device_ptr(const void *p, const char *name);
 const MediumParams &params_of(gf_medium m);
+unsigned long long *work_counters();   // device counters set by gf_bench_set_counters, or NULL
 int device_of(gf_medium m);
 
 // Per-translation-unit launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_rk4(const MediumParams &m, gf_precision prec, const gf_rays &r, double omega,
                        double dt, int64_t n_steps, double radius, int64_t every, double *ckpt,
                        cudaStream_t s);
+size_t adjoint_scratch_bytes(int nb, int64_t n, int64_t every);
+cudaError_t launch_adjoint(const MediumParams &m, int64_t n, double omega, double dt, int64_t n_steps,
+                           int64_t every, const double *ckpt, const int32_t *steps_done, const double *lambda,
+                           int64_t ld, double *dtheta, double *dy0, void *scratch, cudaStream_t s);
 cudaError_t launch_onshell(const MediumParams &m, gf_precision prec, const gf_rays &r,
                            const void *dir, double omega, cudaStream_t s);
 
 // ---------------------------------------------------------------- device side
+
+#include "gf_exp_table.inc"
+
+// 2^(j/64), j = 0..63 (one copy per translation unit; staged into shared memory).
+static __constant__ double c_exp2_tab[64] = {
+#define GF_TAB(i) kExp2Tab[i]
+    GF_TAB(0),  GF_TAB(1),  GF_TAB(2),  GF_TAB(3),  GF_TAB(4),  GF_TAB(5),  GF_TAB(6),  GF_TAB(7),
+    GF_TAB(8),  GF_TAB(9),  GF_TAB(10), GF_TAB(11), GF_TAB(12), GF_TAB(13), GF_TAB(14), GF_TAB(15),
+    GF_TAB(16), GF_TAB(17), GF_TAB(18), GF_TAB(19), GF_TAB(20), GF_TAB(21), GF_TAB(22), GF_TAB(23),
+    GF_TAB(24), GF_TAB(25), GF_TAB(26), GF_TAB(27), GF_TAB(28), GF_TAB(29), GF_TAB(30), GF_TAB(31),
+    GF_TAB(32), GF_TAB(33), GF_TAB(34), GF_TAB(35), GF_TAB(36), GF_TAB(37), GF_TAB(38), GF_TAB(39),
+    GF_TAB(40), GF_TAB(41), GF_TAB(42), GF_TAB(43), GF_TAB(44), GF_TAB(45), GF_TAB(46), GF_TAB(47),
+    GF_TAB(48), GF_TAB(49), GF_TAB(50), GF_TAB(51), GF_TAB(52), GF_TAB(53), GF_TAB(54), GF_TAB(55),
+    GF_TAB(56), GF_TAB(57), GF_TAB(58), GF_TAB(59), GF_TAB(60), GF_TAB(61), GF_TAB(62), GF_TAB(63)
+#undef GF_TAB
+};
+
+__device__ __forceinline__ void stage_exp_table(double *sT)
+{
+    for (int j = threadIdx.x; j < 64; j += blockDim.x) sT[j] = c_exp2_tab[j];
+}
+
+// exp(a) for a <= 0 (finite or -inf; a < -708 returns 0, below the smallest
+// normal double), table-driven after Tang (ACM TOMS 1989): with
+// k = round(64 a / ln2), r = a - k ln2/64 (Cody-Waite two-part ln2/64),
+// |r| <= ln2/128, exp(a) = 2^(k >> 6) * 2^((k & 63)/64) * (1 + expm1(r)) and
+// expm1(r) by its degree-5 Taylor polynomial (truncation < r^6/720 < 4e-17).
+// Ten FP64 operations; the rounding to the integer k, the table index and
+// the power-of-two scaling are integer operations on the bit patterns.
+__device__ __forceinline__ double exp_tang(double a, const double *__restrict__ T)
+{
+    const double shifter = 6755399441055744.0;   // 1.5 * 2^52: fma(a, c, shifter) rounds to integer
+    const double t = fma(a, kInvLn2x64, shifter);
+    const int k = __double2loint(t);
+    const double kd = t - shifter;
+    double r = fma(kd, -kLn2By64Hi, a);
+    r = fma(kd, -kLn2By64Lo, r);
+    double p = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+    p = fma(p, r, 1.0 / 6.0);
+    p = fma(p, r, 0.5);
+    p = fma(p, r, 1.0);
+    p = p * r;                                   // expm1(r)
+    const double Tj = T[k & 63];
+    const double v = fma(Tj, p, Tj);
+    const int hi = __double2hiint(v) + ((k >> 6) << 20);
+    const unsigned ahi = (unsigned)__double2hiint(a);
+    // a <= -708 (sign set, |a| >= 708: hi word >= that of -708.0) flushes to 0
+    return ahi >= 0xC0862000u ? 0.0 : __hiloint2double(hi, __double2loint(v));
+}
 
 template <typename R>
 __device__ __forceinline__ R dev_exp(R a);
@@ -77,12 +131,33 @@ __device__ __forceinline__ void stage_blobs(const MediumParams &m, R *sb)
     for (int j = threadIdx.x; j < m.n_blobs * kBlobStride; j += blockDim.x) sb[j] = src[j];
 }
 
+// Blob terms whose exponent s |x - c|^2 is below this are skipped: their
+// contribution A e^{-40.5} < 2.6e-18 |A| to n^2 (and < 3e-17 |A| / w to
+// grad n^2 for the widths in use) is far below the rounding of the sums.
+constexpr double kBlobCull = -40.5;
+
+// Evaluation context: the shared exp table and a live-term counter.
+template <typename R>
+struct EvalCtx {
+    const double *T = nullptr;   // 2^(j/64) table (FP64 path)
+    int live = 0;                // blob terms evaluated (work counter)
+};
+
+template <typename R>
+__device__ __forceinline__ R blob_exp(R a, const EvalCtx<R> &cx);
+template <>
+__device__ __forceinline__ double blob_exp<double>(double a, const EvalCtx<double> &cx) { return exp_tang(a, cx.T); }
+template <>
+__device__ __forceinline__ float blob_exp<float>(float a, const EvalCtx<float> &) { return expf(a); }
+
 // Squared index n^2 and its gradient for an isotropic medium of kind KIND plus
 // the Gaussian blobs in sb:  n^2 += A exp(s q),  grad += 2 s A exp(s q) (x - c),
-// with q = |x - c|^2 and s = -1 / (2 w^2).
+// with q = |x - c|^2 and s = -1 / (2 w^2).  Field f of blob j is read from
+// sb[(kBlobStride * j + f) * stride] (stride 1: a table shared by the block;
+// stride = block size: one table per thread).
 template <typename R, int KIND>
 __device__ __forceinline__ void iso_index(const MediumParams &m, const R *__restrict__ sb, int nb,
-                                          const R *x, R &n2, R *g)
+                                          const R *x, R &n2, R *g, EvalCtx<R> &cx, int stride = 1)
 {
     if constexpr (KIND == K_HOMOG) {
         n2 = (R)m.n_h2;
@@ -111,34 +186,43 @@ __device__ __forceinline__ void iso_index(const MediumParams &m, const R *__rest
         g[1] = (R)-2 * c * x[1];
         g[2] = (R)-2 * c * x[2];
     }
-#pragma unroll 4
+#pragma unroll 2
     for (int j = 0; j < nb; ++j) {
-        const R *b = sb + kBlobStride * j;
-        R dx = x[0] - b[1], dy = x[1] - b[2], dz = x[2] - b[3];
-        R q = dx * dx + dy * dy + dz * dz;
-        R Ae = b[0] * dev_exp<R>(q * b[4]);
-        n2 += Ae;
-        R c = (R)2 * b[4] * Ae;
-        g[0] += c * dx;
-        g[1] += c * dy;
-        g[2] += c * dz;
+        const R *b = sb + kBlobStride * j * stride;
+        const R dx = x[0] - b[stride], dy = x[1] - b[2 * stride], dz = x[2] - b[3 * stride];
+        const R a = (dx * dx + dy * dy + dz * dz) * b[4 * stride];
+        if (a >= (R)kBlobCull) {
+            const R Ae = b[0] * blob_exp<R>(a, cx);
+            n2 += Ae;
+            const R c = b[5 * stride] * Ae;      // 2 s A e
+            g[0] += c * dx;
+            g[1] += c * dy;
+            g[2] += c * dz;
+            ++cx.live;
+        }
     }
 }
 
 // Ray right-hand side for an isotropic medium, D = |k|^2 - w^2 n^2:
 //   f_x = -D_k / D_w = k / (w n^2),  f_k = D_x / D_w = w grad n^2 / (2 n^2).
-// Returns false (cut-off) where n^2 <= 0; D is set either way.
-template <typename R, int KIND>
+// Returns false (cut-off) where n^2 <= 0.  D is computed when WANT_D.
+template <typename R>
+struct Omega {
+    R w, inv_w, half_w;   // w, 1/w, w/2
+};
+
+template <typename R, int KIND, bool WANT_D>
 __device__ __forceinline__ bool rhs_iso(const MediumParams &m, const R *__restrict__ sb, int nb,
-                                        R omega, const R *y, R *f, R &D)
+                                        const Omega<R> &om, const R *y, R *f, R &D, EvalCtx<R> &cx,
+                                        int stride = 1)
 {
     R n2, g[3];
-    iso_index<R, KIND>(m, sb, nb, y, n2, g);
-    D = y[3] * y[3] + y[4] * y[4] + y[5] * y[5] - omega * omega * n2;
+    iso_index<R, KIND>(m, sb, nb, y, n2, g, cx, stride);
+    if constexpr (WANT_D) D = y[3] * y[3] + y[4] * y[4] + y[5] * y[5] - om.w * om.w * n2;
     if (!(n2 > (R)0)) return false;
-    R inv = (R)1 / n2;
-    R a = inv / omega;
-    R b = (R)0.5 * omega * inv;
+    const R inv = (R)1 / n2;
+    const R a = inv * om.inv_w;
+    const R b = om.half_w * inv;
     f[0] = a * y[3];
     f[1] = a * y[4];
     f[2] = a * y[5];
@@ -233,8 +317,9 @@ __device__ __forceinline__ void spline_fields(const MediumParams &m, const R *x,
 //   f_x = -D_k / D_w = M k / (w eps),
 //   f_k =  D_x / D_w = -(k^T dM k - w^2 d eps) / (2 w eps).
 template <typename R>
-__device__ __forceinline__ bool rhs_spline(const MediumParams &m, R omega, const R *y, R *f, R &D)
+__device__ __forceinline__ bool rhs_spline(const MediumParams &m, const Omega<R> &om, const R *y, R *f, R &D)
 {
+    const R omega = om.w;
     R val[7], grad[7][3];
     spline_fields<R>(m, y, val, grad);
     const R *k = y + 3;
@@ -264,14 +349,21 @@ struct Rhs {
     const MediumParams &m;
     const R *sb;
     int nb;
-    R omega;
-    __device__ __forceinline__ bool operator()(const R *y, R *f, R &D) const
+    Omega<R> om;
+    template <bool WANT_D = true>
+    __device__ __forceinline__ bool eval(const R *y, R *f, R &D, EvalCtx<R> &cx) const
     {
         if constexpr (KIND == K_SPLINE)
-            return rhs_spline<R>(m, omega, y, f, D);
+            return rhs_spline<R>(m, om, y, f, D);
         else
-            return rhs_iso<R, KIND>(m, sb, nb, omega, y, f, D);
+            return rhs_iso<R, KIND, WANT_D>(m, sb, nb, om, y, f, D, cx);
     }
 };
+
+template <typename R>
+__host__ __device__ inline Omega<R> make_omega(double w)
+{
+    return Omega<R>{(R)w, (R)(1.0 / w), (R)(0.5 * w)};
+}
 
 }  // namespace gf

@@ -60,72 +60,95 @@ struct Accum<float> {
     }
 };
 
+// Warp-aggregated add of per-thread work counts (evaluations, blob terms).
+__device__ __forceinline__ void add_work(unsigned long long *counters, long long evals, long long terms)
+{
+    if (counters == nullptr) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        evals += __shfl_down_sync(0xffffffffu, evals, o);
+        terms += __shfl_down_sync(0xffffffffu, terms, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(counters, (unsigned long long)evals);
+        atomicAdd(counters + 1, (unsigned long long)terms);
+    }
+}
+
 template <typename R, int KIND>
 __global__ void __launch_bounds__(kRk4Block) rk4_kernel(const MediumParams m, const RaysView<R> r,
-                                                        const R omega, const R dt, const double dt64,
+                                                        const Omega<R> om, const R dt, const double dt64,
                                                         const int64_t n_steps, const R radius2,
-                                                        const int64_t every, double *__restrict__ ckpt)
+                                                        const int64_t every, double *__restrict__ ckpt,
+                                                        unsigned long long *counters)
 {
     __shared__ R sb[kBlobStride * GF_MAX_BLOBS];
+    __shared__ double sT[64];
     if constexpr (KIND != K_SPLINE) stage_blobs<R>(m, sb);
+    stage_exp_table(sT);
     __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= r.n) return;
-    int st = r.status[i];
-    if (st != GF_RAY_ACTIVE) return;
-
-    const Rhs<R, KIND> f{m, sb, m.n_blobs, omega};
+    int st = GF_RAY_DONE;   // lanes without an active ray skip the loop
     R y[6];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) y[c] = r.y[c * r.ld + i];
-    R dm = r.d_max ? (R)r.d_max[i] : (R)0;
-    const R h2 = dt * (R)0.5, h6 = dt / (R)6;
-    Accum<R> acc_state;
+    R dm = (R)0;
+    if (i < r.n) st = r.status[i];
+    EvalCtx<R> cx;
+    cx.T = sT;
+    long long evals = 0;
     int64_t s = 0;
-    for (; s < n_steps; ++s) {
-        if (ckpt != nullptr && s % every == 0) {
-            double *slot = ckpt + (s / every) * 6 * r.n;
+    const Rhs<R, KIND> f{m, sb, m.n_blobs, om};
+    if (st == GF_RAY_ACTIVE) {
 #pragma unroll
-            for (int c = 0; c < 6; ++c) slot[c * r.n + i] = (double)y[c];
+        for (int c = 0; c < 6; ++c) y[c] = r.y[c * r.ld + i];
+        dm = r.d_max ? (R)r.d_max[i] : (R)0;
+        const R h2 = dt * (R)0.5, h6 = dt / (R)6;
+        Accum<R> acc_state;
+        for (; s < n_steps; ++s) {
+            if (ckpt != nullptr && s % every == 0) {
+                double *slot = ckpt + (s / every) * 6 * r.n;
+#pragma unroll
+                for (int c = 0; c < 6; ++c) slot[c * r.n + i] = (double)y[c];
+            }
+            R K[6], acc[6], Y[6], D;
+            evals += 4;
+            bool ok = f.template eval<true>(y, K, D, cx);
+            dm = fmax(dm, fabs(D));
+            if (!ok) { st = GF_RAY_CUTOFF; break; }
+#pragma unroll
+            for (int c = 0; c < 6; ++c) { acc[c] = K[c]; Y[c] = y[c] + h2 * K[c]; }
+            if (!f.template eval<false>(Y, K, D, cx)) { st = GF_RAY_CUTOFF; break; }
+#pragma unroll
+            for (int c = 0; c < 6; ++c) { acc[c] += (R)2 * K[c]; Y[c] = y[c] + h2 * K[c]; }
+            if (!f.template eval<false>(Y, K, D, cx)) { st = GF_RAY_CUTOFF; break; }
+#pragma unroll
+            for (int c = 0; c < 6; ++c) { acc[c] += (R)2 * K[c]; Y[c] = y[c] + dt * K[c]; }
+            if (!f.template eval<false>(Y, K, D, cx)) { st = GF_RAY_CUTOFF; break; }
+            R inc[6], yn[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) inc[c] = h6 * (acc[c] + K[c]);
+            acc_state.add(y, inc, yn);
+            if (!finite6(yn)) { st = GF_RAY_NONFINITE; break; }
+            acc_state.commit(y, yn);
+            if (radius2 > (R)0 && y[0] * y[0] + y[1] * y[1] + y[2] * y[2] > radius2) {
+                st = GF_RAY_EXITED;
+                ++s;
+                break;
+            }
         }
-        R K[6], acc[6], Y[6], D;
-        bool ok = f(y, K, D);
-        dm = fmax(dm, fabs(D));
-        if (!ok) { st = GF_RAY_CUTOFF; break; }
-#pragma unroll
-        for (int c = 0; c < 6; ++c) { acc[c] = K[c]; Y[c] = y[c] + h2 * K[c]; }
-        if (!f(Y, K, D)) { st = GF_RAY_CUTOFF; break; }
-#pragma unroll
-        for (int c = 0; c < 6; ++c) { acc[c] += (R)2 * K[c]; Y[c] = y[c] + h2 * K[c]; }
-        if (!f(Y, K, D)) { st = GF_RAY_CUTOFF; break; }
-#pragma unroll
-        for (int c = 0; c < 6; ++c) { acc[c] += (R)2 * K[c]; Y[c] = y[c] + dt * K[c]; }
-        if (!f(Y, K, D)) { st = GF_RAY_CUTOFF; break; }
-        R inc[6], yn[6];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) inc[c] = h6 * (acc[c] + K[c]);
-        acc_state.add(y, inc, yn);
-        if (!finite6(yn)) { st = GF_RAY_NONFINITE; break; }
-        acc_state.commit(y, yn);
-        if (radius2 > (R)0 && y[0] * y[0] + y[1] * y[1] + y[2] * y[2] > radius2) {
-            st = GF_RAY_EXITED;
-            ++s;
-            break;
-        }
-    }
-    // s = number of steps applied in this call
-    {
+        // s = number of steps applied in this call
         R K[6], D;
-        f(y, K, D);
+        f.template eval<true>(y, K, D, cx);
+        ++evals;
         dm = fmax(dm, fabs(D));
         if (r.d_res) r.d_res[i] = (double)fabs(D);
         if (r.d_max) r.d_max[i] = (double)dm;
-    }
 #pragma unroll
-    for (int c = 0; c < 6; ++c) r.y[c * r.ld + i] = y[c];
-    if (s > 0) r.t[i] = __dadd_rn(r.t[i], __dmul_rn((double)s, dt64));
-    r.steps[i] += (int32_t)s;
-    r.status[i] = st;
+        for (int c = 0; c < 6; ++c) r.y[c * r.ld + i] = y[c];
+        if (s > 0) r.t[i] = __dadd_rn(r.t[i], __dmul_rn((double)s, dt64));
+        r.steps[i] += (int32_t)s;
+        r.status[i] = st;
+    }
+    add_work(counters, evals, cx.live);
 }
 
 // k = s d with D(x, s d, w) = 0, s = w sqrt(eps / q).
@@ -134,7 +157,9 @@ __global__ void __launch_bounds__(kRk4Block) onshell_kernel(const MediumParams m
                                                             const R *__restrict__ dir, const R omega)
 {
     __shared__ R sb[kBlobStride * GF_MAX_BLOBS];
+    __shared__ double sT[64];
     if constexpr (KIND != K_SPLINE) stage_blobs<R>(m, sb);
+    stage_exp_table(sT);
     __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= r.n) return;
@@ -151,7 +176,9 @@ __global__ void __launch_bounds__(kRk4Block) onshell_kernel(const MediumParams m
         q = d[0] * Md0 + d[1] * Md1 + d[2] * Md2;
     } else {
         R g[3];
-        iso_index<R, KIND>(m, sb, m.n_blobs, x, eps, g);
+        EvalCtx<R> cx;
+        cx.T = sT;
+        iso_index<R, KIND>(m, sb, m.n_blobs, x, eps, g, cx);
         q = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     }
     if (!(eps > (R)0) || !(q > (R)0)) {
@@ -159,9 +186,9 @@ __global__ void __launch_bounds__(kRk4Block) onshell_kernel(const MediumParams m
         for (int c = 0; c < 3; ++c) r.y[(3 + c) * r.ld + i] = (R)0;
         return;
     }
-    R s = omega * sqrt(eps / q);
+    R sc = omega * sqrt(eps / q);
     r.status[i] = GF_RAY_ACTIVE;
-    for (int c = 0; c < 3; ++c) r.y[(3 + c) * r.ld + i] = s * d[c];
+    for (int c = 0; c < 3; ++c) r.y[(3 + c) * r.ld + i] = sc * d[c];
 }
 
 template <typename R>
@@ -177,8 +204,8 @@ static cudaError_t rk4_launch(const MediumParams &m, const gf_rays &r, double om
 {
     const int64_t blocks = (r.n + kRk4Block - 1) / kRk4Block;
     const R r2 = radius > 0 ? (R)(radius * radius) : (R)0;
-    rk4_kernel<R, KIND><<<(unsigned)blocks, kRk4Block, 0, s>>>(m, view<R>(r), (R)omega, (R)dt, dt,
-                                                               n_steps, r2, every, ckpt);
+    rk4_kernel<R, KIND><<<(unsigned)blocks, kRk4Block, 0, s>>>(m, view<R>(r), make_omega<R>(omega), (R)dt,
+                                                               dt, n_steps, r2, every, ckpt, work_counters());
     return cudaGetLastError();
 }
 

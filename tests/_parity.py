@@ -55,20 +55,22 @@ def gpu_rk4(spec, x0, k0, omega, dt, n_steps, radius=0.0, dtype=torch.float64, s
     return res
 
 
-def conditioning_mask(spec, x0, k0, omega, dt, n_steps, ref_y, floor=1e-10):
+def conditioning_mask(spec, x0, k0, omega, dt, n_steps, ref_y, floor=1e-10, rel_perturb=None):
     """Rays whose oracle result moves by more than `floor` when the launch point
-    is perturbed by one ulp: ill-conditioned, excluded from the 1e-9 gate."""
-    x1 = np.nextafter(x0, np.inf)
+    is perturbed by one ulp (FP64: nextafter; FP32 scale: rel_perturb = 2^-23):
+    ill-conditioned at that precision, excluded from the gate and counted."""
+    x1 = np.nextafter(x0, np.inf) if rel_perturb is None else x0 * (1 + rel_perturb)
     r, _ = oracle_rk4(spec, x1, k0, omega, dt, n_steps)
     return rel_err(r.y, ref_y) > floor
 
 
-def assert_parity(g: GpuResult, o: O.Rays, tol: float, cond_mask=None, diag_atol=1e-12):
+def assert_parity(g: GpuResult, o: O.Rays, tol: float, cond_mask=None, diag_atol=1e-12,
+                  min_keep=0.99):
     assert np.array_equal(g.status, o.status), (np.bincount(g.status), np.bincount(o.status))
     assert np.array_equal(g.steps, o.steps)
     e = rel_err(g.y, o.y)
     keep = np.ones(len(e), bool) if cond_mask is None else ~cond_mask
-    assert keep.sum() >= 0.99 * len(e), f"{(~keep).sum()} ill-conditioned rays"
+    assert keep.sum() >= min_keep * len(e), f"{(~keep).sum()} ill-conditioned rays"
     worst = e[keep].max() if keep.any() else 0.0
     assert worst <= tol, f"max rel err {worst:.3e} > {tol:.1e} (ray {np.argmax(np.where(keep, e, 0))})"
     np.testing.assert_allclose(g.t, o.t, rtol=1e-15, atol=0)
