@@ -142,17 +142,22 @@ def run_reference(a):
 
 # --------------------------------------------------------------------------- GPU leg
 
-# Algorithmic FP64 cost of one RK4 ray-step on the GRIN + 16 blob medium; the
-# derivation is in the design doc (flops: add/mul 1, fma 2; exp and 1/x counted
-# separately, not as flops).
-FLOPS_PER_EVAL_BASE = 7 + 8 + 8 + 24
-FLOPS_PER_BLOB = 19
-EVALS_PER_STEP = 4
-FLOPS_PER_STEP_EXTRA = 18
+# Algorithmic FP64 flops (add/mul 1, fma 2) of the fused RK4 kernel, per unit
+# of work; units are counted exactly by an untimed pass with work counters.
+#   live blob term  36: x - c (3), |x - c|^2 (5), exponent (1), table exp (18:
+#                       reduction 7, degree-5 polynomial 9, table fma 2),
+#                       A e, n^2 +=, 2 s A e (3), grad += (6)
+#   culled term      9: x - c, |x - c|^2 and the exponent, then skipped
+#   evaluation      51: GRIN base n^2 and gradient (8), 1/n^2 as 8, the two
+#                       prefactors (2), f (6), stage update and RK4 accumulate (24),
+#                       D at one evaluation in four (5/4 rounded up to 3)
+#   ray-step        18: final y + dt/6 (...) update
+FLOPS_LIVE_TERM, FLOPS_CULLED_TERM, FLOPS_EVAL, FLOPS_STEP = 36, 9, 51, 18
 
 
-def flops_per_ray_step(n_blobs: int) -> int:
-    return EVALS_PER_STEP * (FLOPS_PER_EVAL_BASE + FLOPS_PER_BLOB * n_blobs) + FLOPS_PER_STEP_EXTRA
+def algorithmic_flops(evals: int, live: int, n_blobs: int, ray_steps: int) -> int:
+    culled = evals * n_blobs - live
+    return FLOPS_LIVE_TERM * live + FLOPS_CULLED_TERM * culled + FLOPS_EVAL * evals + FLOPS_STEP * ray_steps
 
 
 def run_gpu(a):
@@ -257,10 +262,17 @@ def run_gpu(a):
         e2e = {"value": world * units * a.steps / te.item(), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    # exact work of one trace launch (untimed pass with counters)
+    counters = torch.zeros(2, dtype=torch.int64, device="cuda")
+    gf.gf_bench_set_counters(counters)
+    step()
+    torch.cuda.synchronize()
+    gf.gf_bench_set_counters(None)
+    evals, live = (int(v) for v in counters.tolist())
     n_blobs = wl.medium["blobs"].shape[0]
-    fl_step = flops_per_ray_step(n_blobs)
+    flops = algorithmic_flops(evals, live, n_blobs, units)
     k_sec = statistics.mean(kern_ms) / 1e3
-    achieved = fl_step * units / k_sec / 1e12
+    achieved = flops / k_sec / 1e12
     sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
     # FP64 non-tensor peak from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flops
     peak = SMS * 2 * 2 * sm_mhz * 1e6 / 1e12 if dtype == torch.float64 else SMS * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -275,7 +287,8 @@ def run_gpu(a):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "rk4_kernel<double, GRIN>", "kernel_ms": 1e3 * k_sec,
-                     "flops_per_ray_step": fl_step,
+                     "flops_per_launch": flops, "evaluations": evals, "blob_terms_live": live,
+                     "blob_terms_total": evals * n_blobs,
                      "peak_basis": f"152 SM x 2 DFMA/clk x 2 flop x {sm_mhz:.0f} MHz (sampled)",
                      "fma_peak_measured_tflops": {"f64": peak64, "f32": peak32}},
         "clocks": clk, "gpu_launches": 2 * a.steps, "e2e": e2e, "wall_s": wall,

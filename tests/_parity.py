@@ -74,6 +74,6 @@ def assert_parity(g: GpuResult, o: O.Rays, tol: float, cond_mask=None, diag_atol
     worst = e[keep].max() if keep.any() else 0.0
     assert worst <= tol, f"max rel err {worst:.3e} > {tol:.1e} (ray {np.argmax(np.where(keep, e, 0))})"
     np.testing.assert_allclose(g.t, o.t, rtol=1e-15, atol=0)
-    np.testing.assert_allclose(g.dres, o.dres, rtol=0, atol=diag_atol)
-    np.testing.assert_allclose(g.dmax, o.dmax, rtol=0, atol=diag_atol)
+    np.testing.assert_allclose(g.dres, o.dres, rtol=1e-9, atol=diag_atol)
+    np.testing.assert_allclose(g.dmax, o.dmax, rtol=1e-9, atol=diag_atol)
     return worst
