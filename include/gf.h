@@ -220,6 +220,34 @@ gf_status gf_trace_adjoint(gf_medium m, int64_t n, double omega, double dt, int6
                            const double *lambda, int64_t ld, double *dL_dtheta, double *dL_dy0,
                            void *scratch, size_t scratch_bytes, void *stream);
 
+/*
+ * gf_trace_adjoint_static -- gf_trace_adjoint without a scratch argument and
+ * without any device allocation, for callers that cannot allocate device
+ * memory once they are running: for example a real-time experiment-control
+ * loop that needs gradients between shots, where cudaMalloc and cudaFree can
+ * block or implicitly synchronise the whole device and break the loop's
+ * timing, or a host code whose device memory is reserved up front by its own
+ * pool.  The paper has no counterpart; this is a deployment variant.
+ * Same arguments, layouts, result and errors as gf_trace_adjoint (identical
+ * kernels, so identical results), except that the scratch is a fixed 64 MiB
+ * device array inside the library: calls needing more than
+ * gf_adjoint_scratch_bytes(m, n, checkpoint_every) <= 64 MiB (about 440 rays
+ * with 64 blobs and checkpoints every 64 steps, 1,750 with checkpoints every
+ * 16) fail with GF_ERR_INVALID_ARG before anything is enqueued.  The array is
+ * held by every GPU on which the library's adjoint module is loaded, until
+ * the process exits.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls share the one array: calls whose work overlaps
+ * on the GPU (different streams, or different threads on the same device)
+ * race on it and must be serialised by the caller.  Nothing in the array
+ * needs to start at zero: every word a call reads is written earlier in the
+ * same call.
+ */
+gf_status gf_trace_adjoint_static(gf_medium m, int64_t n, double omega, double dt, int64_t n_steps,
+                                  int64_t checkpoint_every, const double *ckpt, const int32_t *steps_done,
+                                  const double *lambda, int64_t ld, double *dL_dtheta, double *dL_dy0,
+                                  void *stream);
+
 /* ------------------------------------------------------------ batched DOPRI5 */
 
 /* A batch of media whose rays are stored contiguously per medium. */

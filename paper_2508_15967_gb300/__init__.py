@@ -87,6 +87,7 @@ def lib() -> C.CDLL:
             "gf_bench_exp": ([P, P, P, I64, P], I32),
             "gf_adjoint_scratch_bytes": ([P, I64, I64], C.c_size_t),
             "gf_trace_adjoint": ([P, I64, D, D, I64, I64, P, P, P, I64, P, P, P, C.c_size_t, P], I32),
+            "gf_trace_adjoint_static": ([P, I64, D, D, I64, I64, P, P, P, I64, P, P, P], I32),
             "gf_batch_create": ([P, I32, P, P], I32),
             "gf_batch_destroy": ([P], I32),
             "gf_trace_dopri5": ([P, P, P, D, P, I32, P, P], I32),
@@ -255,6 +256,18 @@ def gf_trace_adjoint(m: Medium, n: int, omega: float, dt: float, n_steps: int, c
         m.handle, n, omega, dt, int(n_steps), int(checkpoint_every), _ptr(ckpt), _ptr(steps_done),
         _ptr(lam), lam.stride(0), _ptr(dtheta), _ptr(dy0), _ptr(scratch), scratch.numel(),
         _stream(stream)))
+
+
+def gf_trace_adjoint_static(m: Medium, n: int, omega: float, dt: float, n_steps: int,
+                            checkpoint_every: int, ckpt: torch.Tensor, steps_done: torch.Tensor,
+                            lam: torch.Tensor, dtheta: torch.Tensor, dy0: torch.Tensor | None = None,
+                            stream=None) -> None:
+    """gf_trace_adjoint with the library's fixed 64 MiB scratch: no device allocation (see gf.h)."""
+    if lam.stride(1) != 1 or (dy0 is not None and dy0.stride(0) != lam.stride(0)):
+        raise ValueError("lam and dy0 must be (6, ld) with unit inner stride and the same ld")
+    _check("gf_trace_adjoint_static", lib().gf_trace_adjoint_static(
+        m.handle, n, omega, dt, int(n_steps), int(checkpoint_every), _ptr(ckpt), _ptr(steps_done),
+        _ptr(lam), lam.stride(0), _ptr(dtheta), _ptr(dy0), _stream(stream)))
 
 
 class TraceRK4(torch.autograd.Function):

@@ -21,6 +21,7 @@
 // re-evaluating any exponential.  Per-thread thetabar columns live in shared
 // memory and are reduced block -> grid in a fixed order (deterministic).
 #include <cmath>
+#include <mutex>
 
 #include "gf_internal.cuh"
 
@@ -260,3 +261,97 @@ cudaError_t launch_adjoint(const MediumParams &m, int64_t n, double omega, doubl
 }
 
 }  // namespace gf
+
+// ------------------------------------------------ allocation-free entry point
+
+namespace gf {
+
+// Fixed scratch of gf_trace_adjoint_static.  It is part of this file's device
+// module, so every GPU on which the module is loaded holds it until the
+// process exits.
+constexpr size_t kStaticAdjointScratchBytes = (size_t)64 << 20;
+static __device__ __align__(256) unsigned char g_adjoint_scratch[kStaticAdjointScratchBytes];
+
+constexpr int kMaxStaticDevices = 64;
+static std::mutex g_static_mutex;
+static void *g_static_ptr[kMaxStaticDevices] = {};
+
+// Device address of g_adjoint_scratch on the current device, looked up once
+// per device (host code cannot use the symbol itself as a device address).
+static gf_status static_scratch(void **out)
+{
+    int dev = -1;
+    gf_status s = cuda_status(cudaGetDevice(&dev), "cudaGetDevice");
+    if (s != GF_OK) return s;
+    if (dev < 0 || dev >= kMaxStaticDevices) {
+        set_error("gf_trace_adjoint_static: device ordinal %d >= %d", dev, kMaxStaticDevices);
+        return GF_ERR_UNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (g_static_ptr[dev] == nullptr) {
+        void *p = nullptr;
+        if ((s = cuda_status(cudaGetSymbolAddress(&p, g_adjoint_scratch), "cudaGetSymbolAddress")) != GF_OK)
+            return s;
+        g_static_ptr[dev] = p;
+    }
+    *out = g_static_ptr[dev];
+    return GF_OK;
+}
+
+}  // namespace gf
+
+extern "C" gf_status gf_trace_adjoint_static(gf_medium m, int64_t n, double omega, double dt,
+                                             int64_t n_steps, int64_t checkpoint_every,
+                                             const double *ckpt, const int32_t *steps_done,
+                                             const double *lambda, int64_t ld, double *dL_dtheta,
+                                             double *dL_dy0, void *stream)
+{
+    using namespace gf;
+    gf_status s;
+    if (m == nullptr) {
+        set_error("gf_trace_adjoint_static: medium is NULL");
+        return GF_ERR_INVALID_ARG;
+    }
+    int dev = -1;
+    if ((s = cuda_status(cudaGetDevice(&dev), "cudaGetDevice")) != GF_OK) return s;
+    if (dev != device_of(m)) {
+        set_error("gf_trace_adjoint_static: medium lives on device %d, current device is %d", device_of(m), dev);
+        return GF_ERR_INVALID_ARG;
+    }
+    const MediumParams &p = params_of(m);
+    if (p.kind == K_SPLINE || p.n_blobs < 1) {
+        set_error("gf_trace_adjoint_static: needs an isotropic medium with at least one blob");
+        return GF_ERR_INVALID_ARG;
+    }
+    if (n < 0 || ld < n || n_steps < 0 || checkpoint_every < 1 || checkpoint_every > 4096 ||
+        !(omega > 0) || !std::isfinite(omega) || !(dt > 0) || !std::isfinite(dt)) {
+        set_error("gf_trace_adjoint_static: need n >= 0, ld >= n, n_steps >= 0, "
+                  "1 <= checkpoint_every <= 4096, omega > 0, dt > 0");
+        return GF_ERR_INVALID_ARG;
+    }
+    const size_t need = adjoint_scratch_bytes(p.n_blobs, n, checkpoint_every);
+    if (need > kStaticAdjointScratchBytes) {
+        set_error("gf_trace_adjoint_static: %lld rays with %d blobs and checkpoints every %lld steps need "
+                  "%zu bytes of scratch; the fixed array holds %zu (use fewer rays per call, a shorter "
+                  "checkpoint interval, or gf_trace_adjoint)",
+                  (long long)n, p.n_blobs, (long long)checkpoint_every, need, kStaticAdjointScratchBytes);
+        return GF_ERR_INVALID_ARG;
+    }
+    if ((s = check_device_ptr(dL_dtheta, "dL_dtheta")) != GF_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n == 0)
+        return cuda_status(cudaMemsetAsync(dL_dtheta, 0, sizeof(double) * p.n_blobs, st),
+                           "gf_trace_adjoint_static memset");
+    if ((s = check_device_ptr(ckpt, "ckpt")) != GF_OK || (s = check_device_ptr(steps_done, "steps_done")) != GF_OK ||
+        (s = check_device_ptr(lambda, "lambda")) != GF_OK)
+        return s;
+    if (dL_dy0 && (s = check_device_ptr(dL_dy0, "dL_dy0")) != GF_OK) return s;
+    void *scratch = nullptr;
+    if ((s = static_scratch(&scratch)) != GF_OK) return s;
+    // every scratch word the kernels read is written earlier in the same call
+    // (block partials, then the stage values of each segment), so nothing
+    // needs clearing between calls
+    return cuda_status(launch_adjoint(p, n, omega, dt, n_steps, checkpoint_every, ckpt, steps_done, lambda, ld,
+                                      dL_dtheta, dL_dy0, scratch, st),
+                       "gf_trace_adjoint_static launch");
+}
