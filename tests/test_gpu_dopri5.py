@@ -89,7 +89,9 @@ def _compare_fixed_time(g, o, om, off, x0, k0, ctl, t_end):
     assert (g["t"] == t_end).all()
     ref = _oracle(om, off, x0, k0, dict(ctl, **TIGHT))
     _as_accurate(rel_err(g["y"], ref.y), rel_err(o.y, ref.y))
-    np.testing.assert_allclose(g["dmax"], o.dmax, atol=1e-9)
+    # max |D| along an adaptive trace measures that trace's own integration
+    # error: same magnitude on both sides, not the same value
+    _as_accurate(g["dmax"], o.dmax)
 
 
 def _err_at_own_time(y, t, rows, om, off, x0, k0, ctl):
