@@ -50,6 +50,8 @@ def parse():
                     help="rays of the oracle sample (x the full step count)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched-DOPRI5 and adjoint measurements")
     return ap.parse_args()
 
 
@@ -158,6 +160,101 @@ FLOPS_LIVE_TERM, FLOPS_CULLED_TERM, FLOPS_EVAL, FLOPS_STEP = 36, 9, 51, 18
 def algorithmic_flops(evals: int, live: int, n_blobs: int, ray_steps: int) -> int:
     culled = evals * n_blobs - live
     return FLOPS_LIVE_TERM * live + FLOPS_CULLED_TERM * culled + FLOPS_EVAL * evals + FLOPS_STEP * ray_steps
+
+
+def measure_batched(gf, torch, tune_cache: str | None = None) -> dict:
+    """Batched DOPRI5 workload (4096 Luneburg + 8-blob media, ~12.56M rays,
+    rtol = atol = 1e-9, exit at r = 1.5): persistent work-stealing graph launch
+    vs one launch per medium (also a graph), each timed once after a warm-up."""
+    wl = W.batched()
+    blobs, off = wl.extra["blobs"], wl.extra["offsets"]
+    media = [gf.gf_medium_create("luneburg", blobs=blobs[j]) for j in range(len(off) - 1)]
+    batch = gf.gf_batch_create(media, off)
+    init = gf.Rays.from_numpy(wl.x0, None)
+    dirs = torch.from_numpy(np.ascontiguousarray(wl.d.T)).cuda()
+    stream = torch.cuda.current_stream().cuda_stream
+    for j, m in enumerate(media):                      # on-shell k per medium
+        lo, hi = int(off[j]), int(off[j + 1])
+        if hi > lo:
+            s = gf.GfRays(hi - lo, init.y.stride(0), init.y.data_ptr() + 8 * lo, init.t.data_ptr() + 8 * lo,
+                          init.status.data_ptr() + 4 * lo, init.steps.data_ptr() + 4 * lo,
+                          init.d_res.data_ptr() + 8 * lo, init.d_max.data_ptr() + 8 * lo)
+            gf._check("gf_rays_onshell", gf.lib().gf_rays_onshell(m.handle, gf.GF_F64, gf.C.byref(s),
+                                                                  dirs.data_ptr() + 8 * lo, 1.0, stream))
+    e = wl.extra
+    ctl = gf.step_ctl(rtol=e["rtol"], atol=e["atol"], h0=e["h0"], t_max=e["t_max"], radius=wl.radius,
+                      max_steps=e["max_steps"])
+    t0 = time.perf_counter()
+    tune = gf.gf_dopri5_autotune(batch, init, 1.0, ctl, tune_cache)
+    tune_s = time.perf_counter() - t0
+    rays = init.clone()
+    rej = torch.zeros(rays.n, dtype=torch.int32, device="cuda")
+    out = {}
+    for name, sched in (("persistent", gf.GF_SCHED_PERSISTENT), ("per_medium", gf.GF_SCHED_PER_MEDIUM)):
+        ms = []
+        for _ in range(2):                             # warm-up (graph capture), then timed
+            for src, dst in zip((init.y, init.t, init.status, init.steps, init.d_max),
+                                (rays.y, rays.t, rays.status, rays.steps, rays.d_max)):
+                dst.copy_(src)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            gf.gf_trace_dopri5(batch, rays, rej, 1.0, ctl, sched, None)
+            ev1.record()
+            torch.cuda.synchronize()
+            ms.append(ev0.elapsed_time(ev1))
+        steps = int(rays.steps.to(torch.int64).sum().item())
+        out[name] = {"ms": ms[-1], "accepted_ray_steps": steps,
+                     "rejected": int(rej.to(torch.int64).sum().item()),
+                     "ray_steps_per_s": steps / (ms[-1] / 1e3)}
+    return {"workload": f"4096 Luneburg+8-blob media, {wl.n} rays, DOPRI5 rtol=atol=1e-9, exit r=1.5",
+            "persistent": out["persistent"], "per_medium": out["per_medium"],
+            "speedup_persistent_vs_per_medium": out["per_medium"]["ms"] / out["persistent"]["ms"],
+            "tune": {"block": tune.block, "rays_per_thread": tune.rays_per_thread,
+                     "compaction": tune.compaction, "chunk": tune.chunk, "seconds": tune_s}}
+
+
+def measure_adjoint(gf, torch) -> dict:
+    """Adjoint workload (65,536 rays, Luneburg + 64 blobs, RK4 dt 1e-3 x 4000,
+    checkpoints every 64): forward with checkpoints and backward through the
+    autograd Function, plus a plain forward, each timed after a warm-up."""
+    wl = W.adjoint()
+    m = gf.gf_medium_create(**wl.medium)
+    init = gf.Rays.empty(wl.n)
+    init.y[:3].copy_(torch.from_numpy(np.ascontiguousarray(wl.x0.T)).cuda())
+    gf.gf_rays_onshell(m, init, torch.from_numpy(np.ascontiguousarray(wl.d.T)).cuda(), 1.0)
+    y0 = init.y.clone()
+    # targets: the same rays traced with the hidden amplitudes theta*
+    gf.gf_medium_set_amplitudes(m, torch.tensor(wl.extra["theta_star"], device="cuda"))
+    star = gf.Rays.empty(wl.n, diagnostics=False)
+    star.y.copy_(y0)
+    gf.gf_trace_rk4(m, star, 1.0, wl.dt, wl.n_steps)
+    xstar = star.y[:3].clone()
+    theta = torch.tensor(wl.extra["theta"], device="cuda", requires_grad=True)
+    gf.gf_medium_set_amplitudes(m, theta.detach())
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    res = {}
+    for _ in range(2):
+        e0, e1, e2, e3, e4 = ev(), ev(), ev(), ev(), ev()
+        e0.record()
+        plain = gf.Rays.empty(wl.n, diagnostics=False)
+        plain.y.copy_(y0)
+        gf.gf_trace_rk4(m, plain, 1.0, wl.dt, wl.n_steps)
+        e1.record()
+        yN = gf.trace_rk4_autograd(m, theta, y0, 1.0, wl.dt, wl.n_steps, wl.extra["checkpoint_every"])
+        e2.record()
+        loss = ((yN[:3] - xstar) ** 2).sum()
+        e3.record()
+        loss.backward()
+        e4.record()
+        torch.cuda.synchronize()
+        res = {"plain_forward_ms": e0.elapsed_time(e1), "forward_ckpt_ms": e1.elapsed_time(e2),
+               "backward_ms": e3.elapsed_time(e4)}
+        theta.grad = None
+    res["backward_over_forward"] = res["backward_ms"] / res["forward_ckpt_ms"]
+    res["total_over_plain_forward"] = (res["forward_ckpt_ms"] + res["backward_ms"]) / res["plain_forward_ms"]
+    res["loss"] = loss.item()
+    res["workload"] = "65536 rays, Luneburg + 64 blobs, RK4 dt=1e-3 x 4000, checkpoint every 64"
+    return res
 
 
 def run_gpu(a):
@@ -293,6 +390,9 @@ def run_gpu(a):
                      "fma_peak_measured_tflops": {"f64": peak64, "f32": peak32}},
         "clocks": clk, "gpu_launches": 2 * a.steps, "e2e": e2e, "wall_s": wall,
     }
+    if world == 1 and not a.no_extras:
+        line["adjoint"] = measure_adjoint(gf, torch)
+        line["batched"] = measure_batched(gf, torch)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cb = oracle_throughput(W.grin(n=a.cpu_rays, n_steps=a.nsteps), a.cpu_rays)
         cb.pop("seconds")

@@ -160,6 +160,23 @@ gf_status gf_rays_onshell(gf_medium m, gf_precision prec, const gf_rays *rays, c
                           double omega, void *stream);
 
 /*
+ * gf_rays_newton_kx -- the paper's ray initialisation (Sec. 4): with w, x, k_y
+ * and k_z fixed, solve D(x, k, w) = 0 for k_x by Newton's method,
+ * k_x <- k_x - D / (dD/dk_x), to |D| < tol (the paper uses 1e-15); the k_x in
+ * rays->y on entry is the initial guess and selects the root (D is quadratic
+ * in k_x for every medium here, so the guess picks one of two branches).  An
+ * iteration whose step no longer changes k_x beyond rounding (|dk_x| <=
+ * 2^-50 |k_x|) ends the solve, converged if |D| <= 8 tol.  Writes row 3 of y
+ * and status: GF_RAY_ACTIVE when converged, GF_RAY_CUTOFF when no real root
+ * was reached in max_iter iterations (evanescent: k_y, k_z too large) or
+ * dD/dk_x vanished; leaves t, steps, d_res, d_max untouched.
+ * Errors: GF_ERR_INVALID_ARG (tol <= 0, max_iter outside [1, 10000], ...),
+ * GF_ERR_CUDA.
+ */
+gf_status gf_rays_newton_kx(gf_medium m, gf_precision prec, const gf_rays *rays, double omega, double tol,
+                            int32_t max_iter, void *stream);
+
+/*
  * gf_trace_rk4 -- advance every active ray by up to n_steps classic RK4 steps
  * of fixed size dt of the ray equations (Eqs. 2-3), fused into one kernel with
  * the ray state held in registers (Sec. 4: one kernel with inputs x, k, t, w

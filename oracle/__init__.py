@@ -66,6 +66,7 @@ def lib():
         _lib.or_index_hess.argtypes = [P, I64, P, P]
         _lib.or_onshell.argtypes = [P, I64, P, P, D, P, P]
         _lib.or_trace_rk4.argtypes = [P, I64, P, P, P, P, P, P, D, D, I64, D, I64, P]
+        _lib.or_newton_kx.argtypes = [P, I64, P, P, D, D, C.c_int, P, P]
         _lib.or_trace_rk4_kink.argtypes = [P, I64, P, P, P, P, P, P, D, D, I64, D, P]
         _lib.or_trace_dopri5.argtypes = [P, I64, P, P, P, P, P, P, P, P, D, P]
         _lib.or_tangent_rk4.argtypes = [P, I64, P, P, P, P, P, D, D, I64, D]
@@ -133,6 +134,18 @@ def onshell(m: Medium, x0, d, omega: float = 1.0):
     s = m.struct()
     lib().or_onshell(C.byref(s), x0.shape[0], _p(x0), _p(d), omega, _p(k0), _p(st))
     return k0, st
+
+
+def newton_kx(m: Medium, x, k, omega: float = 1.0, tol: float = 1e-15, max_iter: int = 50):
+    """Solve D = 0 for k_x by Newton from the k_x in k (k_y, k_z fixed).
+    Returns (k (n,3), status (n,), iterations (n,))."""
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    k = np.array(k, dtype=np.float64).reshape(-1, 3)
+    st = np.empty(x.shape[0], np.int32)
+    it = np.empty(x.shape[0], np.int32)
+    s = m.struct()
+    lib().or_newton_kx(C.byref(s), x.shape[0], _p(x), _p(k), omega, tol, max_iter, _p(st), _p(it))
+    return k, st, it
 
 
 @dataclass

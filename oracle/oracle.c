@@ -345,6 +345,43 @@ void or_onshell(const or_medium *m, int64_t n, const double *x0, const double *d
     }
 }
 
+/* ------------------------------------------------------ public: Newton k_x */
+
+/* The paper's ray initialisation (Sec. 4): w, x, k_y and k_z are fixed and
+ * k_x solves D(x, k, w) = 0 by Newton's method, k_x <- k_x - D / (dD/dk_x),
+ * to |D| < tol; the initial guess (k_x on entry) selects the root.  An
+ * iteration also stops, converged, when its step no longer changes k_x beyond
+ * rounding (|dk_x| <= 2^-50 |k_x|) with |D| <= 8 tol.  Rays that do not
+ * converge in max_iter steps, or meet dD/dk_x = 0, get OR_CUTOFF (no
+ * propagating root) and keep their last k_x.  k: (n, 3) in/out; iters: (n,). */
+void or_newton_kx(const or_medium *m, int64_t n, const double *x, double *k, double w, double tol,
+                  int max_iter, int32_t *status, int32_t *iters)
+{
+    int64_t r;
+#pragma omp parallel for schedule(static)
+    for (r = 0; r < n; r++) {
+        double *kr = k + 3 * r;
+        int it, ok = 0;
+        for (it = 0; it < max_iter; it++) {
+            or_disp d;
+            double step;
+            or_dispersion(m, x + 3 * r, kr, w, &d);
+            if (fabs(d.D) < tol) { ok = 1; break; }
+            if (d.Dk[0] == 0.0 || !isfinite(d.D)) break;
+            step = d.D / d.Dk[0];
+            kr[0] = kr[0] - step;
+            if (fabs(step) <= 0x1p-50 * fabs(kr[0])) {
+                or_dispersion(m, x + 3 * r, kr, w, &d);
+                ok = fabs(d.D) <= 8.0 * tol;
+                it++;
+                break;
+            }
+        }
+        status[r] = ok ? OR_ACTIVE : OR_CUTOFF;
+        iters[r] = it;
+    }
+}
+
 /* ------------------------------------------------------------ public: RK4 */
 
 /* One ray, classic RK4 with fixed dt for up to n_steps steps (Sec. 4):

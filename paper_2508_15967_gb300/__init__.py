@@ -82,6 +82,7 @@ def lib() -> C.CDLL:
             "gf_medium_set_amplitudes": ([P, P, P], I32),
             "gf_rays_onshell": ([P, I32, P, P, D, P], I32),
             "gf_trace_rk4": ([P, I32, P, D, D, I64, D, I64, P, P], I32),
+            "gf_rays_newton_kx": ([P, I32, P, D, D, I32, P], I32),
             "gf_bench_fma_peak": ([I32, I64, I32, P, P], I32),
             "gf_bench_set_counters": ([P], I32),
             "gf_bench_exp": ([P, P, P, I64, P], I32),
@@ -225,6 +226,14 @@ def gf_rays_onshell(m: Medium, rays: Rays, direction: torch.Tensor, omega: float
     s = rays.struct()
     _check("gf_rays_onshell", lib().gf_rays_onshell(m.handle, rays.precision, C.byref(s),
                                                     _ptr(direction), omega, _stream(stream)))
+
+
+def gf_rays_newton_kx(m: Medium, rays: Rays, omega: float = 1.0, tol: float = 1e-15,
+                      max_iter: int = 50, stream=None) -> None:
+    """Solve D = 0 for k_x by Newton from the k_x in rays.y[3] (k_y, k_z fixed)."""
+    s = rays.struct()
+    _check("gf_rays_newton_kx", lib().gf_rays_newton_kx(m.handle, rays.precision, C.byref(s), omega, tol,
+                                                        max_iter, _stream(stream)))
 
 
 def gf_trace_rk4(m: Medium, rays: Rays, omega: float, dt: float, n_steps: int, radius: float = 0.0,

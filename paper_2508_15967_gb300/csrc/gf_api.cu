@@ -271,6 +271,25 @@ gf_status gf_rays_onshell(gf_medium m, gf_precision prec, const gf_rays *rays, c
                        "gf_rays_onshell launch");
 }
 
+gf_status gf_rays_newton_kx(gf_medium m, gf_precision prec, const gf_rays *rays, double omega, double tol,
+                            int32_t max_iter, void *stream)
+{
+    gf_status s;
+    if ((s = check_medium(m)) != GF_OK) return s;
+    if (prec != GF_F32 && prec != GF_F64) {
+        set_error("gf_rays_newton_kx: unknown precision %d", (int)prec);
+        return GF_ERR_INVALID_ARG;
+    }
+    if (!(omega > 0) || !std::isfinite(omega) || !(tol > 0) || !std::isfinite(tol) || max_iter < 1 ||
+        max_iter > 10000) {
+        set_error("gf_rays_newton_kx: need omega > 0, tol > 0, 1 <= max_iter <= 10000");
+        return GF_ERR_INVALID_ARG;
+    }
+    if ((s = check_rays(rays, false)) != GF_OK) return s;
+    return cuda_status(launch_newton_kx(m->p, prec, *rays, omega, tol, max_iter, (cudaStream_t)stream),
+                       "gf_rays_newton_kx launch");
+}
+
 gf_status gf_trace_rk4(gf_medium m, gf_precision prec, const gf_rays *rays, double omega, double dt,
                        int64_t n_steps, double radius, int64_t checkpoint_every, double *ckpt,
                        void *stream)

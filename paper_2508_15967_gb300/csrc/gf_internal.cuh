@@ -55,6 +55,8 @@ size_t adjoint_scratch_bytes(int nb, int64_t n, int64_t every);
 cudaError_t launch_adjoint(const MediumParams &m, int64_t n, double omega, double dt, int64_t n_steps,
                            int64_t every, const double *ckpt, const int32_t *steps_done, const double *lambda,
                            int64_t ld, double *dtheta, double *dy0, void *scratch, cudaStream_t s);
+cudaError_t launch_newton_kx(const MediumParams &m, gf_precision prec, const gf_rays &r, double omega, double tol,
+                             int max_iter, cudaStream_t s);
 cudaError_t launch_onshell(const MediumParams &m, gf_precision prec, const gf_rays &r,
                            const void *dir, double omega, cudaStream_t s);
 
@@ -135,13 +137,28 @@ __device__ __forceinline__ void stage_blobs(const MediumParams &m, R *sb)
 // contribution A e^{-40.5} < 2.6e-18 |A| to n^2 (and < 3e-17 |A| / w to
 // grad n^2 for the widths in use) is far below the rounding of the sums.
 constexpr double kBlobCull = -40.5;
+// FP32 pre-test for the FP64 path: a term whose exponent, computed in FP32
+// from rounded x, c and s, is below -41 has an exact exponent below -40.5
+// (the FP32 error is < 1e-3 for |s| <= 200 and |x - c| < 4), so it is skipped
+// before any FP64 work; the FP64 test then decides the remaining terms
+// exactly as without the pre-test.
+constexpr float kBlobCullF = -41.0f;
 
-// Evaluation context: the shared exp table and a live-term counter.
+// Evaluation context: the shared exp table, the FP32 copy of the blob
+// centres and exponent factors (cx, cy, cz, s per blob; FP64 path with a
+// block-shared table only), and a live-term counter.
 template <typename R>
 struct EvalCtx {
     const double *T = nullptr;   // 2^(j/64) table (FP64 path)
+    const float *pre = nullptr;  // FP32 pre-test table, 4 floats per blob, or NULL
     int live = 0;                // blob terms evaluated (work counter)
 };
+
+// Stage the FP32 pre-test table (cx, cy, cz, s) from the float blob rows.
+__device__ __forceinline__ void stage_pretest(const MediumParams &m, float *sp)
+{
+    for (int j = threadIdx.x; j < m.n_blobs * 4; j += blockDim.x) sp[j] = m.blobs32[(j >> 2) * kBlobStride + 1 + (j & 3)];
+}
 
 template <typename R>
 __device__ __forceinline__ R blob_exp(R a, const EvalCtx<R> &cx);
@@ -186,8 +203,19 @@ __device__ __forceinline__ void iso_index(const MediumParams &m, const R *__rest
         g[1] = (R)-2 * c * x[1];
         g[2] = (R)-2 * c * x[2];
     }
+    float xf0 = 0.f, xf1 = 0.f, xf2 = 0.f;
+    if (cx.pre != nullptr) {
+        xf0 = (float)x[0];
+        xf1 = (float)x[1];
+        xf2 = (float)x[2];
+    }
 #pragma unroll 2
     for (int j = 0; j < nb; ++j) {
+        if (cx.pre != nullptr) {
+            const float *bp = cx.pre + 4 * j;
+            const float ex = xf0 - bp[0], ey = xf1 - bp[1], ez = xf2 - bp[2];
+            if ((ex * ex + ey * ey + ez * ez) * bp[3] < kBlobCullF) continue;
+        }
         const R *b = sb + kBlobStride * j * stride;
         const R dx = x[0] - b[stride], dy = x[1] - b[2 * stride], dz = x[2] - b[3 * stride];
         const R a = (dx * dx + dy * dy + dz * dz) * b[4 * stride];

@@ -76,7 +76,7 @@ __device__ __forceinline__ void add_work(unsigned long long *counters, long long
 }
 
 template <typename R, int KIND>
-__global__ void __launch_bounds__(kRk4Block) rk4_kernel(const MediumParams m, const RaysView<R> r,
+__global__ void __launch_bounds__(kRk4Block, (KIND == K_SPLINE || sizeof(R) == 4) ? 1 : 5) rk4_kernel(const MediumParams m, const RaysView<R> r,
                                                         const Omega<R> om, const R dt, const double dt64,
                                                         const int64_t n_steps, const R radius2,
                                                         const int64_t every, double *__restrict__ ckpt,
@@ -84,7 +84,10 @@ __global__ void __launch_bounds__(kRk4Block) rk4_kernel(const MediumParams m, co
 {
     __shared__ R sb[kBlobStride * GF_MAX_BLOBS];
     __shared__ double sT[64];
+    __shared__ float sp[4 * GF_MAX_BLOBS];
     if constexpr (KIND != K_SPLINE) stage_blobs<R>(m, sb);
+    constexpr bool kPretest = sizeof(R) == 8 && KIND != K_SPLINE;
+    if constexpr (kPretest) stage_pretest(m, sp);
     stage_exp_table(sT);
     __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -94,6 +97,7 @@ __global__ void __launch_bounds__(kRk4Block) rk4_kernel(const MediumParams m, co
     if (i < r.n) st = r.status[i];
     EvalCtx<R> cx;
     cx.T = sT;
+    if constexpr (kPretest) cx.pre = sp;
     long long evals = 0;
     int64_t s = 0;
     const Rhs<R, KIND> f{m, sb, m.n_blobs, om};
@@ -191,6 +195,59 @@ __global__ void __launch_bounds__(kRk4Block) onshell_kernel(const MediumParams m
     for (int c = 0; c < 3; ++c) r.y[(3 + c) * r.ld + i] = sc * d[c];
 }
 
+// The paper's ray initialisation (Sec. 4): w, x, k_y, k_z fixed, k_x from
+// Newton on D = 0 to |D| < tol, starting from the k_x held in the rays; the
+// medium (n^2, or M and eps) is evaluated once at x, after which D is a
+// quadratic in k_x and every iteration is a few scalar operations.
+template <typename R, int KIND>
+__global__ void __launch_bounds__(kRk4Block) newton_kx_kernel(const MediumParams m, const RaysView<R> r,
+                                                              const R omega, const R tol, const int max_iter)
+{
+    __shared__ R sb[kBlobStride * GF_MAX_BLOBS];
+    __shared__ double sT[64];
+    if constexpr (KIND != K_SPLINE) stage_blobs<R>(m, sb);
+    stage_exp_table(sT);
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= r.n) return;
+    const R x[3] = {r.y[i], r.y[r.ld + i], r.y[2 * r.ld + i]};
+    R kx = r.y[3 * r.ld + i];
+    const R ky = r.y[4 * r.ld + i], kz = r.y[5 * r.ld + i];
+    // D(k_x) = a k_x^2 + 2 b k_x + c  with  dD/dk_x = 2 (a k_x + b)
+    R a, b, c;
+    if constexpr (KIND == K_SPLINE) {
+        R val[7], grad[7][3];
+        spline_fields<R>(m, x, val, grad);
+        a = val[0];
+        b = val[1] * ky + val[2] * kz;
+        c = val[3] * ky * ky + (R)2 * val[4] * ky * kz + val[5] * kz * kz - omega * omega * val[6];
+    } else {
+        R n2, g[3];
+        EvalCtx<R> cx;
+        cx.T = sT;
+        iso_index<R, KIND>(m, sb, m.n_blobs, x, n2, g, cx);
+        a = (R)1;
+        b = (R)0;
+        c = ky * ky + kz * kz - omega * omega * n2;
+    }
+    bool ok = false;
+    for (int it = 0; it < max_iter; ++it) {
+        const R D = (a * kx + (R)2 * b) * kx + c;
+        if (fabs(D) < tol) { ok = true; break; }
+        const R Dk = (R)2 * (a * kx + b);
+        if (Dk == (R)0 || !isfinite(D)) break;
+        const R step = D / Dk;
+        kx = kx - step;
+        if (fabs(step) <= (R)0x1p-50 * fabs(kx)) {
+            const R D2 = (a * kx + (R)2 * b) * kx + c;
+            ok = fabs(D2) <= (R)8 * tol;
+            break;
+        }
+    }
+    r.y[3 * r.ld + i] = kx;
+    r.status[i] = ok ? GF_RAY_ACTIVE : GF_RAY_CUTOFF;
+}
+
 template <typename R>
 static RaysView<R> view(const gf_rays &r)
 {
@@ -237,6 +294,26 @@ cudaError_t launch_rk4(const MediumParams &m, gf_precision prec, const gf_rays &
         GF_KIND_SWITCH(m.kind, rk4_launch, double, m, r, omega, dt, n_steps, radius, every, ckpt, s)
     } else {
         GF_KIND_SWITCH(m.kind, rk4_launch, float, m, r, omega, dt, n_steps, radius, every, ckpt, s)
+    }
+}
+
+template <typename R, int KIND>
+static cudaError_t newton_launch(const MediumParams &m, const gf_rays &r, double omega, double tol, int max_iter,
+                                 cudaStream_t s)
+{
+    const int64_t blocks = (r.n + kRk4Block - 1) / kRk4Block;
+    newton_kx_kernel<R, KIND><<<(unsigned)blocks, kRk4Block, 0, s>>>(m, view<R>(r), (R)omega, (R)tol, max_iter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_newton_kx(const MediumParams &m, gf_precision prec, const gf_rays &r, double omega, double tol,
+                             int max_iter, cudaStream_t s)
+{
+    if (r.n == 0) return cudaSuccess;
+    if (prec == GF_F64) {
+        GF_KIND_SWITCH(m.kind, newton_launch, double, m, r, omega, tol, max_iter, s)
+    } else {
+        GF_KIND_SWITCH(m.kind, newton_launch, float, m, r, omega, tol, max_iter, s)
     }
 }
 

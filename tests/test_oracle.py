@@ -611,3 +611,53 @@ def test_loss_gradient_matches_loss_differences():
         bm[j, 0] -= h
         fd = (loss(bp) - loss(bm)) / (2 * h)
         assert abs(g[j] - fd) < 1e-6 * max(1.0, abs(fd))
+
+
+# ---------------------------------------------------------------- Newton k_x
+
+def test_newton_kx_finds_the_closed_form_roots():
+    """Isotropic: k_x = +-sqrt(w^2 n^2 - k_y^2 - k_z^2), the sign of the guess
+    picks the branch; |D| below the paper's 1e-15 (Sec. 4) or at rounding."""
+    m = O.medium(kind="grin", n0=1.5, a=2.0, blobs=W.blob_table(np.random.default_rng(7), 4, 0.01))
+    rng = np.random.default_rng(8)
+    x = rng.uniform(-0.2, 0.2, (40, 3))
+    kyz = rng.uniform(-0.5, 0.5, (40, 2))
+    n2 = O.eval_dispersion(m, x, np.zeros((40, 3)), 1.3)[:, 8]
+    exact = np.sqrt(1.3 ** 2 * n2 - (kyz ** 2).sum(1))
+    for sign in (1.0, -1.0):
+        k = np.column_stack([sign * np.full(40, 0.7), kyz])
+        kk, st, it = O.newton_kx(m, x, k, 1.3)
+        assert (st == O.ACTIVE).all() and (it < 12).all()
+        np.testing.assert_allclose(kk[:, 0], sign * exact, rtol=1e-15)
+        np.testing.assert_array_equal(kk[:, 1:], kyz)
+        assert np.abs(O.eval_dispersion(m, x, kk, 1.3)[:, 0]).max() <= 8e-15
+
+
+def test_newton_kx_spline_quadratic_roots_and_no_root():
+    """Spline medium: D is quadratic in k_x, M11 k_x^2 + 2 b k_x + c = 0 with
+    b = M12 k_y + M13 k_z, c = M22 k_y^2 + 2 M23 k_y k_z + M33 k_z^2 - w^2 eps;
+    rays with k_y, k_z too large have no real root and get the cut-off status."""
+    grid = W.aniso_grid(np.random.default_rng(9), g=16, n_modes=6)
+    m = O.medium(kind="spline", grid=grid)
+    rng = np.random.default_rng(10)
+    x = rng.uniform(-1, 1, (30, 3))
+    kyz = rng.uniform(-0.3, 0.3, (30, 2))
+    ev = O.eval_dispersion(m, x, np.column_stack([np.ones(30), np.zeros((30, 2))]), 1.0)
+    # D(k_x = 1, 0, 0) = M11 - eps and D_k = 2 M e_x give M11, M12, M13; probe the rest
+    M = np.empty((30, 3, 3))
+    for c in range(3):
+        e = np.zeros((30, 3))
+        e[:, c] = 1.0
+        M[:, :, c] = O.eval_dispersion(m, x, e, 1.0)[:, 4:7] / 2
+    eps = ev[:, 8]
+    b = M[:, 0, 1] * kyz[:, 0] + M[:, 0, 2] * kyz[:, 1]
+    c = (M[:, 1, 1] * kyz[:, 0] ** 2 + 2 * M[:, 1, 2] * kyz[:, 0] * kyz[:, 1]
+         + M[:, 2, 2] * kyz[:, 1] ** 2 - eps)
+    disc = np.sqrt(b * b - M[:, 0, 0] * c)
+    roots = {1.0: (-b + disc) / M[:, 0, 0], -1.0: (-b - disc) / M[:, 0, 0]}
+    for sign in (1.0, -1.0):
+        kk, st, _ = O.newton_kx(m, x, np.column_stack([np.full(30, 3 * sign), kyz]))
+        assert (st == O.ACTIVE).all()
+        np.testing.assert_allclose(kk[:, 0], roots[sign], rtol=1e-13, atol=1e-15)
+    kk, st, it = O.newton_kx(m, x[:3], np.column_stack([np.ones(3), np.full((3, 2), 3.0)]), max_iter=60)
+    assert (st == O.CUTOFF).all()
