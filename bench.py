@@ -156,6 +156,12 @@ def run_reference(a):
 #   ray-step        18: final y + dt/6 (...) update
 FLOPS_LIVE_TERM, FLOPS_CULLED_TERM, FLOPS_EVAL, FLOPS_STEP = 36, 9, 51, 18
 
+# DRAM bytes (read + write) of one rk4_kernel<double, GRIN> launch over
+# 1,048,576 rays, from an ncu capture of the same launch shape (the kernel
+# loads and stores the ray state once, so the count does not depend on the
+# number of steps).  Valid only for the FP64 GRIN kernel as captured.
+TRAFFIC_BYTES_1M = 75_638_528 + 23_869_184
+
 
 def algorithmic_flops(evals: int, live: int, n_blobs: int, ray_steps: int) -> int:
     culled = evals * n_blobs - live
@@ -382,7 +388,8 @@ def run_gpu(a):
                    "rays_per_gpu": wl.n, "rk4_steps": wl.n_steps, "parallelism": f"ray shards x{world}",
                    "l2": "256 MiB buffer written between timed steps"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": TRAFFIC_BYTES_1M if (wl.n == 1 << 20 and dtype == torch.float64) else None,
                      "kernel": "rk4_kernel<double, GRIN>", "kernel_ms": 1e3 * k_sec,
                      "flops_per_launch": flops, "evaluations": evals, "blob_terms_live": live,
                      "blob_terms_total": evals * n_blobs,
