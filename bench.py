@@ -45,7 +45,9 @@ def parse():
     ap.add_argument("--impl", choices=["gf", "reference"], default="gf")
     ap.add_argument("--rays", type=int, default=1 << 20)
     ap.add_argument("--nsteps", type=int, default=10000)
-    ap.add_argument("--precision", choices=["f64", "f32"], default="f64")
+    ap.add_argument("--precision", choices=["f64", "f32", "f64x"], default="f64",
+                    help="f64: IEEE double throughout (the headline); f32; f64x: double state and "
+                         "integrator with double-float blob sums")
     ap.add_argument("--cpu-rays", type=int, default=4096,
                     help="rays of the oracle sample (x the full step count)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -279,7 +281,8 @@ def run_gpu(a):
         if world > 1:
             dist.barrier()
 
-    dtype = torch.float64 if a.precision == "f64" else torch.float32
+    dtype = torch.float32 if a.precision == "f32" else torch.float64
+    prec = {"f64": gf.GF_F64, "f32": gf.GF_F32, "f64x": gf.GF_F64X}[a.precision]
     wl = W.grin(n=a.rays, n_steps=a.nsteps, shard=rank)
     m = gf.gf_medium_create(**wl.medium)
     x0 = torch.from_numpy(np.ascontiguousarray(wl.x0.T)).to("cuda", dtype)
@@ -301,7 +304,7 @@ def run_gpu(a):
         gf.gf_rays_onshell(m, rays, dirs, wl.omega)
         if k_ev:
             k_ev[0].record(stream)
-        gf.gf_trace_rk4(m, rays, wl.omega, wl.dt, wl.n_steps)
+        gf.gf_trace_rk4(m, rays, wl.omega, wl.dt, wl.n_steps, precision=prec)
         if k_ev:
             k_ev[1].record(stream)
 
@@ -356,7 +359,7 @@ def run_gpu(a):
         torch.cuda.synchronize()
         e0 = time.perf_counter()
         for _ in range(a.steps):
-            gf.trace_host(m, x0_h, d_h, wl.omega, wl.dt, wl.n_steps, rays, dirs, out)
+            gf.trace_host(m, x0_h, d_h, wl.omega, wl.dt, wl.n_steps, rays, dirs, out, precision=prec)
         torch.cuda.synchronize()
         barrier()
         te = torch.tensor([time.perf_counter() - e0], dtype=torch.float64, device="cuda")
@@ -382,14 +385,15 @@ def run_gpu(a):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": 1e3 * t_max / a.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if dtype == torch.float64 else "f32",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f64": "f64", "f32": "f32", "f64x": "f64 state, f32x2 blob sums"}[a.precision],
         "data": "synthetic",
         "config": {"workload": f"grin_fibre_16_blobs rays={wl.n} rk4_steps={wl.n_steps} dt={wl.dt}",
                    "rays_per_gpu": wl.n, "rk4_steps": wl.n_steps, "parallelism": f"ray shards x{world}",
                    "l2": "256 MiB buffer written between timed steps"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
-                     "traffic": TRAFFIC_BYTES_1M if (wl.n == 1 << 20 and dtype == torch.float64) else None,
+                     "traffic": TRAFFIC_BYTES_1M if (wl.n == 1 << 20 and a.precision == "f64") else None,
                      "kernel": "rk4_kernel<double, GRIN>", "kernel_ms": 1e3 * k_sec,
                      "flops_per_launch": flops, "evaluations": evals, "blob_terms_live": live,
                      "blob_terms_total": evals * n_blobs,

@@ -52,7 +52,12 @@ typedef enum {
     GF_ERR_TIMEOUT = 5        /* a bounded device-side wait gave up                 */
 } gf_status;
 
-typedef enum { GF_F32 = 0, GF_F64 = 1 } gf_precision;
+/* GF_F64: every operation in IEEE double.  GF_F32: float, Kahan-compensated
+ * state.  GF_F64X: double state, integrator, D and right-hand side, with the
+ * Gaussian-blob sums computed in double-float (pairs of floats, ~48-bit
+ * significand, relative error ~1e-15 per term) on the FP32 pipes; ray buffers
+ * as for GF_F64. */
+typedef enum { GF_F32 = 0, GF_F64 = 1, GF_F64X = 2 } gf_precision;
 
 typedef enum {
     GF_MED_HOMOG = 0,
@@ -193,9 +198,10 @@ gf_status gf_rays_newton_kx(gf_medium m, gf_precision prec, const gf_rays *rays,
  * step j * checkpoint_every of this call (rays that stopped earlier leave
  * their later slots unwritten).
  * prec: GF_F64 computes in double; GF_F32 in float with Kahan-compensated
- * state updates, t kept in double.
+ * state updates, t kept in double; GF_F64X as GF_F64 with the blob sums in
+ * double-float (media without blobs run the GF_F64 kernel).
  * Errors: GF_ERR_INVALID_ARG, GF_ERR_UNSUPPORTED (ckpt with GF_F32),
- * GF_ERR_CUDA.
+ * GF_ERR_CUDA.  gf_rays_onshell and gf_rays_newton_kx treat GF_F64X as GF_F64.
  */
 gf_status gf_trace_rk4(gf_medium m, gf_precision prec, const gf_rays *rays, double omega,
                        double dt, int64_t n_steps, double radius, int64_t checkpoint_every,

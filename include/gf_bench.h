@@ -46,6 +46,14 @@ gf_status gf_bench_set_counters(unsigned long long *counters);
  */
 gf_status gf_bench_exp(const double *in, double *out_lib, double *out_cuda, int64_t n, void *stream);
 
+/*
+ * gf_bench_exp_df -- evaluate the double-float exponential of the GF_F64X
+ * blob evaluator (defined for -44 < a <= 0) on n device doubles (each first
+ * split into a float pair), writing hi + lo as doubles to `out` (device).
+ * Errors: GF_ERR_INVALID_ARG, GF_ERR_CUDA.
+ */
+gf_status gf_bench_exp_df(const double *in, double *out, int64_t n, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

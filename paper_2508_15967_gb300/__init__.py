@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libgf.so")
 
 GF_OK, GF_ERR_INVALID_ARG, GF_ERR_CUDA, GF_ERR_OOM, GF_ERR_UNSUPPORTED, GF_ERR_TIMEOUT = range(6)
-GF_F32, GF_F64 = 0, 1
+GF_F32, GF_F64, GF_F64X = 0, 1, 2
 KINDS = {"homog": 0, "luneburg": 1, "grin": 2, "quadratic": 3, "spline": 4}
 (GF_RAY_ACTIVE, GF_RAY_EXITED, GF_RAY_CUTOFF, GF_RAY_NONFINITE, GF_RAY_MAX_STEPS,
  GF_RAY_STEP_UNDERFLOW, GF_RAY_DONE) = range(7)
@@ -86,6 +86,7 @@ def lib() -> C.CDLL:
             "gf_bench_fma_peak": ([I32, I64, I32, P, P], I32),
             "gf_bench_set_counters": ([P], I32),
             "gf_bench_exp": ([P, P, P, I64, P], I32),
+            "gf_bench_exp_df": ([P, P, I64, P], I32),
             "gf_adjoint_scratch_bytes": ([P, I64, I64], C.c_size_t),
             "gf_trace_adjoint": ([P, I64, D, D, I64, I64, P, P, P, I64, P, P, P, C.c_size_t, P], I32),
             "gf_trace_adjoint_static": ([P, I64, D, D, I64, I64, P, P, P, I64, P, P, P], I32),
@@ -237,10 +238,15 @@ def gf_rays_newton_kx(m: Medium, rays: Rays, omega: float = 1.0, tol: float = 1e
 
 
 def gf_trace_rk4(m: Medium, rays: Rays, omega: float, dt: float, n_steps: int, radius: float = 0.0,
-                 checkpoint_every: int = 0, ckpt: torch.Tensor | None = None, stream=None) -> None:
-    """Advance active rays by n_steps fixed RK4 steps in place (see gf.h)."""
+                 checkpoint_every: int = 0, ckpt: torch.Tensor | None = None, stream=None,
+                 precision: int | None = None) -> None:
+    """Advance active rays by n_steps fixed RK4 steps in place (see gf.h).
+    precision: None = from the ray dtype (GF_F64 / GF_F32); GF_F64X for float64 rays."""
     s = rays.struct()
-    _check("gf_trace_rk4", lib().gf_trace_rk4(m.handle, rays.precision, C.byref(s), omega, dt,
+    prec = rays.precision if precision is None else precision
+    if prec == GF_F64X and rays.y.dtype != torch.float64:
+        raise ValueError("GF_F64X needs float64 rays")
+    _check("gf_trace_rk4", lib().gf_trace_rk4(m.handle, prec, C.byref(s), omega, dt,
                                               int(n_steps), radius, int(checkpoint_every),
                                               _ptr(ckpt), _stream(stream)))
 
@@ -386,7 +392,7 @@ def gf_dopri5_autotune(b: Batch, rays: Rays, omega: float = 1.0, ctl: GfStepCtl 
 
 def trace_host(m: Medium, x0_host: torch.Tensor, dir_host: torch.Tensor, omega: float, dt: float,
                n_steps: int, rays: Rays | None = None, dirs: torch.Tensor | None = None,
-               out: dict | None = None, radius: float = 0.0) -> dict:
+               out: dict | None = None, radius: float = 0.0, precision: int | None = None) -> dict:
     """End-to-end call on host buffers: copy launch points and directions
     ((3, n) host tensors, pinned for overlap) to the device, set the rays on
     shell, trace n_steps RK4 steps, and copy every ray buffer back.  Device
@@ -404,7 +410,7 @@ def trace_host(m: Medium, x0_host: torch.Tensor, dir_host: torch.Tensor, omega: 
     rays.steps.zero_()
     rays.d_max.zero_()
     gf_rays_onshell(m, rays, dirs, omega)
-    gf_trace_rk4(m, rays, omega, dt, n_steps, radius)
+    gf_trace_rk4(m, rays, omega, dt, n_steps, radius, precision=precision)
     if out is None:
         out = {k: torch.empty(getattr(rays, k).shape, dtype=getattr(rays, k).dtype).pin_memory()
                for k in ("y", "t", "status", "steps", "d_res", "d_max")}
@@ -433,6 +439,14 @@ def gf_bench_exp(a: torch.Tensor):
     o1, o2 = torch.empty_like(a), torch.empty_like(a)
     _check("gf_bench_exp", lib().gf_bench_exp(_ptr(a), _ptr(o1), _ptr(o2), a.numel(), _stream(None)))
     return o1, o2
+
+
+def gf_bench_exp_df(a: torch.Tensor) -> torch.Tensor:
+    """Double-float exp of a float64 device tensor (hi + lo returned as float64)."""
+    a = a.contiguous()
+    o = torch.empty_like(a)
+    _check("gf_bench_exp_df", lib().gf_bench_exp_df(_ptr(a), _ptr(o), a.numel(), _stream(None)))
+    return o
 
 
 def medium_from_workload(spec: dict) -> Medium:

@@ -256,7 +256,7 @@ gf_status gf_rays_onshell(gf_medium m, gf_precision prec, const gf_rays *rays, c
 {
     gf_status s;
     if ((s = check_medium(m)) != GF_OK) return s;
-    if (prec != GF_F32 && prec != GF_F64) {
+    if (prec != GF_F32 && prec != GF_F64 && prec != GF_F64X) {
         set_error("gf_rays_onshell: unknown precision %d", (int)prec);
         return GF_ERR_INVALID_ARG;
     }
@@ -276,7 +276,7 @@ gf_status gf_rays_newton_kx(gf_medium m, gf_precision prec, const gf_rays *rays,
 {
     gf_status s;
     if ((s = check_medium(m)) != GF_OK) return s;
-    if (prec != GF_F32 && prec != GF_F64) {
+    if (prec != GF_F32 && prec != GF_F64 && prec != GF_F64X) {
         set_error("gf_rays_newton_kx: unknown precision %d", (int)prec);
         return GF_ERR_INVALID_ARG;
     }
@@ -296,7 +296,7 @@ gf_status gf_trace_rk4(gf_medium m, gf_precision prec, const gf_rays *rays, doub
 {
     gf_status s;
     if ((s = check_medium(m)) != GF_OK) return s;
-    if (prec != GF_F32 && prec != GF_F64) {
+    if (prec != GF_F32 && prec != GF_F64 && prec != GF_F64X) {
         set_error("gf_trace_rk4: unknown precision %d", (int)prec);
         return GF_ERR_INVALID_ARG;
     }
@@ -307,8 +307,8 @@ gf_status gf_trace_rk4(gf_medium m, gf_precision prec, const gf_rays *rays, doub
     }
     if ((s = check_rays(rays, true)) != GF_OK) return s;
     if (ckpt != nullptr) {
-        if (prec != GF_F64) {
-            set_error("gf_trace_rk4: checkpoints are only produced by the FP64 path");
+        if (prec == GF_F32) {
+            set_error("gf_trace_rk4: checkpoints are only produced by the FP64 paths");
             return GF_ERR_UNSUPPORTED;
         }
         if (checkpoint_every <= 0) {

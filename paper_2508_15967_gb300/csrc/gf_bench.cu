@@ -1,4 +1,5 @@
 // gf_bench.cu -- FMA-throughput microbenchmark behind gf_bench_fma_peak.
+#include "gf_dfloat.cuh"
 #include "gf_internal.cuh"
 #include "../../include/gf_bench.h"
 
@@ -50,6 +51,16 @@ static gf_status run_peak(int64_t iters, int bps, double *tflops, double *ms)
     return GF_OK;
 }
 
+__global__ void dfexp_check_kernel(const double *in, double *out, int64_t n)
+{
+    __shared__ float sT[128];
+    stage_dfexp_table(sT);
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = df_to_double(df_exp(df_from_double(in[i]), sT));
+}
+
 __global__ void exp_check_kernel(const double *in, double *out_lib, double *out_cuda, int64_t n)
 {
     __shared__ double sT[64];
@@ -77,6 +88,19 @@ extern "C" gf_status gf_bench_exp(const double *in, double *out_lib, double *out
         return s;
     gf::exp_check_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(in, out_lib, out_cuda, n);
     return gf::cuda_status(cudaGetLastError(), "gf_bench_exp launch");
+}
+
+extern "C" gf_status gf_bench_exp_df(const double *in, double *out, int64_t n, void *stream)
+{
+    if (n < 0) {
+        gf::set_error("gf_bench_exp_df: n < 0");
+        return GF_ERR_INVALID_ARG;
+    }
+    if (n == 0) return GF_OK;
+    gf_status s;
+    if ((s = gf::check_device_ptr(in, "in")) != GF_OK || (s = gf::check_device_ptr(out, "out")) != GF_OK) return s;
+    gf::dfexp_check_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(in, out, n);
+    return gf::cuda_status(cudaGetLastError(), "gf_bench_exp_df launch");
 }
 
 extern "C" gf_status gf_bench_fma_peak(gf_precision prec, int64_t iters, int32_t blocks_per_sm,

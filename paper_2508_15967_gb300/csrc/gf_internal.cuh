@@ -151,6 +151,8 @@ template <typename R>
 struct EvalCtx {
     const double *T = nullptr;   // 2^(j/64) table (FP64 path)
     const float *pre = nullptr;  // FP32 pre-test table, 4 floats per blob, or NULL
+    const float *dfb = nullptr;  // double-float blob rows (GF_F64X mode)
+    const float *dfT = nullptr;  // double-float 2^(j/64) table (GF_F64X mode)
     int live = 0;                // blob terms evaluated (work counter)
 };
 

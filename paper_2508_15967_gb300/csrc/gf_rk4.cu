@@ -6,9 +6,55 @@
 // step) and stored once -- the load-once / store-once kernel shape of the
 // paper's generated RK4 ray update (Sec. 2.2, Sec. 4).  The blob table is
 // staged in shared memory and read as warp-wide broadcasts.
+#include "gf_dfloat.cuh"
 #include "gf_internal.cuh"
 
 namespace gf {
+
+// Right-hand side with the blob sums in double-float (GF_F64X): base index,
+// D and f in FP64 exactly as rhs_iso, blob terms from blobs_df.
+template <int KIND>
+struct RhsDF {
+    const MediumParams &m;
+    int nb;
+    Omega<double> om;
+    template <bool WANT_D = true>
+    __device__ __forceinline__ bool eval(const double *y, double *f, double &D, EvalCtx<double> &cx) const
+    {
+        double n2, g[3];
+        EvalCtx<double> base;
+        iso_index<double, KIND>(m, nullptr, 0, y, n2, g, base);
+        blobs_df(cx.dfb, nb, y, n2, g, cx.dfT, cx.live);
+        if constexpr (WANT_D) D = y[3] * y[3] + y[4] * y[4] + y[5] * y[5] - om.w * om.w * n2;
+        if (!(n2 > 0.0)) return false;
+        const double inv = 1.0 / n2;
+        const double a = inv * om.inv_w, b = om.half_w * inv;
+        f[0] = a * y[3];
+        f[1] = a * y[4];
+        f[2] = a * y[5];
+        f[3] = b * g[0];
+        f[4] = b * g[1];
+        f[5] = b * g[2];
+        return true;
+    }
+};
+
+template <typename R, int KIND, bool DF>
+struct RhsSel {
+    using type = Rhs<R, KIND>;
+    static __device__ __forceinline__ type make(const MediumParams &m, const R *sb, const Omega<R> &om)
+    {
+        return type{m, sb, m.n_blobs, om};
+    }
+};
+template <int KIND>
+struct RhsSel<double, KIND, true> {
+    using type = RhsDF<KIND>;
+    static __device__ __forceinline__ type make(const MediumParams &m, const double *, const Omega<double> &om)
+    {
+        return type{m, m.n_blobs, om};
+    }
+};
 
 constexpr int kRk4Block = 128;
 
@@ -75,19 +121,24 @@ __device__ __forceinline__ void add_work(unsigned long long *counters, long long
     }
 }
 
-template <typename R, int KIND>
-__global__ void __launch_bounds__(kRk4Block, (KIND == K_SPLINE || sizeof(R) == 4) ? 1 : 5) rk4_kernel(const MediumParams m, const RaysView<R> r,
-                                                        const Omega<R> om, const R dt, const double dt64,
-                                                        const int64_t n_steps, const R radius2,
-                                                        const int64_t every, double *__restrict__ ckpt,
-                                                        unsigned long long *counters)
+template <typename R, int KIND, bool DF>
+__global__ void __launch_bounds__(kRk4Block, (KIND == K_SPLINE || sizeof(R) == 4 || DF) ? 1 : 5)
+rk4_kernel(const MediumParams m, const RaysView<R> r, const Omega<R> om, const R dt, const double dt64,
+           const int64_t n_steps, const R radius2, const int64_t every, double *__restrict__ ckpt,
+           unsigned long long *counters)
 {
     __shared__ R sb[kBlobStride * GF_MAX_BLOBS];
     __shared__ double sT[64];
     __shared__ float sp[4 * GF_MAX_BLOBS];
-    if constexpr (KIND != K_SPLINE) stage_blobs<R>(m, sb);
-    constexpr bool kPretest = sizeof(R) == 8 && KIND != K_SPLINE;
+    __shared__ float sdf[DF ? kDfBlobStride * GF_MAX_BLOBS : 1];
+    __shared__ float sdT[DF ? 128 : 1];
+    if constexpr (KIND != K_SPLINE && !DF) stage_blobs<R>(m, sb);
+    constexpr bool kPretest = sizeof(R) == 8 && KIND != K_SPLINE && !DF;
     if constexpr (kPretest) stage_pretest(m, sp);
+    if constexpr (DF) {
+        stage_df_blobs(m, sdf);
+        stage_dfexp_table(sdT);
+    }
     stage_exp_table(sT);
     __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -98,9 +149,13 @@ __global__ void __launch_bounds__(kRk4Block, (KIND == K_SPLINE || sizeof(R) == 4
     EvalCtx<R> cx;
     cx.T = sT;
     if constexpr (kPretest) cx.pre = sp;
+    if constexpr (DF) {
+        cx.dfb = sdf;
+        cx.dfT = sdT;
+    }
     long long evals = 0;
     int64_t s = 0;
-    const Rhs<R, KIND> f{m, sb, m.n_blobs, om};
+    const auto f = RhsSel<R, KIND, DF>::make(m, sb, om);
     if (st == GF_RAY_ACTIVE) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) y[c] = r.y[c * r.ld + i];
@@ -254,16 +309,25 @@ static RaysView<R> view(const gf_rays &r)
     return RaysView<R>{r.n, r.ld, (R *)r.y, r.t, r.status, r.steps, r.d_res, r.d_max};
 }
 
-template <typename R, int KIND>
+template <typename R, int KIND, bool DF = false>
 static cudaError_t rk4_launch(const MediumParams &m, const gf_rays &r, double omega, double dt,
                               int64_t n_steps, double radius, int64_t every, double *ckpt,
                               cudaStream_t s)
 {
     const int64_t blocks = (r.n + kRk4Block - 1) / kRk4Block;
     const R r2 = radius > 0 ? (R)(radius * radius) : (R)0;
-    rk4_kernel<R, KIND><<<(unsigned)blocks, kRk4Block, 0, s>>>(m, view<R>(r), make_omega<R>(omega), (R)dt,
-                                                               dt, n_steps, r2, every, ckpt, work_counters());
+    rk4_kernel<R, KIND, DF><<<(unsigned)blocks, kRk4Block, 0, s>>>(m, view<R>(r), make_omega<R>(omega), (R)dt,
+                                                                   dt, n_steps, r2, every, ckpt, work_counters());
     return cudaGetLastError();
+}
+
+template <typename R, int KIND>
+static cudaError_t rk4_launch_df(const MediumParams &m, const gf_rays &r, double omega, double dt,
+                                 int64_t n_steps, double radius, int64_t every, double *ckpt, cudaStream_t s)
+{
+    // media without blobs have nothing to evaluate in double-float
+    if (m.n_blobs == 0) return rk4_launch<double, KIND, false>(m, r, omega, dt, n_steps, radius, every, ckpt, s);
+    return rk4_launch<double, KIND, true>(m, r, omega, dt, n_steps, radius, every, ckpt, s);
 }
 
 template <typename R, int KIND>
@@ -292,6 +356,15 @@ cudaError_t launch_rk4(const MediumParams &m, gf_precision prec, const gf_rays &
     if (r.n == 0) return cudaSuccess;
     if (prec == GF_F64) {
         GF_KIND_SWITCH(m.kind, rk4_launch, double, m, r, omega, dt, n_steps, radius, every, ckpt, s)
+    } else if (prec == GF_F64X) {
+        switch (m.kind) {
+        case K_HOMOG: return rk4_launch_df<double, K_HOMOG>(m, r, omega, dt, n_steps, radius, every, ckpt, s);
+        case K_LUNEBURG: return rk4_launch_df<double, K_LUNEBURG>(m, r, omega, dt, n_steps, radius, every, ckpt, s);
+        case K_GRIN: return rk4_launch_df<double, K_GRIN>(m, r, omega, dt, n_steps, radius, every, ckpt, s);
+        case K_QUADRATIC: return rk4_launch_df<double, K_QUADRATIC>(m, r, omega, dt, n_steps, radius, every, ckpt, s);
+        case K_SPLINE: return rk4_launch<double, K_SPLINE>(m, r, omega, dt, n_steps, radius, every, ckpt, s);
+        default: return cudaErrorInvalidValue;
+        }
     } else {
         GF_KIND_SWITCH(m.kind, rk4_launch, float, m, r, omega, dt, n_steps, radius, every, ckpt, s)
     }
@@ -310,7 +383,7 @@ cudaError_t launch_newton_kx(const MediumParams &m, gf_precision prec, const gf_
                              int max_iter, cudaStream_t s)
 {
     if (r.n == 0) return cudaSuccess;
-    if (prec == GF_F64) {
+    if (prec == GF_F64 || prec == GF_F64X) {
         GF_KIND_SWITCH(m.kind, newton_launch, double, m, r, omega, tol, max_iter, s)
     } else {
         GF_KIND_SWITCH(m.kind, newton_launch, float, m, r, omega, tol, max_iter, s)
@@ -321,7 +394,7 @@ cudaError_t launch_onshell(const MediumParams &m, gf_precision prec, const gf_ra
                            double omega, cudaStream_t s)
 {
     if (r.n == 0) return cudaSuccess;
-    if (prec == GF_F64) {
+    if (prec == GF_F64 || prec == GF_F64X) {
         GF_KIND_SWITCH(m.kind, onshell_launch, double, m, r, dir, omega, s)
     } else {
         GF_KIND_SWITCH(m.kind, onshell_launch, float, m, r, dir, omega, s)
