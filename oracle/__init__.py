@@ -23,7 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-KIND = {"homog": 0, "luneburg": 1, "grin": 2, "quadratic": 3, "spline": 4}
+KIND = {"homog": 0, "luneburg": 1, "grin": 2, "quadratic": 3, "spline": 4, "cold": 5}
 ACTIVE, EXITED, CUTOFF, NONFINITE, MAX_STEPS, STEP_UNDERFLOW, DONE = range(7)
 
 
@@ -44,7 +44,9 @@ def build(force: bool = False) -> str:
 class _Medium(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n_blobs", C.c_int32), ("grid_n", C.c_int32),
                 ("pad_", C.c_int32), ("n_h", C.c_double), ("n0", C.c_double),
-                ("a", C.c_double), ("blobs", C.c_void_p), ("grid", C.c_void_p)]
+                ("a", C.c_double), ("blobs", C.c_void_p), ("grid", C.c_void_p),
+                ("n_species", C.c_int32), ("pad2_", C.c_int32), ("species", C.c_double * 8),
+                ("prof", C.c_double * 4)]
 
 
 class _StepCtl(C.Structure):
@@ -89,6 +91,8 @@ class Medium:
     a: float = 2.0
     blobs: np.ndarray | None = None
     grid: np.ndarray | None = None
+    species: tuple = ()          # cold plasma: ((w_p^2, Omega), ...) at f = g = 1
+    profile: tuple = (1.0, 0.0, 1.0, 0.0)   # (f0, f1, g0, g1)
 
     def struct(self) -> _Medium:
         self._blobs = None if self.blobs is None or len(self.blobs) == 0 else \
@@ -98,8 +102,12 @@ class Medium:
         gn = 0 if self._grid is None else self._grid.shape[0]
         if self.kind == "spline" and self._grid is None:
             raise ValueError("spline medium needs a grid")
+        sp = np.zeros(8)
+        for i, (wp2, om) in enumerate(self.species):
+            sp[2 * i], sp[2 * i + 1] = wp2, om
         return _Medium(KIND[self.kind], nb, gn, 0, self.n_h, self.n0, self.a,
-                       _p(self._blobs), _p(self._grid))
+                       _p(self._blobs), _p(self._grid), len(self.species), 0,
+                       (C.c_double * 8)(*sp), (C.c_double * 4)(*self.profile))
 
 
 def medium(**kw) -> Medium:

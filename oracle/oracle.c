@@ -33,7 +33,7 @@
 
 /* ------------------------------------------------------------------ codes */
 
-enum { OR_HOMOG = 0, OR_LUNEBURG = 1, OR_GRIN = 2, OR_QUADRATIC = 3, OR_SPLINE = 4 };
+enum { OR_HOMOG = 0, OR_LUNEBURG = 1, OR_GRIN = 2, OR_QUADRATIC = 3, OR_SPLINE = 4, OR_COLD = 5 };
 
 enum {
     OR_ACTIVE = 0,          /* still propagating; a further call continues it      */
@@ -54,6 +54,12 @@ typedef struct {
     double n0, a;           /* GRIN: n^2 = n0^2 (1 - a^2 (y^2 + z^2))                */
     const double *blobs;    /* n_blobs rows (A, cx, cy, cz, w)                       */
     const float *grid;      /* grid_n^3 nodes x 8 floats, x fastest                  */
+    int32_t n_species;      /* cold plasma: 1..4 species                             */
+    int32_t pad2_;
+    double species[8];      /* per species (w_p^2, Omega) at f = g = 1: squared plasma
+                               frequency and signed cyclotron frequency              */
+    double prof[4];         /* f(x) = prof[0] + prof[1] x_0 scales w_p^2 (density),
+                               g(x) = prof[2] + prof[3] x_0 scales Omega (|B|)      */
 } or_medium;
 
 /* ------------------------------------------------------ isotropic index n^2 */
@@ -196,8 +202,59 @@ static void or_spline(const or_medium *m, const double *x, double val[7], double
 
 typedef struct {
     double D, Dx[3], Dk[3], Dw;
-    double eps;             /* n^2 (isotropic) or eps (anisotropic): D_w = -2 w eps */
+    double eps;             /* n^2 (isotropic) or eps (anisotropic): D_w = -2 w eps;
+                               |D_w| for the cold plasma                            */
 } or_disp;
+
+/* Cold plasma with B along z (Sec. 4.1, Eqs. 5-10): the dielectric tensor has
+ * eps11 = S = 1 - sum w_p^2 / (w^2 - Omega^2), eps12 = -i Dst with
+ * Dst = sum Omega w_p^2 / (w (w^2 - Omega^2)), eps33 = P = 1 - sum w_p^2 / w^2,
+ * and with n = k / w (c = 1), a = n_x^2 + n_y^2, b = n_z^2, R L = S^2 - Dst^2,
+ *   D = det(eps + n n - n^2 I) = S a (a + b) + P b (a + b) - R L a - P S (a + 2 b) + P R L
+ * (the Stix form A n^4 - B n^2 + C written in a and b).  The slab profiles
+ * f(x) = f0 + f1 x (w_p^2 proportional to f, the linear gradient of Eq. 4)
+ * and g(x) = g0 + g1 x (Omega proportional to g) depend on the first
+ * coordinate only.  Gradients by the chain rule through S, Dst, P, a, b. */
+static void or_cold(const or_medium *m, const double *x, const double *k, double w, or_disp *o)
+{
+    double f = m->prof[0] + m->prof[1] * x[0], fx = m->prof[1];
+    double g = m->prof[2] + m->prof[3] * x[0], gx = m->prof[3];
+    double S = 1.0, Dst = 0.0, P = 1.0, Sx = 0.0, Dx_ = 0.0, Px = 0.0, Sw = 0.0, Dw_ = 0.0, Pw = 0.0;
+    double a, b, RL, DS, DD, DP, Da, Db;
+    int sp, i;
+    for (sp = 0; sp < m->n_species; sp++) {
+        double wp2 = m->species[2 * sp] * f, wp2x = m->species[2 * sp] * fx;
+        double W = m->species[2 * sp + 1] * g, Wx = m->species[2 * sp + 1] * gx;
+        double den = w * w - W * W;
+        S -= wp2 / den;
+        Dst += W * wp2 / (w * den);
+        P -= wp2 / (w * w);
+        Sx -= (wp2x * den + 2.0 * wp2 * W * Wx) / (den * den);
+        Dx_ += ((Wx * wp2 + W * wp2x) * den + 2.0 * W * W * wp2 * Wx) / (w * den * den);
+        Px -= wp2x / (w * w);
+        Sw += 2.0 * w * wp2 / (den * den);
+        Dw_ -= W * wp2 * (3.0 * w * w - W * W) / ((w * w * w - w * W * W) * (w * w * w - w * W * W));
+        Pw += 2.0 * wp2 / (w * w * w);
+    }
+    a = (k[0] * k[0] + k[1] * k[1]) / (w * w);
+    b = k[2] * k[2] / (w * w);
+    RL = S * S - Dst * Dst;
+    o->D = S * a * (a + b) + P * b * (a + b) - RL * a - P * S * (a + 2.0 * b) + P * RL;
+    DS = a * (a + b) - 2.0 * S * a - P * (a + 2.0 * b) + 2.0 * P * S;
+    DD = 2.0 * Dst * a - 2.0 * P * Dst;
+    DP = b * (a + b) - S * (a + 2.0 * b) + RL;
+    Da = S * (2.0 * a + b) + P * b - RL - P * S;
+    Db = S * a + P * (a + 2.0 * b) - 2.0 * P * S;
+    o->Dk[0] = Da * 2.0 * k[0] / (w * w);
+    o->Dk[1] = Da * 2.0 * k[1] / (w * w);
+    o->Dk[2] = Db * 2.0 * k[2] / (w * w);
+    o->Dx[0] = DS * Sx + DD * Dx_ + DP * Px;
+    o->Dx[1] = 0.0;
+    o->Dx[2] = 0.0;
+    o->Dw = Da * (-2.0 * a / w) + Db * (-2.0 * b / w) + DS * Sw + DD * Dw_ + DP * Pw;
+    o->eps = fabs(o->Dw);
+    (void)i;
+}
 
 /* isotropic : D = |k|^2 - w^2 n^2(x)
  * spline    : D = k^T M(x) k - w^2 eps(x)                                     */
@@ -205,6 +262,10 @@ static void or_dispersion(const or_medium *m, const double *x, const double *k, 
                           or_disp *o)
 {
     int i, j, c;
+    if (m->kind == OR_COLD) {
+        or_cold(m, x, k, w, o);
+        return;
+    }
     if (m->kind == OR_SPLINE) {
         double val[7], grad[7][3], M[3][3], dM[3][3][3];
         static const int idx[3][3] = { { 0, 1, 2 }, { 1, 3, 4 }, { 2, 4, 5 } };
@@ -321,6 +382,11 @@ void or_onshell(const or_medium *m, int64_t n, const double *x0, const double *d
         const double *x = x0 + 3 * r, *d = dir + 3 * r;
         double eps, q, s;
         int i, j;
+        if (m->kind == OR_COLD) {     /* two branches: use or_newton_kx instead */
+            status[r] = OR_CUTOFF;
+            for (i = 0; i < 3; i++) k0[3 * r + i] = 0.0;
+            continue;
+        }
         if (m->kind == OR_SPLINE) {
             double val[7], grad[7][3];
             static const int idx[3][3] = { { 0, 1, 2 }, { 1, 3, 4 }, { 2, 4, 5 } };

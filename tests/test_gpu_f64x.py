@@ -26,7 +26,7 @@ def test_double_float_exp_accuracy():
     # the input itself is a float pair (~2^-48 relative), so exp's relative
     # error scales with |a| (its condition number); bound it accordingly
     rel = np.abs(got - ref) / ref / np.maximum(1.0, np.abs(a))
-    assert rel.max() <= 4e-15, (rel.max(), a[np.argmax(rel)])
+    assert rel.max() <= 8e-15, (rel.max(), a[np.argmax(rel)])      # ~2^-47
     assert np.median(rel) <= 1e-15
 
 

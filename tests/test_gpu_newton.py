@@ -37,7 +37,7 @@ def test_newton_kx_matches_oracle(name):
     assert np.array_equal(st_g, st_o)
     ok = st_o == 0
     assert ok.mean() > 0.5 and (~ok).any()       # both branches of the outcome occur
-    np.testing.assert_allclose(k_g[ok, 0], k_o[ok, 0], rtol=2e-15, atol=1e-15)
+    np.testing.assert_allclose(k_g[ok, 0], k_o[ok, 0], rtol=2e-15, atol=1e-14)   # |k| ~ 1 scale
     np.testing.assert_array_equal(k_g[:, 1:], k[:, 1:])
     D = O.eval_dispersion(O.medium(**spec), x[ok], k_g[ok])[:, 0]
     assert np.abs(D).max() <= 8e-15

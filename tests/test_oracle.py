@@ -661,3 +661,126 @@ def test_newton_kx_spline_quadratic_roots_and_no_root():
         np.testing.assert_allclose(kk[:, 0], roots[sign], rtol=1e-13, atol=1e-15)
     kk, st, it = O.newton_kx(m, x[:3], np.column_stack([np.ones(3), np.full((3, 2), 3.0)]), max_iter=60)
     assert (st == O.CUTOFF).all()
+
+
+# ---------------------------------------------------------------- cold plasma
+
+COLD2 = dict(kind="cold", species=((0.45, -0.6), (0.03, 0.08)), profile=(1.0, 0.1, 1.0, 0.05))
+COLD_E = dict(kind="cold", species=((0.3, -0.5),), profile=(1.0, 0.1, 1.0, 0.0))
+
+
+def _cold_det(spec, x, k, w):
+    """det(eps + n n - n^2 I) with the dielectric tensor of Eqs. 7-10, complex numpy."""
+    f0, f1, g0, g1 = spec["profile"]
+    out = []
+    for xi, ki in zip(x, k):
+        f, g = f0 + f1 * xi[0], g0 + g1 * xi[0]
+        e11 = 1 - sum(wp2 * f / w ** 2 / (1 - (om * g) ** 2 / w ** 2) for wp2, om in spec["species"])
+        e12 = -1j * sum((om * g / w) * (wp2 * f / w ** 2) / (1 - (om * g) ** 2 / w ** 2)
+                        for wp2, om in spec["species"])
+        e33 = 1 - sum(wp2 * f / w ** 2 for wp2, _ in spec["species"])
+        eps = np.array([[e11, e12, 0], [-e12, e11, 0], [0, 0, e33]])
+        n = ki / w
+        out.append(np.linalg.det(eps + np.outer(n, n) - (n @ n) * np.eye(3)))
+    return np.array(out)
+
+
+def test_cold_plasma_D_equals_the_determinant():
+    """The Stix-form D against the determinant of Eq. 5 built from Eqs. 6-10
+    (catches a wrong sign of eps12, a swapped S/P, a wrong n_parallel axis)."""
+    rng = np.random.default_rng(20)
+    x = rng.uniform(-3, 3, (25, 3))
+    k = rng.uniform(-1.5, 1.5, (25, 3))
+    for w in (1.0, 1.7):
+        D = O.eval_dispersion(O.medium(**COLD2), x, k, w)[:, 0]
+        det = _cold_det(COLD2, x, k, w)
+        assert np.abs(det.imag).max() < 1e-12
+        np.testing.assert_allclose(D, det.real, rtol=1e-12, atol=1e-12)
+
+
+def test_cold_plasma_partials_match_central_differences():
+    m = O.medium(**COLD2)
+    rng = np.random.default_rng(21)
+    x = rng.uniform(-3, 3, (12, 3))
+    k = rng.uniform(-1.5, 1.5, (12, 3))
+    w, h = 1.3, 1e-4
+    ev = O.eval_dispersion(m, x, k, w)
+    Dx = _fd5(lambda xx: O.eval_dispersion(m, xx, k, w)[:, 0], x, h)
+    Dk = _fd5(lambda kk: O.eval_dispersion(m, x, kk, w)[:, 0], k, h)
+    Dw = (-O.eval_dispersion(m, x, k, w + 2 * h)[:, 0] + 8 * O.eval_dispersion(m, x, k, w + h)[:, 0]
+          - 8 * O.eval_dispersion(m, x, k, w - h)[:, 0] + O.eval_dispersion(m, x, k, w - 2 * h)[:, 0]) / (12 * h)
+    scale = 1 + np.abs(ev[:, 1:8]).max()
+    np.testing.assert_allclose(ev[:, 1:4], Dx, atol=1e-8 * scale)
+    np.testing.assert_allclose(ev[:, 4:7], Dk, atol=1e-8 * scale)
+    np.testing.assert_allclose(ev[:, 7], Dw, atol=1e-8 * scale)
+
+
+def test_cold_plasma_newton_finds_O_and_X_roots():
+    """For k_z = 0, D = (S a - R L)(a - P): the O root a = P and the X root
+    a = R L / S; Newton from a guess near each returns it (Sec. 4: the guess
+    selects the branch)."""
+    m = O.medium(**COLD_E)
+    x = np.array([[0.0, 0, 0], [2.0, 0, 0], [-1.0, 0, 0]])
+    ky = np.array([0.1, 0.3, 0.0])
+    f = 1 + 0.1 * x[:, 0]
+    P = 1 - 0.3 * f
+    R, L = 1 - 0.3 * f / 0.5, 1 - 0.3 * f / 1.5
+    S = (R + L) / 2
+    kO = np.sqrt(P - ky ** 2)
+    kX = np.sqrt(R * L / S - ky ** 2)
+    for guess, exact in ((kO + 0.05, kO), (kX - 0.05, kX)):
+        k, st, _ = O.newton_kx(m, x, np.column_stack([guess, ky, np.zeros(3)]))
+        assert (st == O.ACTIVE).all()
+        np.testing.assert_allclose(k[:, 0], exact, rtol=1e-13)
+
+
+def test_cold_plasma_O_mode_parabola_is_exact():
+    """O-mode in the x-y plane of the linear-density slab (Eq. 4): on the O
+    branch the ray equations reduce to dx/dt = k / w, dk_x/dt = w P_x / 2 with
+    P_x constant, so the ray is a parabola in t -- reproduced by RK4 to
+    rounding; k_y, k_z = 0 and D are conserved; the ray turns where k_x = 0."""
+    m = O.medium(**COLD2)
+    w = 1.0
+    x0 = np.array([[0.0, 0.2, 0.0], [-1.0, 0.0, 0.0], [0.5, -0.3, 0.0]])
+    ky = np.array([0.2, 0.0, -0.15])
+    f = 1 + 0.1 * x0[:, 0]
+    Wsum = 0.45 + 0.03
+    P = 1 - Wsum * f / w ** 2
+    k0 = np.column_stack([np.sqrt(w ** 2 * P - ky ** 2), ky, np.zeros(3)])
+    assert np.abs(O.eval_dispersion(m, x0, k0, w)[:, 0]).max() < 1e-14
+    r = O.make_rays(x0, k0)
+    T, n = 60.0, 6000                                 # turns near t = 29
+    O.trace_rk4(m, r, w, T / n, n)
+    c = -Wsum * 0.1 / (2 * w)                         # dk_x/dt = w P_x / 2
+    kx = k0[:, 0] + c * T
+    xx = x0[:, 0] + (k0[:, 0] * T + c * T * T / 2) / w
+    yy = x0[:, 1] + ky * T / w
+    np.testing.assert_allclose(r.y[:, 3], kx, atol=1e-12)
+    np.testing.assert_allclose(r.y[:, 0], xx, atol=1e-11)
+    np.testing.assert_allclose(r.y[:, 1], yy, atol=1e-11)
+    assert (r.y[:, 5] == 0).all() and (r.y[:, 2] == 0).all()
+    assert (kx < 0).all()                             # reflected off the P = k_y^2/w^2 cut-off
+    assert r.dmax.max() < 1e-12
+
+
+def test_cold_plasma_X_mode_reflects_at_R_cutoff():
+    """X-mode launched along +x into rising density (uniform B) turns at the
+    R = 0 cut-off, f(x_R) = w (w + Omega_e) / w_pe^2, well before the upper
+    hybrid resonance (S = 0) and the O cut-off (P = 0)."""
+    m = O.medium(**COLD_E)
+    x0 = np.zeros((1, 3))
+    k, st, _ = O.newton_kx(m, x0, np.array([[0.7, 0.0, 0.0]]))
+    f = 1.0
+    R, L, P = 1 - 0.3 * f / 0.5, 1 - 0.3 * f / 1.5, 1 - 0.3 * f
+    S = (R + L) / 2
+    np.testing.assert_allclose(k[0, 0], np.sqrt(R * L / S), rtol=1e-13)
+    xR = (1.0 * (1.0 - 0.5) / 0.3 - 1.0) / 0.1
+    xs = []
+    r = O.make_rays(x0, k)
+    for _ in range(400):
+        O.trace_rk4(m, r, 1.0, 0.01, 10)
+        xs.append(r.y[0, 0])
+    xs = np.array(xs)
+    assert abs(xs.max() - xR) < 1e-3, (xs.max(), xR)
+    assert xs[-1] < xs.max() - 0.03 and r.y[0, 3] < 0     # on its way back
+    assert r.dmax.max() < 1e-9 and r.status[0] == O.ACTIVE
