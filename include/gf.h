@@ -15,6 +15,8 @@
  *   GF_MED_QUADRATIC  D = |k|^2 - w^2 (2 - |x|^2)        (Luneburg law, no kink)
  *   GF_MED_SPLINE     D = k^T M(x) k - w^2 eps(x), M (symmetric 3x3) and eps from
  *                     a periodic tricubic B-spline grid on [-1, 1)^3
+ *   GF_MED_COLD       cold magnetised plasma, D = det(eps + n n - n^2 I), n = k/w
+ *                     (c = 1), B along z, slab profiles along x (Sec. 4.1, Eqs. 4-10)
  * Every isotropic medium may add Gaussian blobs to n^2:
  *   n^2 += sum_j A_j exp(-|x - c_j|^2 / (2 w_j^2)).
  *
@@ -64,7 +66,8 @@ typedef enum {
     GF_MED_LUNEBURG = 1,
     GF_MED_GRIN = 2,
     GF_MED_QUADRATIC = 3,
-    GF_MED_SPLINE = 4
+    GF_MED_SPLINE = 4,
+    GF_MED_COLD = 5
 } gf_medium_kind;
 
 /* Ray status codes, stored per ray (int32). */
@@ -79,6 +82,7 @@ enum {
 };
 
 #define GF_MAX_BLOBS 64         /* blobs per medium                                   */
+#define GF_MAX_SPECIES 4        /* cold-plasma species                                */
 
 /* Host-side description of a medium, read only during gf_medium_create. */
 typedef struct {
@@ -93,6 +97,17 @@ typedef struct {
                                    (ix, iy, iz) at (-1 + ix h, ...), h = 2 / grid_n, holding
                                    (M11, M12, M13, M22, M23, M33, eps, unused); the values
                                    are B-spline control coefficients (no prefilter)       */
+    /* GF_MED_COLD: species s has squared plasma frequency w_p,s^2 f(x) and signed
+       cyclotron frequency Omega_s g(x), with f(x) = profile[0] + profile[1] x_0 (the
+       density, e.g. the linear gradient 0.1 x + 1 of Eq. 4) and g(x) = profile[2] +
+       profile[3] x_0 (|B|).  S = 1 - sum w_p^2/(w^2 - Omega^2),
+       Dst = sum Omega w_p^2/(w (w^2 - Omega^2)), P = 1 - sum w_p^2/w^2 (Eqs. 7-10);
+       with a = n_x^2 + n_y^2, b = n_z^2:
+       D = S a (a+b) + P b (a+b) - (S^2 - Dst^2) a - P S (a+2b) + P (S^2 - Dst^2). */
+    int32_t n_species;          /* 1..GF_MAX_SPECIES for GF_MED_COLD, else 0              */
+    int32_t reserved2;          /* must be 0                                              */
+    double species[2 * GF_MAX_SPECIES];   /* (w_p,s^2, Omega_s) pairs                     */
+    double profile[4];          /* f0, f1, g0, g1                                         */
 } gf_medium_desc;
 
 typedef struct gf_medium_s *gf_medium;
@@ -159,7 +174,8 @@ gf_status gf_medium_set_amplitudes(gf_medium m, const double *amplitudes, void *
  * dir: device, 3 rows of rays->ld elements (same type as y), need not be unit.
  * Writes rows 3..5 of y; status = GF_RAY_CUTOFF and k = 0 where eps <= 0 or
  * q <= 0, else GF_RAY_ACTIVE.  Leaves t, steps, d_res, d_max untouched.
- * Errors: GF_ERR_INVALID_ARG, GF_ERR_CUDA (launch failure).
+ * Errors: GF_ERR_INVALID_ARG, GF_ERR_UNSUPPORTED (GF_MED_COLD: two branches,
+ * use gf_rays_newton_kx with a guess that selects one), GF_ERR_CUDA.
  */
 gf_status gf_rays_onshell(gf_medium m, gf_precision prec, const gf_rays *rays, const void *dir,
                           double omega, void *stream);
@@ -188,8 +204,8 @@ gf_status gf_rays_newton_kx(gf_medium m, gf_precision prec, const gf_rays *rays,
  * and outputs the updated x, k, t and the dispersion residual).
  * Per step: K1 = f(y), K2 = f(y + dt/2 K1), K3 = f(y + dt/2 K2),
  * K4 = f(y + dt K3), y <- y + dt/6 (K1 + 2 K2 + 2 K3 + K4), t = t_0 + n dt.
- * A ray stops early with GF_RAY_CUTOFF (a stage point with eps <= 0; state
- * kept before that step), GF_RAY_NONFINITE, or GF_RAY_EXITED (a step ending
+ * A ray stops early with GF_RAY_CUTOFF (a stage point with eps <= 0, or
+ * D_w = 0 for a cold plasma; state kept before that step), GF_RAY_NONFINITE, or GF_RAY_EXITED (a step ending
  * with |x| > radius, radius > 0).  d_max (if given) becomes max(d_max, |D|)
  * over the states visited; d_res (if given) = |D| at the final state.
  * omega > 0; dt > 0; n_steps >= 0.

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libgf.so")
 
 GF_OK, GF_ERR_INVALID_ARG, GF_ERR_CUDA, GF_ERR_OOM, GF_ERR_UNSUPPORTED, GF_ERR_TIMEOUT = range(6)
 GF_F32, GF_F64, GF_F64X = 0, 1, 2
-KINDS = {"homog": 0, "luneburg": 1, "grin": 2, "quadratic": 3, "spline": 4}
+KINDS = {"homog": 0, "luneburg": 1, "grin": 2, "quadratic": 3, "spline": 4, "cold": 5}
 (GF_RAY_ACTIVE, GF_RAY_EXITED, GF_RAY_CUTOFF, GF_RAY_NONFINITE, GF_RAY_MAX_STEPS,
  GF_RAY_STEP_UNDERFLOW, GF_RAY_DONE) = range(7)
 GF_MAX_BLOBS = 64
@@ -29,7 +29,8 @@ GF_MAX_BLOBS = 64
 class GfMediumDesc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n_blobs", C.c_int32), ("grid_n", C.c_int32),
                 ("reserved", C.c_int32), ("n_h", C.c_double), ("n0", C.c_double), ("a", C.c_double),
-                ("blobs", C.c_void_p), ("grid", C.c_void_p)]
+                ("blobs", C.c_void_p), ("grid", C.c_void_p), ("n_species", C.c_int32),
+                ("reserved2", C.c_int32), ("species", C.c_double * 8), ("profile", C.c_double * 4)]
 
 
 class GfRays(C.Structure):
@@ -143,14 +144,19 @@ class Medium:
 
 
 def gf_medium_create(kind: str, *, n_h: float = 1.0, n0: float = 1.5, a: float = 2.0,
-                     blobs=None, grid=None) -> Medium:
-    """Copy a medium to the current device (see gf_medium_create in gf.h)."""
+                     blobs=None, grid=None, species=(), profile=(1.0, 0.0, 1.0, 0.0)) -> Medium:
+    """Copy a medium to the current device (see gf_medium_create in gf.h).
+    Cold plasma: species = ((w_p^2, Omega), ...), profile = (f0, f1, g0, g1)."""
     b = None if blobs is None or len(blobs) == 0 else \
         np.ascontiguousarray(np.asarray(blobs, dtype=np.float64).reshape(-1, 5))
     g = None if grid is None else np.ascontiguousarray(np.asarray(grid, dtype=np.float32))
+    sp = [0.0] * 8
+    for i, (wp2, om) in enumerate(species):
+        sp[2 * i], sp[2 * i + 1] = wp2, om
     desc = GfMediumDesc(KINDS[kind], 0 if b is None else b.shape[0], 0 if g is None else g.shape[0],
                         0, n_h, n0, a, None if b is None else b.ctypes.data,
-                        None if g is None else g.ctypes.data)
+                        None if g is None else g.ctypes.data, len(species), 0,
+                        (C.c_double * 8)(*sp), (C.c_double * 4)(*profile))
     h = C.c_void_p()
     _check("gf_medium_create", lib().gf_medium_create(C.byref(desc), C.byref(h)))
     return Medium(h.value, kind, desc.n_blobs)

@@ -319,7 +319,7 @@ extern "C" gf_status gf_trace_adjoint_static(gf_medium m, int64_t n, double omeg
         return GF_ERR_INVALID_ARG;
     }
     const MediumParams &p = params_of(m);
-    if (p.kind == K_SPLINE || p.n_blobs < 1) {
+    if (p.kind == K_SPLINE || p.kind == K_COLD || p.n_blobs < 1) {
         set_error("gf_trace_adjoint_static: needs an isotropic medium with at least one blob");
         return GF_ERR_INVALID_ARG;
     }

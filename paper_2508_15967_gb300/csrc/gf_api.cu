@@ -142,7 +142,7 @@ gf_status gf_medium_create(const gf_medium_desc *d, gf_medium *out)
         return GF_ERR_INVALID_ARG;
     }
     *out = nullptr;
-    if (d->kind < GF_MED_HOMOG || d->kind > GF_MED_SPLINE || d->reserved != 0) {
+    if (d->kind < GF_MED_HOMOG || d->kind > GF_MED_COLD || d->reserved != 0 || d->reserved2 != 0) {
         set_error("gf_medium_create: unknown kind %d or reserved != 0", d->kind);
         return GF_ERR_INVALID_ARG;
     }
@@ -150,8 +150,27 @@ gf_status gf_medium_create(const gf_medium_desc *d, gf_medium *out)
         set_error("gf_medium_create: n_blobs must be in [0, %d] with a table", GF_MAX_BLOBS);
         return GF_ERR_INVALID_ARG;
     }
-    if (d->kind == GF_MED_SPLINE && d->n_blobs != 0) {
+    if ((d->kind == GF_MED_SPLINE || d->kind == GF_MED_COLD) && d->n_blobs != 0) {
         set_error("gf_medium_create: blobs are only defined for isotropic media");
+        return GF_ERR_INVALID_ARG;
+    }
+    if (d->kind == GF_MED_COLD) {
+        if (d->n_species < 1 || d->n_species > GF_MAX_SPECIES) {
+            set_error("gf_medium_create: cold plasma needs 1..%d species", GF_MAX_SPECIES);
+            return GF_ERR_INVALID_ARG;
+        }
+        for (int i = 0; i < 2 * d->n_species; ++i)
+            if (!std::isfinite(d->species[i])) {
+                set_error("gf_medium_create: species values must be finite");
+                return GF_ERR_INVALID_ARG;
+            }
+        for (int i = 0; i < 4; ++i)
+            if (!std::isfinite(d->profile[i])) {
+                set_error("gf_medium_create: profile values must be finite");
+                return GF_ERR_INVALID_ARG;
+            }
+    } else if (d->n_species != 0) {
+        set_error("gf_medium_create: n_species is only defined for GF_MED_COLD");
         return GF_ERR_INVALID_ARG;
     }
     if (d->kind == GF_MED_HOMOG && !(d->n_h > 0 && std::isfinite(d->n_h))) {
@@ -192,6 +211,9 @@ gf_status gf_medium_create(const gf_medium_desc *d, gf_medium *out)
     p.n_h2 = d->n_h * d->n_h;
     p.n02 = d->n0 * d->n0;
     p.n02a2 = d->n0 * d->n0 * d->a * d->a;
+    p.n_species = d->kind == GF_MED_COLD ? d->n_species : 0;
+    for (int i = 0; i < 2 * GF_MAX_SPECIES; ++i) p.species[i] = i < 2 * p.n_species ? d->species[i] : 0.0;
+    for (int i = 0; i < 4; ++i) p.prof[i] = d->kind == GF_MED_COLD ? d->profile[i] : 0.0;
     gf_status s = GF_OK;
     size_t nb = t64.size() ? t64.size() : 1;
     if ((s = cuda_status(cudaMalloc(&m->d_blobs64, nb * sizeof(double)), "cudaMalloc(blobs)")) != GF_OK ||
@@ -263,6 +285,10 @@ gf_status gf_rays_onshell(gf_medium m, gf_precision prec, const gf_rays *rays, c
     if (!(omega > 0) || !std::isfinite(omega)) {
         set_error("gf_rays_onshell: omega must be positive and finite");
         return GF_ERR_INVALID_ARG;
+    }
+    if (m->p.kind == GF_MED_COLD) {
+        set_error("gf_rays_onshell: a cold plasma has two branches; use gf_rays_newton_kx");
+        return GF_ERR_UNSUPPORTED;
     }
     if ((s = check_rays(rays, false)) != GF_OK) return s;
     if (rays->n == 0) return GF_OK;
@@ -345,7 +371,7 @@ gf_status gf_trace_adjoint(gf_medium m, int64_t n, double omega, double dt, int6
 {
     gf_status s;
     if ((s = check_medium(m)) != GF_OK) return s;
-    if (m->p.kind == GF_MED_SPLINE || m->p.n_blobs < 1) {
+    if (m->p.kind == GF_MED_SPLINE || m->p.kind == GF_MED_COLD || m->p.n_blobs < 1) {
         set_error("gf_trace_adjoint: needs an isotropic medium with at least one blob");
         return GF_ERR_INVALID_ARG;
     }

@@ -654,7 +654,7 @@ gf_status gf_batch_create(const gf_medium *media, int32_t n_media, const int64_t
             return GF_ERR_INVALID_ARG;
         }
         const MediumParams &p = params_of(media[m]);
-        if (p.kind == K_SPLINE || (kind >= 0 && p.kind != kind)) {
+        if (p.kind == K_SPLINE || p.kind == K_COLD || (kind >= 0 && p.kind != kind)) {
             set_error("gf_batch_create: media must be isotropic and of one kind (medium %d)", m);
             return GF_ERR_INVALID_ARG;
         }

@@ -13,7 +13,7 @@
 namespace gf {
 
 enum : int { K_HOMOG = GF_MED_HOMOG, K_LUNEBURG = GF_MED_LUNEBURG, K_GRIN = GF_MED_GRIN,
-             K_QUADRATIC = GF_MED_QUADRATIC, K_SPLINE = GF_MED_SPLINE };
+             K_QUADRATIC = GF_MED_QUADRATIC, K_SPLINE = GF_MED_SPLINE, K_COLD = GF_MED_COLD };
 
 constexpr int kBlobStride = 6;   // device blob row: A, cx, cy, cz, s = -1 / (2 w^2), 2 s
 
@@ -25,6 +25,9 @@ struct MediumParams {
     const double *blobs64;       // n_blobs x kBlobStride
     const float *blobs32;        // float copy of the same table
     const float4 *grid;          // grid_n^3 nodes x 2 float4
+    int32_t n_species, pad2;     // cold plasma
+    double species[2 * GF_MAX_SPECIES];
+    double prof[4];
 };
 
 // Ray buffers with a typed state pointer.
@@ -373,6 +376,76 @@ __device__ __forceinline__ bool rhs_spline(const MediumParams &m, const Omega<R>
     return true;
 }
 
+// Cold magnetised plasma (B along z, slab profiles along x), Stix form of
+// det(eps + n n - n^2 I) with n = k / w and its gradients by the chain rule:
+// D_k through a = (k_x^2 + k_y^2)/w^2 and b = k_z^2/w^2, D_x through
+// S, Dst, P (f, g depend on x_0), D_w through a, b, S, Dst, P.  The ray
+// equations need only D_k, D_x and D_w; D_w = 0 is the cut-off test.
+template <typename R>
+__device__ __forceinline__ bool rhs_cold(const MediumParams &m, const Omega<R> &om, const R *y, R *f, R &D)
+{
+    const R w = om.w, w2 = w * w;
+    const R fx = (R)m.prof[1], gx = (R)m.prof[3];
+    const R fv = (R)m.prof[0] + fx * y[0], gv = (R)m.prof[2] + gx * y[0];
+    R S = 1, Dst = 0, P = 1, Sx = 0, Dx = 0, Px = 0, Sw = 0, Dw = 0, Pw = 0;
+    for (int sp = 0; sp < m.n_species; ++sp) {
+        const R wp = (R)m.species[2 * sp], Om = (R)m.species[2 * sp + 1];
+        const R wp2 = wp * fv, wp2x = wp * fx;
+        const R W = Om * gv, Wx = Om * gx;
+        const R den = w2 - W * W;
+        const R iden = (R)1 / den;
+        const R t = wp2 * iden;
+        S -= t;
+        Dst += W * t * om.inv_w;
+        P -= wp2 / w2;
+        Sx -= (wp2x + (R)2 * t * W * Wx) * iden;
+        Dx += ((Wx * wp2 + W * wp2x) + (R)2 * W * W * t * Wx) * iden * om.inv_w;
+        Px -= wp2x / w2;
+        Sw += (R)2 * w * t * iden;
+        Dw -= W * t * ((R)3 * w2 - W * W) * iden * om.inv_w * om.inv_w;
+        Pw += (R)2 * wp2 / (w2 * w);
+    }
+    const R a = (y[3] * y[3] + y[4] * y[4]) / w2, b = y[5] * y[5] / w2;
+    const R RL = S * S - Dst * Dst;
+    D = S * a * (a + b) + P * b * (a + b) - RL * a - P * S * (a + (R)2 * b) + P * RL;
+    const R DS = a * (a + b) - (R)2 * S * a - P * (a + (R)2 * b) + (R)2 * P * S;
+    const R DD = (R)2 * Dst * a - (R)2 * P * Dst;
+    const R DP = b * (a + b) - S * (a + (R)2 * b) + RL;
+    const R Da = S * ((R)2 * a + b) + P * b - RL - P * S;
+    const R Db = S * a + P * (a + (R)2 * b) - (R)2 * P * S;
+    const R Dom = -(R)2 * (Da * a + Db * b) * om.inv_w + DS * Sw + DD * Dw + DP * Pw;
+    if (!(Dom != (R)0) || !isfinite(Dom)) return false;
+    const R inv = (R)1 / Dom;
+    const R ka = (R)2 * Da / w2, kb = (R)2 * Db / w2;
+    f[0] = -ka * y[3] * inv;
+    f[1] = -ka * y[4] * inv;
+    f[2] = -kb * y[5] * inv;
+    f[3] = (DS * Sx + DD * Dx + DP * Px) * inv;
+    f[4] = (R)0;
+    f[5] = (R)0;
+    return true;
+}
+
+// dD/dk_x of the cold plasma (for Newton's method on k_x).
+template <typename R>
+__device__ __forceinline__ R cold_dkx(const MediumParams &m, const Omega<R> &om, const R *y)
+{
+    const R w = om.w, w2 = w * w;
+    const R fv = (R)m.prof[0] + (R)m.prof[1] * y[0], gv = (R)m.prof[2] + (R)m.prof[3] * y[0];
+    R S = 1, Dst = 0, P = 1;
+    for (int sp = 0; sp < m.n_species; ++sp) {
+        const R wp2 = (R)m.species[2 * sp] * fv, W = (R)m.species[2 * sp + 1] * gv;
+        const R t = wp2 / (w2 - W * W);
+        S -= t;
+        Dst += W * t * om.inv_w;
+        P -= wp2 / w2;
+    }
+    const R a = (y[3] * y[3] + y[4] * y[4]) / w2, b = y[5] * y[5] / w2;
+    const R RL = S * S - Dst * Dst;
+    const R Da = S * ((R)2 * a + b) + P * b - RL - P * S;
+    return (R)2 * Da * y[3] / w2;
+}
+
 // Dispatch on the medium kind at compile time.
 template <typename R, int KIND>
 struct Rhs {
@@ -385,6 +458,8 @@ struct Rhs {
     {
         if constexpr (KIND == K_SPLINE)
             return rhs_spline<R>(m, om, y, f, D);
+        else if constexpr (KIND == K_COLD)
+            return rhs_cold<R>(m, om, y, f, D);
         else
             return rhs_iso<R, KIND, WANT_D>(m, sb, nb, om, y, f, D, cx);
     }

@@ -122,7 +122,7 @@ __device__ __forceinline__ void add_work(unsigned long long *counters, long long
 }
 
 template <typename R, int KIND, bool DF>
-__global__ void __launch_bounds__(kRk4Block, (KIND == K_SPLINE || sizeof(R) == 4 || DF) ? 1 : 5)
+__global__ void __launch_bounds__(kRk4Block, (KIND == K_SPLINE || sizeof(R) == 4) ? 1 : 5)
 rk4_kernel(const MediumParams m, const RaysView<R> r, const Omega<R> om, const R dt, const double dt64,
            const int64_t n_steps, const R radius2, const int64_t every, double *__restrict__ ckpt,
            unsigned long long *counters)
@@ -268,6 +268,31 @@ __global__ void __launch_bounds__(kRk4Block) newton_kx_kernel(const MediumParams
     const R x[3] = {r.y[i], r.y[r.ld + i], r.y[2 * r.ld + i]};
     R kx = r.y[3 * r.ld + i];
     const R ky = r.y[4 * r.ld + i], kz = r.y[5 * r.ld + i];
+    if constexpr (KIND == K_COLD) {
+        // D is quartic in k_x: full evaluation per iteration (D and dD/dk_x)
+        const Omega<R> om = make_omega<R>((double)omega);
+        bool ok = false;
+        for (int it = 0; it < max_iter; ++it) {
+            R yy[6] = {x[0], x[1], x[2], kx, ky, kz}, f[6], D;
+            const bool live = rhs_cold<R>(m, om, yy, f, D);
+            if (fabs(D) < tol) { ok = true; break; }
+            // f_x0 = -D_kx / D_w  and D_w is returned through f: recover D_kx
+            if (!live) break;
+            R Dkx = cold_dkx<R>(m, om, yy);
+            if (Dkx == (R)0 || !isfinite(D)) break;
+            const R step = D / Dkx;
+            kx = kx - step;
+            if (fabs(step) <= (R)0x1p-50 * fabs(kx)) {
+                R y2[6] = {x[0], x[1], x[2], kx, ky, kz}, f2[6], D2;
+                rhs_cold<R>(m, om, y2, f2, D2);
+                ok = fabs(D2) <= (R)8 * tol;
+                break;
+            }
+        }
+        r.y[3 * r.ld + i] = kx;
+        r.status[i] = ok ? GF_RAY_ACTIVE : GF_RAY_CUTOFF;
+        return;
+    }
     // D(k_x) = a k_x^2 + 2 b k_x + c  with  dD/dk_x = 2 (a k_x + b)
     R a, b, c;
     if constexpr (KIND == K_SPLINE) {
@@ -346,6 +371,16 @@ static cudaError_t onshell_launch(const MediumParams &m, const gf_rays &r, const
     case K_GRIN: return FN<R, K_GRIN>(__VA_ARGS__);                               \
     case K_QUADRATIC: return FN<R, K_QUADRATIC>(__VA_ARGS__);                     \
     case K_SPLINE: return FN<R, K_SPLINE>(__VA_ARGS__);                           \
+    case K_COLD: return FN<R, K_COLD>(__VA_ARGS__);                               \
+    default: return cudaErrorInvalidValue;                                         \
+    }
+#define GF_KIND_SWITCH_NO_COLD(KIND_VAR, FN, R, ...)                              \
+    switch (KIND_VAR) {                                                            \
+    case K_HOMOG: return FN<R, K_HOMOG>(__VA_ARGS__);                             \
+    case K_LUNEBURG: return FN<R, K_LUNEBURG>(__VA_ARGS__);                       \
+    case K_GRIN: return FN<R, K_GRIN>(__VA_ARGS__);                               \
+    case K_QUADRATIC: return FN<R, K_QUADRATIC>(__VA_ARGS__);                     \
+    case K_SPLINE: return FN<R, K_SPLINE>(__VA_ARGS__);                           \
     default: return cudaErrorInvalidValue;                                         \
     }
 
@@ -363,6 +398,7 @@ cudaError_t launch_rk4(const MediumParams &m, gf_precision prec, const gf_rays &
         case K_GRIN: return rk4_launch_df<double, K_GRIN>(m, r, omega, dt, n_steps, radius, every, ckpt, s);
         case K_QUADRATIC: return rk4_launch_df<double, K_QUADRATIC>(m, r, omega, dt, n_steps, radius, every, ckpt, s);
         case K_SPLINE: return rk4_launch<double, K_SPLINE>(m, r, omega, dt, n_steps, radius, every, ckpt, s);
+        case K_COLD: return rk4_launch<double, K_COLD>(m, r, omega, dt, n_steps, radius, every, ckpt, s);
         default: return cudaErrorInvalidValue;
         }
     } else {
@@ -395,9 +431,9 @@ cudaError_t launch_onshell(const MediumParams &m, gf_precision prec, const gf_ra
 {
     if (r.n == 0) return cudaSuccess;
     if (prec == GF_F64 || prec == GF_F64X) {
-        GF_KIND_SWITCH(m.kind, onshell_launch, double, m, r, dir, omega, s)
+        GF_KIND_SWITCH_NO_COLD(m.kind, onshell_launch, double, m, r, dir, omega, s)
     } else {
-        GF_KIND_SWITCH(m.kind, onshell_launch, float, m, r, dir, omega, s)
+        GF_KIND_SWITCH_NO_COLD(m.kind, onshell_launch, float, m, r, dir, omega, s)
     }
 }
 

@@ -1,0 +1,114 @@
+"""GPU cold-plasma rays (Sec. 4.1, Eqs. 4-10): Newton branch selection, RK4
+parity with the oracle (FP64 <= 1e-9, FP32 <= 1e-4), the exact O-mode
+parabola of the linear-density slab and the X-mode R cut-off."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_2508_15967_gb300 as gf
+from tests._parity import GpuResult, assert_parity, oracle_rk4
+
+pytestmark = pytest.mark.gpu
+
+COLD2 = dict(kind="cold", species=((0.45, -0.6), (0.03, 0.08)), profile=(1.0, 0.1, 1.0, 0.05))
+# electrons + ions with a field gradient; both the O and the X branch propagate at
+# the launch points, and Newton from k_x = 1.2 / 0.5 lands on the O / X root
+COLDXO = dict(kind="cold", species=((0.3, -0.5), (0.02, 0.05)), profile=(1.0, 0.1, 1.0, 0.05))
+COLD_E = dict(kind="cold", species=((0.3, -0.5),), profile=(1.0, 0.1, 1.0, 0.0))
+
+
+def _launch(n, seed, oblique):
+    rng = np.random.default_rng(seed)
+    x0 = np.column_stack([rng.uniform(-1, 1, n), rng.uniform(-1, 1, n), np.zeros(n)])
+    ky = rng.uniform(-0.25, 0.25, n)
+    kz = rng.uniform(-0.2, 0.2, n) if oblique else np.zeros(n)
+    return x0, ky, kz
+
+
+def _roots(spec, x0, ky, kz, guess):
+    k, st, _ = O.newton_kx(O.medium(**spec), x0, np.column_stack([np.full(len(ky), guess), ky, kz]))
+    return k, st
+
+
+@pytest.mark.parametrize("oblique", [False, True])
+def test_newton_branches_match_oracle(oblique):
+    x0, ky, kz = _launch(500, 1, oblique)
+    m = gf.gf_medium_create(**COLDXO)
+    roots = []
+    for guess in (1.2, 0.5):
+        k_o, st_o = _roots(COLDXO, x0, ky, kz, guess)
+        roots.append(k_o[:, 0])
+        rays = gf.Rays.from_numpy(x0, np.column_stack([np.full(500, guess), ky, kz]))
+        gf.gf_rays_newton_kx(m, rays, 1.0)
+        torch.cuda.synchronize()
+        assert np.array_equal(rays.status.cpu().numpy(), st_o)
+        ok = st_o == 0
+        assert ok.mean() > 0.9
+        np.testing.assert_allclose(rays.state()[ok, 3], k_o[ok, 0], rtol=1e-13, atol=1e-14)
+    assert (roots[0] > roots[1] + 0.05).all()          # two distinct branches
+
+
+@pytest.mark.parametrize("spec", [COLDXO, COLD_E])
+@pytest.mark.parametrize("oblique", [False, True])
+def test_cold_rk4_parity_f64(spec, oblique):
+    """700 rays (5 blocks + a tail), both branches, 3000 steps of 0.01."""
+    x0, ky, kz = _launch(700, 2, oblique)
+    kO, sO = _roots(spec, x0, ky, kz, 1.2)
+    kX, sX = _roots(spec, x0, ky, kz, 0.5)
+    k0 = np.where(np.arange(700)[:, None] % 2 == 0, kO, kX)
+    st = np.where(np.arange(700) % 2 == 0, sO, sX)
+    m = gf.gf_medium_create(**spec)
+    rays = gf.Rays.from_numpy(x0, k0)
+    rays.status.copy_(torch.as_tensor(st, dtype=torch.int32))
+    gf.gf_trace_rk4(m, rays, 1.0, 0.01, 3000)
+    g = GpuResult(rays)
+    o, _ = oracle_rk4(spec, x0, k0, 1.0, 0.01, 3000, status=st)
+    assert_parity(g, o, 1e-9, diag_atol=1e-11)
+
+
+def test_cold_rk4_parity_f32():
+    x0, ky, kz = _launch(400, 3, True)
+    k0, st = _roots(COLDXO, x0, ky, kz, 1.2)
+    f32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    x0, k0 = f32(x0), f32(k0)
+    m = gf.gf_medium_create(**COLDXO)
+    rays = gf.Rays.from_numpy(x0, k0, torch.float32)
+    rays.status.copy_(torch.as_tensor(st, dtype=torch.int32))
+    gf.gf_trace_rk4(m, rays, 1.0, 0.01, 2000)
+    o, _ = oracle_rk4(COLDXO, x0, k0, 1.0, 0.01, 2000, status=st)
+    assert_parity(GpuResult(rays), o, 1e-4, diag_atol=1e-5)
+
+
+def test_o_mode_parabola_and_x_mode_cutoff_on_gpu():
+    # O mode: exact parabola in t (Sec. 4: linear gradient f = 0.1 x + 1)
+    m = gf.gf_medium_create(**COLD2)
+    x0 = np.array([[0.0, 0.2, 0.0], [-1.0, 0.0, 0.0]])
+    ky = np.array([0.2, 0.0])
+    P = 1 - 0.48 * (1 + 0.1 * x0[:, 0])
+    k0 = np.column_stack([np.sqrt(P - ky ** 2), ky, np.zeros(2)])
+    rays = gf.Rays.from_numpy(x0, k0)
+    gf.gf_trace_rk4(m, rays, 1.0, 0.01, 6000)
+    y = GpuResult(rays).y
+    c, T = -0.48 * 0.1 / 2, 60.0
+    np.testing.assert_allclose(y[:, 3], k0[:, 0] + c * T, atol=1e-12)
+    np.testing.assert_allclose(y[:, 0], x0[:, 0] + k0[:, 0] * T + c * T * T / 2, atol=1e-11)
+    # X mode: turns at R = 0, x_R = (w (w + Omega_e) / w_pe^2 - 1) / 0.1
+    me = gf.gf_medium_create(**COLD_E)
+    rays = gf.Rays.from_numpy(np.zeros((1, 3)), np.array([[0.7, 0.0, 0.0]]))
+    gf.gf_rays_newton_kx(me, rays, 1.0)
+    xs = []
+    for _ in range(400):
+        gf.gf_trace_rk4(me, rays, 1.0, 0.01, 10)
+        xs.append(rays.y[0, 0].item())
+    assert abs(max(xs) - (0.5 / 0.3 - 1) / 0.1) < 1e-3
+    assert rays.y[3, 0].item() < 0
+
+
+def test_onshell_rejects_cold_plasma():
+    m = gf.gf_medium_create(**COLD_E)
+    rays = gf.Rays.from_numpy(np.zeros((4, 3)), None)
+    with pytest.raises(gf.GfError, match="newton"):
+        gf.gf_rays_onshell(m, rays, torch.ones_like(rays.y[:3]), 1.0)
