@@ -221,6 +221,58 @@ def measure_batched(gf, torch, tune_cache: str | None = None) -> dict:
                      "compaction": tune.compaction, "chunk": tune.chunk, "seconds": tune_s}}
 
 
+# FP64 flops of one evaluation of the separable tricubic spline medium:
+# 16 (y, z) rows x (4 nodes x 7 channels x 2 fma for value and d/dx, then
+# 7 channels x 4 fma into value and the three gradients) = 1344 fma, weights
+# of three axes (~60 flops), D and the right-hand side (~60 flops).
+FLOPS_SPLINE_EVAL = 2 * 1344 + 60 + 60
+
+
+def measure_aniso(gf, torch, peak_tflops: float) -> dict:
+    """Anisotropic tricubic B-spline workload (262,144 rays, 128^3 grid, RK4
+    dt = 1e-3 x 4000, FP64), one warm-up trace of 100 steps then one timed."""
+    wl = W.aniso()
+    m = gf.gf_medium_create(**wl.medium)
+    init = gf.Rays.from_numpy(wl.x0, None)
+    gf.gf_rays_onshell(m, init, torch.from_numpy(np.ascontiguousarray(wl.d.T)).cuda(), 1.0)
+    rays = init.clone()
+    gf.gf_trace_rk4(m, rays, 1.0, wl.dt, 100)
+    rays = init.clone()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    gf.gf_trace_rk4(m, rays, 1.0, wl.dt, wl.n_steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    units = int(rays.steps.to(torch.int64).sum().item())
+    flops = (4 * units + wl.n) * FLOPS_SPLINE_EVAL
+    return {"workload": f"{wl.n} rays, 128^3 tricubic spline grid (64 MiB FP32), RK4 dt=1e-3 x {wl.n_steps}, FP64",
+            "ms": ms, "ray_steps_per_s": units / (ms / 1e3),
+            "achieved_tflops": flops / (ms / 1e3) / 1e12, "frac_fp64_peak": flops / (ms / 1e3) / 1e12 / peak_tflops,
+            "max_abs_D": rays.d_max.max().item()}
+
+
+def measure_f64x(gf, torch, wl, m, x0, dirs, rays) -> dict:
+    """The headline workload in the GF_F64X mode (double state and integrator,
+    double-float blob sums), one warm-up and one timed trace."""
+    ms = []
+    for _ in range(2):
+        rays.y[:3].copy_(x0)
+        for t in (rays.t, rays.status, rays.steps, rays.d_max):
+            t.zero_()
+        gf.gf_rays_onshell(m, rays, dirs, wl.omega)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        gf.gf_trace_rk4(m, rays, wl.omega, wl.dt, wl.n_steps, precision=gf.GF_F64X)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    units = int(rays.steps.to(torch.int64).sum().item())
+    return {"ray_steps_per_s": units / (ms[-1] / 1e3), "ms": ms[-1], "max_abs_D": rays.d_max.max().item(),
+            "dtype": "f64 state and integrator, f32x2 (double-float) blob sums",
+            "parity": "<= 1e-9 relative to the FP64 oracle in tests/test_gpu_f64x.py"}
+
+
 def measure_adjoint(gf, torch) -> dict:
     """Adjoint workload (65,536 rays, Luneburg + 64 blobs, RK4 dt 1e-3 x 4000,
     checkpoints every 64): forward with checkpoints and backward through the
@@ -402,6 +454,9 @@ def run_gpu(a):
         "clocks": clk, "gpu_launches": 2 * a.steps, "e2e": e2e, "wall_s": wall,
     }
     if world == 1 and not a.no_extras:
+        if a.precision == "f64":
+            line["f64x"] = measure_f64x(gf, torch, wl, m, x0, dirs, rays)
+        line["aniso"] = measure_aniso(gf, torch, peak)
         line["adjoint"] = measure_adjoint(gf, torch)
         line["batched"] = measure_batched(gf, torch)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
