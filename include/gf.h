@@ -223,6 +223,36 @@ gf_status gf_trace_rk4(gf_medium m, gf_precision prec, const gf_rays *rays, doub
                        double dt, int64_t n_steps, double radius, int64_t checkpoint_every,
                        double *ckpt, void *stream);
 
+/* ------------------------------------------------------- generated media */
+
+/*
+ * gf_jit_medium_create -- compile a generated dispersion relation into an RK4
+ * ray kernel at run time and wrap it as a medium for gf_trace_rk4.
+ * Paper: expression graphs of D are differentiated and simplified
+ * symbolically, then emitted as kernel source -- one register per node, each
+ * shared sub-graph once -- and JIT-compiled for the device (Sec. 2.1-2.2);
+ * the RK4 ray update is one fused kernel (Sec. 4).
+ * source: CUDA C defining
+ *   __device__ void gf_user_dispersion(const double *y, double w, double *out)
+ * with y = (x0, x1, x2, k0, k1, k2) and out[0..7] = (D, D_x0, D_x1, D_x2,
+ * D_k0, D_k1, D_k2, D_w) (the symbolic front end writes it).  It is compiled
+ * with NVRTC (loaded on first use) for the current device (sm_103a on GB300)
+ * together with the library's RK4 kernel; the right-hand side is the generic
+ * f = (-D_k / D_w, D_x / D_w) and a ray stops with GF_RAY_CUTOFF where D_w = 0
+ * or is not finite.  Such a medium runs in gf_trace_rk4 with GF_F64 only,
+ * without checkpoints; destroy it with gf_medium_destroy.  Synchronous.
+ * Errors: GF_ERR_INVALID_ARG (the source does not compile; the compiler log
+ * is in gf_last_error), GF_ERR_UNSUPPORTED (NVRTC not available), GF_ERR_CUDA.
+ */
+gf_status gf_jit_medium_create(const char *source, gf_medium *out);
+
+/*
+ * gf_jit_compile_check -- compile generated source for `arch` (e.g. "sm_103a")
+ * without loading it (no device needed); the NVRTC log is copied to `log`
+ * (may be NULL, truncated to log_size).  Errors as gf_jit_medium_create.
+ */
+gf_status gf_jit_compile_check(const char *source, const char *arch, char *log, size_t log_size);
+
 /* ------------------------------------------------------------------ adjoint */
 
 /*

@@ -91,6 +91,8 @@ def lib() -> C.CDLL:
             "gf_adjoint_scratch_bytes": ([P, I64, I64], C.c_size_t),
             "gf_trace_adjoint": ([P, I64, D, D, I64, I64, P, P, P, I64, P, P, P, C.c_size_t, P], I32),
             "gf_trace_adjoint_static": ([P, I64, D, D, I64, I64, P, P, P, I64, P, P, P], I32),
+            "gf_jit_medium_create": ([C.c_char_p, P], I32),
+            "gf_jit_compile_check": ([C.c_char_p, C.c_char_p, C.c_char_p, C.c_size_t], I32),
             "gf_batch_create": ([P, I32, P, P], I32),
             "gf_batch_destroy": ([P], I32),
             "gf_trace_dopri5": ([P, P, P, D, P, I32, P, P], I32),
@@ -160,6 +162,20 @@ def gf_medium_create(kind: str, *, n_h: float = 1.0, n0: float = 1.5, a: float =
     h = C.c_void_p()
     _check("gf_medium_create", lib().gf_medium_create(C.byref(desc), C.byref(h)))
     return Medium(h.value, kind, desc.n_blobs)
+
+
+def gf_jit_medium_create(source: str) -> Medium:
+    """Compile generated CUDA source of gf_user_dispersion into an RK4 medium (see gf.h)."""
+    h = C.c_void_p()
+    _check("gf_jit_medium_create", lib().gf_jit_medium_create(source.encode(), C.byref(h)))
+    return Medium(h.value, "generated", 0)
+
+
+def gf_jit_compile_check(source: str, arch: str = "sm_103a") -> tuple[int, str]:
+    """(status, compiler log) of compiling generated source without loading it."""
+    buf = C.create_string_buffer(1 << 16)
+    st = lib().gf_jit_compile_check(source.encode(), arch.encode(), buf, len(buf))
+    return st, buf.value.decode(errors="replace")
 
 
 def gf_medium_destroy(m: Medium) -> None:

@@ -72,7 +72,7 @@ def build(force: bool = False, ptxas_info: bool = False, verbose: bool = False) 
             if log:
                 sys.stderr.write(log)
     tmp = LIB + ".tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *[o for o, _ in results]]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-ldl"]
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError(f"link of libgf.so failed:\n{p.stderr}")

@@ -2,9 +2,9 @@
 
 Method: P. T. P. Tang, "Table-driven implementation of the exponential
 function in IEEE floating-point arithmetic", ACM TOMS 15 (1989) 144-157, with
-a 64-entry table and Cody-Waite two-constant argument reduction (W. J. Cody
+a 256-entry table and Cody-Waite two-constant argument reduction (W. J. Cody
 and W. Waite, Software Manual for the Elementary Functions, 1980):
-    a = (64 m + j) ln2/64 + r,  exp(a) = 2^m * 2^(j/64) * exp(r),  |r| <= ln2/128.
+    a = (256 m + j) ln2/256 + r,  exp(a) = 2^m * 2^(j/256) * exp(r),  |r| <= ln2/512.
 Every value is computed here with 60-digit decimal arithmetic and rounded once
 to the nearest double.  Run: python gen_exp_table.py > gf_exp_table.inc
 """
@@ -34,18 +34,18 @@ def trunc_bits(x: float, bits: int) -> float:
 
 
 def main():
-    L = ln2() / 64
-    hi = trunc_bits(to_double(L), 36)            # |k| < 2^17 for |a| < 709: k*hi exact
+    L = ln2() / 256
+    hi = trunc_bits(to_double(L), 35)            # |k| < 2^18 for |a| < 709: k*hi exact
     lo = to_double(L - Decimal(hi))
-    inv = to_double(64 / ln2())
+    inv = to_double(256 / ln2())
     print("// Generated by gen_exp_table.py -- constants of the table-driven exp")
-    print("// (Tang 1989, 64-entry table; Cody-Waite split of ln2/64).")
-    print(f"constexpr double kInvLn2x64 = {hexf(inv)};   // 64 / ln 2")
-    print(f"constexpr double kLn2By64Hi = {hexf(hi)};   // ln2/64, 36 significant bits")
-    print(f"constexpr double kLn2By64Lo = {hexf(lo)};   // ln2/64 - kLn2By64Hi")
-    print("constexpr double kExp2Tab[64] = {   // 2^(j/64), correctly rounded")
-    for j in range(64):
-        v = to_double((Decimal(j) / 64 * ln2()).exp())
+    print("// (Tang 1989, 256-entry table; Cody-Waite split of ln2/256).")
+    print(f"constexpr double kInvLn2xN = {hexf(inv)};   // 256 / ln 2")
+    print(f"constexpr double kLn2ByNHi = {hexf(hi)};   // ln2/256, 35 significant bits")
+    print(f"constexpr double kLn2ByNLo = {hexf(lo)};   // ln2/256 - kLn2ByNHi")
+    print("constexpr double kExp2Tab[256] = {   // 2^(j/256), correctly rounded")
+    for j in range(256):
+        v = to_double((Decimal(j) / 256 * ln2()).exp())
         print(f"    {hexf(v)},")
     print("};")
 

@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kAdjBlock) adjoint_kernel(
     const double *__restrict__ lambda, const int64_t ld, double *__restrict__ dy0, const AdjScratch S)
 {
     __shared__ double sb[kBlobStride * GF_MAX_BLOBS];
-    __shared__ double sT[64];
+    __shared__ double sT[kExpTabN];
     extern __shared__ double tb[];   // thetabar columns: tb[j * blockDim + tid]
     const int nb = m.n_blobs;
     stage_blobs<double>(m, sb);
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kAdjBlock) adjoint_kernel(
                         const double dx = Y[0] - b[1], dy = Y[1] - b[2], dz = Y[2] - b[3];
                         const double arg = (dx * dx + dy * dy + dz * dz) * b[4];
                         double G = 0.0;   // negligible terms (see kBlobCull) are stored as 0
-                        if (arg >= kBlobCull) {
+                        if (!below_cull(arg)) {
                             G = exp_tang(arg, sT);
                             const double AG = b[0] * G;
                             n2 += AG;

@@ -9,14 +9,6 @@
 
 #include "gf_internal.cuh"
 
-struct gf_medium_s {
-    gf::MediumParams p{};
-    int device = -1;
-    double *d_blobs64 = nullptr;
-    float *d_blobs32 = nullptr;
-    float4 *d_grid = nullptr;
-};
-
 namespace gf {
 
 static thread_local std::string g_err;
@@ -112,6 +104,7 @@ static void free_medium(gf_medium m)
     if (m->d_blobs64) cudaFree(m->d_blobs64);
     if (m->d_blobs32) cudaFree(m->d_blobs32);
     if (m->d_grid) cudaFree(m->d_grid);
+    if (m->jit_lib) cudaLibraryUnload(m->jit_lib);
     delete m;
 }
 
@@ -286,8 +279,8 @@ gf_status gf_rays_onshell(gf_medium m, gf_precision prec, const gf_rays *rays, c
         set_error("gf_rays_onshell: omega must be positive and finite");
         return GF_ERR_INVALID_ARG;
     }
-    if (m->p.kind == GF_MED_COLD) {
-        set_error("gf_rays_onshell: a cold plasma has two branches; use gf_rays_newton_kx");
+    if (m->p.kind == GF_MED_COLD || m->jit_lib != nullptr) {
+        set_error("gf_rays_onshell: not defined for cold-plasma or generated media; use gf_rays_newton_kx");
         return GF_ERR_UNSUPPORTED;
     }
     if ((s = check_rays(rays, false)) != GF_OK) return s;
@@ -312,6 +305,10 @@ gf_status gf_rays_newton_kx(gf_medium m, gf_precision prec, const gf_rays *rays,
         return GF_ERR_INVALID_ARG;
     }
     if ((s = check_rays(rays, false)) != GF_OK) return s;
+    if (m->jit_lib != nullptr) {
+        set_error("gf_rays_newton_kx: not available for generated media");
+        return GF_ERR_UNSUPPORTED;
+    }
     return cuda_status(launch_newton_kx(m->p, prec, *rays, omega, tol, max_iter, (cudaStream_t)stream),
                        "gf_rays_newton_kx launch");
 }
@@ -332,6 +329,14 @@ gf_status gf_trace_rk4(gf_medium m, gf_precision prec, const gf_rays *rays, doub
         return GF_ERR_INVALID_ARG;
     }
     if ((s = check_rays(rays, true)) != GF_OK) return s;
+    if (m->jit_lib != nullptr) {
+        if (prec != GF_F64 || ckpt != nullptr) {
+            set_error("gf_trace_rk4: a generated (JIT) medium runs in GF_F64 without checkpoints");
+            return GF_ERR_UNSUPPORTED;
+        }
+        return cuda_status(launch_rk4_jit(m, *rays, omega, dt, n_steps, radius, (cudaStream_t)stream),
+                           "gf_trace_rk4 (generated medium) launch");
+    }
     if (ckpt != nullptr) {
         if (prec == GF_F32) {
             set_error("gf_trace_rk4: checkpoints are only produced by the FP64 paths");
@@ -371,7 +376,7 @@ gf_status gf_trace_adjoint(gf_medium m, int64_t n, double omega, double dt, int6
 {
     gf_status s;
     if ((s = check_medium(m)) != GF_OK) return s;
-    if (m->p.kind == GF_MED_SPLINE || m->p.kind == GF_MED_COLD || m->p.n_blobs < 1) {
+    if (m->p.kind == GF_MED_SPLINE || m->p.kind == GF_MED_COLD || m->p.n_blobs < 1 || m->jit_lib != nullptr) {
         set_error("gf_trace_adjoint: needs an isotropic medium with at least one blob");
         return GF_ERR_INVALID_ARG;
     }

@@ -63,7 +63,7 @@ __global__ void dfexp_check_kernel(const double *in, double *out, int64_t n)
 
 __global__ void exp_check_kernel(const double *in, double *out_lib, double *out_cuda, int64_t n)
 {
-    __shared__ double sT[64];
+    __shared__ double sT[kExpTabN];
     stage_exp_table(sT);
     __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

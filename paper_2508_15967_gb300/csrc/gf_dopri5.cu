@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(128) dopri5_medium_kernel(const BatchView B, c
                                                             const Ctl c)
 {
     extern __shared__ double sm_dyn[];
-    __shared__ double sT[64];
+    __shared__ double sT[kExpTabN];
     stage_exp_table(sT);
     __syncthreads();
     const int stride = blockDim.x;
@@ -232,7 +232,7 @@ __global__ void dopri5_persistent_kernel(const BatchView B, const RaysView<doubl
                                          const int compaction, int *__restrict__ head)
 {
     extern __shared__ double sm_dyn[];
-    __shared__ double sT[64];
+    __shared__ double sT[kExpTabN];
     stage_exp_table(sT);
     __syncthreads();
     const int stride = blockDim.x * RPT;

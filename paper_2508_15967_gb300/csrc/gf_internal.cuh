@@ -40,6 +40,22 @@ struct RaysView {
     double *d_res, *d_max;
 };
 
+}  // namespace gf
+
+// A device medium: parameters for the built-in kernels, or a generated RK4
+// kernel compiled at run time (jit_lib != nullptr).
+struct gf_medium_s {
+    gf::MediumParams p{};
+    int device = -1;
+    double *d_blobs64 = nullptr;
+    float *d_blobs32 = nullptr;
+    float4 *d_grid = nullptr;
+    cudaLibrary_t jit_lib = nullptr;
+    cudaKernel_t jit_kernel = nullptr;
+};
+
+namespace gf {
+
 // ------------------------------------------------------------------ host side
 
 void set_error(const char *fmt, ...);
@@ -58,6 +74,8 @@ size_t adjoint_scratch_bytes(int nb, int64_t n, int64_t every);
 cudaError_t launch_adjoint(const MediumParams &m, int64_t n, double omega, double dt, int64_t n_steps,
                            int64_t every, const double *ckpt, const int32_t *steps_done, const double *lambda,
                            int64_t ld, double *dtheta, double *dy0, void *scratch, cudaStream_t s);
+cudaError_t launch_rk4_jit(gf_medium m, const gf_rays &r, double omega, double dt, int64_t n_steps,
+                           double radius, cudaStream_t s);
 cudaError_t launch_newton_kx(const MediumParams &m, gf_precision prec, const gf_rays &r, double omega, double tol,
                              int max_iter, cudaStream_t s);
 cudaError_t launch_onshell(const MediumParams &m, gf_precision prec, const gf_rays &r,
@@ -67,51 +85,58 @@ cudaError_t launch_onshell(const MediumParams &m, gf_precision prec, const gf_ra
 
 #include "gf_exp_table.inc"
 
-// 2^(j/64), j = 0..63 (one copy per translation unit; staged into shared memory).
-static __constant__ double c_exp2_tab[64] = {
-#define GF_TAB(i) kExp2Tab[i]
-    GF_TAB(0),  GF_TAB(1),  GF_TAB(2),  GF_TAB(3),  GF_TAB(4),  GF_TAB(5),  GF_TAB(6),  GF_TAB(7),
-    GF_TAB(8),  GF_TAB(9),  GF_TAB(10), GF_TAB(11), GF_TAB(12), GF_TAB(13), GF_TAB(14), GF_TAB(15),
-    GF_TAB(16), GF_TAB(17), GF_TAB(18), GF_TAB(19), GF_TAB(20), GF_TAB(21), GF_TAB(22), GF_TAB(23),
-    GF_TAB(24), GF_TAB(25), GF_TAB(26), GF_TAB(27), GF_TAB(28), GF_TAB(29), GF_TAB(30), GF_TAB(31),
-    GF_TAB(32), GF_TAB(33), GF_TAB(34), GF_TAB(35), GF_TAB(36), GF_TAB(37), GF_TAB(38), GF_TAB(39),
-    GF_TAB(40), GF_TAB(41), GF_TAB(42), GF_TAB(43), GF_TAB(44), GF_TAB(45), GF_TAB(46), GF_TAB(47),
-    GF_TAB(48), GF_TAB(49), GF_TAB(50), GF_TAB(51), GF_TAB(52), GF_TAB(53), GF_TAB(54), GF_TAB(55),
-    GF_TAB(56), GF_TAB(57), GF_TAB(58), GF_TAB(59), GF_TAB(60), GF_TAB(61), GF_TAB(62), GF_TAB(63)
-#undef GF_TAB
+constexpr int kExpTabN = 256;
+
+// 2^(j/256), j = 0..255 (one copy per translation unit; staged into shared memory).
+static __constant__ double c_exp2_tab[kExpTabN] = {
+#define GF_T8(i) kExp2Tab[i], kExp2Tab[i + 1], kExp2Tab[i + 2], kExp2Tab[i + 3], \
+                 kExp2Tab[i + 4], kExp2Tab[i + 5], kExp2Tab[i + 6], kExp2Tab[i + 7]
+#define GF_T64(i) GF_T8(i), GF_T8(i + 8), GF_T8(i + 16), GF_T8(i + 24), GF_T8(i + 32), GF_T8(i + 40), \
+                  GF_T8(i + 48), GF_T8(i + 56)
+    GF_T64(0), GF_T64(64), GF_T64(128), GF_T64(192)
+#undef GF_T64
+#undef GF_T8
 };
 
 __device__ __forceinline__ void stage_exp_table(double *sT)
 {
-    for (int j = threadIdx.x; j < 64; j += blockDim.x) sT[j] = c_exp2_tab[j];
+    for (int j = threadIdx.x; j < kExpTabN; j += blockDim.x) sT[j] = c_exp2_tab[j];
 }
 
-// exp(a) for a <= 0 (finite or -inf; a < -708 returns 0, below the smallest
+// exp(a) for a <= 0 (finite or -inf; a <= -708 returns 0, below the smallest
 // normal double), table-driven after Tang (ACM TOMS 1989): with
-// k = round(64 a / ln2), r = a - k ln2/64 (Cody-Waite two-part ln2/64),
-// |r| <= ln2/128, exp(a) = 2^(k >> 6) * 2^((k & 63)/64) * (1 + expm1(r)) and
-// expm1(r) by its degree-5 Taylor polynomial (truncation < r^6/720 < 4e-17).
-// Ten FP64 operations; the rounding to the integer k, the table index and
+// k = round(256 a / ln2), r = a - k ln2/256 (Cody-Waite two-part ln2/256),
+// |r| <= ln2/512, exp(a) = 2^(k >> 8) * 2^((k & 255)/256) * (1 + expm1(r)) and
+// expm1(r) by its degree-4 Taylor polynomial (truncation < r^5/120 < 4e-17).
+// Nine FP64 operations; the rounding to the integer k, the table index and
 // the power-of-two scaling are integer operations on the bit patterns.
 __device__ __forceinline__ double exp_tang(double a, const double *__restrict__ T)
 {
     const double shifter = 6755399441055744.0;   // 1.5 * 2^52: fma(a, c, shifter) rounds to integer
-    const double t = fma(a, kInvLn2x64, shifter);
+    const double t = fma(a, kInvLn2xN, shifter);
     const int k = __double2loint(t);
     const double kd = t - shifter;
-    double r = fma(kd, -kLn2By64Hi, a);
-    r = fma(kd, -kLn2By64Lo, r);
-    double p = fma(r, 1.0 / 120.0, 1.0 / 24.0);
-    p = fma(p, r, 1.0 / 6.0);
+    double r = fma(kd, -kLn2ByNHi, a);
+    r = fma(kd, -kLn2ByNLo, r);
+    double p = fma(r, 1.0 / 24.0, 1.0 / 6.0);
     p = fma(p, r, 0.5);
     p = fma(p, r, 1.0);
     p = p * r;                                   // expm1(r)
-    const double Tj = T[k & 63];
+    const double Tj = T[k & (kExpTabN - 1)];
     const double v = fma(Tj, p, Tj);
-    const int hi = __double2hiint(v) + ((k >> 6) << 20);
+    const int hi = __double2hiint(v) + ((k >> 8) << 20);
     const unsigned ahi = (unsigned)__double2hiint(a);
     // a <= -708 (sign set, |a| >= 708: hi word >= that of -708.0) flushes to 0
     return ahi >= 0xC0862000u ? 0.0 : __hiloint2double(hi, __double2loint(v));
+}
+
+// a < -40.5 for a double, decided on the bit pattern with integer compares
+// (for negative a, larger magnitude means a larger unsigned pattern; NaN with
+// the sign bit set also counts as negligible).  Same decision as the FP64
+// comparison, without an FP64 instruction.
+__device__ __forceinline__ bool below_cull(double a)
+{
+    return (unsigned long long)__double_as_longlong(a) > 0xC044400000000000ull;   // bits of -40.5
 }
 
 template <typename R>
@@ -224,7 +249,12 @@ __device__ __forceinline__ void iso_index(const MediumParams &m, const R *__rest
         const R *b = sb + kBlobStride * j * stride;
         const R dx = x[0] - b[stride], dy = x[1] - b[2 * stride], dz = x[2] - b[3 * stride];
         const R a = (dx * dx + dy * dy + dz * dz) * b[4 * stride];
-        if (a >= (R)kBlobCull) {
+        bool live;
+        if constexpr (sizeof(R) == 8)
+            live = !below_cull(a);
+        else
+            live = a >= (R)kBlobCull;
+        if (live) {
             const R Ae = b[0] * blob_exp<R>(a, cx);
             n2 += Ae;
             const R c = b[5 * stride] * Ae;      // 2 s A e

@@ -128,7 +128,7 @@ rk4_kernel(const MediumParams m, const RaysView<R> r, const Omega<R> om, const R
            unsigned long long *counters)
 {
     __shared__ R sb[kBlobStride * GF_MAX_BLOBS];
-    __shared__ double sT[64];
+    __shared__ double sT[kExpTabN];
     __shared__ float sp[4 * GF_MAX_BLOBS];
     __shared__ float sdf[DF ? kDfBlobStride * GF_MAX_BLOBS : 1];
     __shared__ float sdT[DF ? 128 : 1];
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kRk4Block) onshell_kernel(const MediumParams m
                                                             const R *__restrict__ dir, const R omega)
 {
     __shared__ R sb[kBlobStride * GF_MAX_BLOBS];
-    __shared__ double sT[64];
+    __shared__ double sT[kExpTabN];
     if constexpr (KIND != K_SPLINE) stage_blobs<R>(m, sb);
     stage_exp_table(sT);
     __syncthreads();
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(kRk4Block) newton_kx_kernel(const MediumParams
                                                               const R omega, const R tol, const int max_iter)
 {
     __shared__ R sb[kBlobStride * GF_MAX_BLOBS];
-    __shared__ double sT[64];
+    __shared__ double sT[kExpTabN];
     if constexpr (KIND != K_SPLINE) stage_blobs<R>(m, sb);
     stage_exp_table(sT);
     __syncthreads();
