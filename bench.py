@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-DOPRI5 and adjoint measurements")
+    ap.add_argument("--workload", choices=["grin", "batched", "aniso", "adjoint", "generated"],
+                    default="grin", help="grin: the headline line; others print that measurement alone")
+    ap.add_argument("--media", type=int, default=4096, help="batched: number of media")
     return ap.parse_args()
 
 
@@ -170,11 +173,11 @@ def algorithmic_flops(evals: int, live: int, n_blobs: int, ray_steps: int) -> in
     return FLOPS_LIVE_TERM * live + FLOPS_CULLED_TERM * culled + FLOPS_EVAL * evals + FLOPS_STEP * ray_steps
 
 
-def measure_batched(gf, torch, tune_cache: str | None = None) -> dict:
+def measure_batched(gf, torch, tune_cache: str | None = None, n_media: int = 4096) -> dict:
     """Batched DOPRI5 workload (4096 Luneburg + 8-blob media, ~12.56M rays,
     rtol = atol = 1e-9, exit at r = 1.5): persistent work-stealing graph launch
     vs one launch per medium (also a graph), each timed once after a warm-up."""
-    wl = W.batched()
+    wl = W.batched(n_media=n_media)
     blobs, off = wl.extra["blobs"], wl.extra["offsets"]
     media = [gf.gf_medium_create("luneburg", blobs=blobs[j]) for j in range(len(off) - 1)]
     batch = gf.gf_batch_create(media, off)
@@ -214,7 +217,7 @@ def measure_batched(gf, torch, tune_cache: str | None = None) -> dict:
         out[name] = {"ms": ms[-1], "accepted_ray_steps": steps,
                      "rejected": int(rej.to(torch.int64).sum().item()),
                      "ray_steps_per_s": steps / (ms[-1] / 1e3)}
-    return {"workload": f"4096 Luneburg+8-blob media, {wl.n} rays, DOPRI5 rtol=atol=1e-9, exit r=1.5",
+    return {"workload": f"{n_media} Luneburg+8-blob media, {wl.n} rays, DOPRI5 rtol=atol=1e-9, exit r=1.5",
             "persistent": out["persistent"], "per_medium": out["per_medium"],
             "speedup_persistent_vs_per_medium": out["per_medium"]["ms"] / out["persistent"]["ms"],
             "tune": {"block": tune.block, "rays_per_thread": tune.rays_per_thread,
@@ -271,6 +274,37 @@ def measure_f64x(gf, torch, wl, m, x0, dirs, rays) -> dict:
     return {"ray_steps_per_s": units / (ms[-1] / 1e3), "ms": ms[-1], "max_abs_D": rays.d_max.max().item(),
             "dtype": "f64 state and integrator, f32x2 (double-float) blob sums",
             "parity": "<= 1e-9 relative to the FP64 oracle in tests/test_gpu_f64x.py"}
+
+
+def measure_generated(gf, torch, n_rays: int, n_steps: int) -> dict:
+    """The GRIN + 16 blob medium written symbolically and compiled at run time
+    (the paper's route: graph, df, reduce, generated kernel) against the
+    hand-written FP64 kernel, same rays and steps."""
+    from paper_2508_15967_gb300 import symbolic as S
+    wl = W.grin(n=n_rays, n_steps=n_steps)
+    D = S.isotropic(S.grin_n2(1.5, 2.0) + S.gaussian_blobs(wl.medium["blobs"]))
+    t0 = time.perf_counter()
+    mg = gf.gf_jit_medium_create(S.medium_source(D))
+    jit_s = time.perf_counter() - t0
+    mh = gf.gf_medium_create(**wl.medium)
+    init = gf.Rays.from_numpy(wl.x0, None)
+    gf.gf_rays_onshell(mh, init, torch.from_numpy(np.ascontiguousarray(wl.d.T)).cuda(), 1.0)
+    out = {}
+    for name, m in (("generated", mg), ("handwritten", mh)):
+        for _ in range(2):
+            rays = init.clone()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            gf.gf_trace_rk4(m, rays, 1.0, wl.dt, wl.n_steps)
+            e1.record()
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[name] = {"ms": ms, "ray_steps_per_s": wl.n * wl.n_steps / (ms / 1e3), "y": rays.y.clone()}
+    dev = ((out["generated"].pop("y") - out["handwritten"].pop("y")).abs().max()).item()
+    return {"workload": f"GRIN + 16 blobs, {wl.n} rays x {wl.n_steps} RK4 steps, FP64",
+            "generated": out["generated"], "handwritten": out["handwritten"],
+            "nvrtc_compile_s": jit_s, "graph_nodes": S.count_nodes(S.gradients(D)),
+            "max_abs_state_difference": dev}
 
 
 def measure_adjoint(gf, torch) -> dict:
@@ -469,10 +503,30 @@ def run_gpu(a):
         dist.destroy_process_group()
 
 
+def run_workload(a):
+    """One secondary measurement alone (rank 0, one GPU), as a JSON line."""
+    import torch
+    import paper_2508_15967_gb300 as gf
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    sm = 2070.0
+    peak = SMS * 2 * 2 * sm * 1e6 / 1e12
+    if a.workload == "batched":
+        res = measure_batched(gf, torch, n_media=a.media)
+    elif a.workload == "aniso":
+        res = measure_aniso(gf, torch, peak)
+    elif a.workload == "adjoint":
+        res = measure_adjoint(gf, torch)
+    else:
+        res = measure_generated(gf, torch, min(a.rays, 1 << 18), min(a.nsteps, 2000))
+    print(json.dumps({"workload": a.workload, **res}), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload != "grin":
+        run_workload(a)
     else:
         run_gpu(a)
 
