@@ -221,7 +221,7 @@ static void or_cold(const or_medium *m, const double *x, const double *k, double
     double g = m->prof[2] + m->prof[3] * x[0], gx = m->prof[3];
     double S = 1.0, Dst = 0.0, P = 1.0, Sx = 0.0, Dx_ = 0.0, Px = 0.0, Sw = 0.0, Dw_ = 0.0, Pw = 0.0;
     double a, b, RL, DS, DD, DP, Da, Db;
-    int sp, i;
+    int sp;
     for (sp = 0; sp < m->n_species; sp++) {
         double wp2 = m->species[2 * sp] * f, wp2x = m->species[2 * sp] * fx;
         double W = m->species[2 * sp + 1] * g, Wx = m->species[2 * sp + 1] * gx;
@@ -253,7 +253,6 @@ static void or_cold(const or_medium *m, const double *x, const double *k, double
     o->Dx[2] = 0.0;
     o->Dw = Da * (-2.0 * a / w) + Db * (-2.0 * b / w) + DS * Sw + DD * Dw_ + DP * Pw;
     o->eps = fabs(o->Dw);
-    (void)i;
 }
 
 /* isotropic : D = |k|^2 - w^2 n^2(x)

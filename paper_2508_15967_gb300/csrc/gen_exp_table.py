@@ -2,16 +2,19 @@
 
 Method: P. T. P. Tang, "Table-driven implementation of the exponential
 function in IEEE floating-point arithmetic", ACM TOMS 15 (1989) 144-157, with
-a 256-entry table and Cody-Waite two-constant argument reduction (W. J. Cody
+a 2048-entry table and Cody-Waite two-constant argument reduction (W. J. Cody
 and W. Waite, Software Manual for the Elementary Functions, 1980):
-    a = (256 m + j) ln2/256 + r,  exp(a) = 2^m * 2^(j/256) * exp(r),  |r| <= ln2/512.
+    a = (2048 m + j) ln2/2048 + r,  exp(a) = 2^m * 2^(j/2048) * exp(r),  |r| <= ln2/4096.
 Every value is computed here with 60-digit decimal arithmetic and rounded once
 to the nearest double.  Run: python gen_exp_table.py > gf_exp_table.inc
 """
 from decimal import Decimal, getcontext
-import struct
+import math
 
 getcontext().prec = 60
+
+N = 2048
+HI_BITS = 31      # |k| < 2^22 for |a| < 709, so k * hi is exact
 
 
 def ln2() -> Decimal:
@@ -22,32 +25,29 @@ def to_double(d: Decimal) -> float:
     return float(d)          # correctly rounded from the decimal string
 
 
-def hexf(x: float) -> str:
-    return float.hex(x)
-
-
 def trunc_bits(x: float, bits: int) -> float:
     """x with its significand truncated to `bits` bits (so k * x is exact for small k)."""
-    m, e = __import__("math").frexp(x)
+    m, e = math.frexp(x)
     scale = 2 ** bits
-    return __import__("math").ldexp(int(m * scale) / scale, e)
+    return math.ldexp(int(m * scale) / scale, e)
 
 
 def main():
-    L = ln2() / 256
-    hi = trunc_bits(to_double(L), 35)            # |k| < 2^18 for |a| < 709: k*hi exact
+    L = ln2() / N
+    hi = trunc_bits(to_double(L), HI_BITS)
     lo = to_double(L - Decimal(hi))
-    inv = to_double(256 / ln2())
+    inv = to_double(N / ln2())
     print("// Generated by gen_exp_table.py -- constants of the table-driven exp")
-    print("// (Tang 1989, 256-entry table; Cody-Waite split of ln2/256).")
-    print(f"constexpr double kInvLn2xN = {hexf(inv)};   // 256 / ln 2")
-    print(f"constexpr double kLn2ByNHi = {hexf(hi)};   // ln2/256, 35 significant bits")
-    print(f"constexpr double kLn2ByNLo = {hexf(lo)};   // ln2/256 - kLn2ByNHi")
-    print("constexpr double kExp2Tab[256] = {   // 2^(j/256), correctly rounded")
-    for j in range(256):
-        v = to_double((Decimal(j) / 256 * ln2()).exp())
-        print(f"    {hexf(v)},")
-    print("};")
+    print(f"// (Tang 1989, {N}-entry table; Cody-Waite split of ln2/{N}).")
+    print(f"constexpr double kInvLn2xN = {float.hex(inv)};   // {N} / ln 2")
+    print(f"constexpr double kLn2ByNHi = {float.hex(hi)};   // ln2/{N}, {HI_BITS} significant bits")
+    print(f"constexpr double kLn2ByNLo = {float.hex(lo)};   // ln2/{N} - kLn2ByNHi")
+    print(f"// 2^(j/{N}), j = 0..{N - 1}, correctly rounded (initialiser of a device array)")
+    print("#define GF_EXP2_TAB_VALUES \\")
+    for j in range(N):
+        v = to_double((Decimal(j) / N * ln2()).exp())
+        print(f"    {float.hex(v)}{',' if j < N - 1 else ''} \\")
+    print("")
 
 
 if __name__ == "__main__":

@@ -78,7 +78,8 @@ __global__ void __launch_bounds__(kAdjBlock) adjoint_kernel(
     __shared__ double sT[kExpTabN];
     extern __shared__ double tb[];   // thetabar columns: tb[j * blockDim + tid]
     const int nb = m.n_blobs;
-    stage_blobs<double>(m, sb);
+    // plain rows (A, c, s, 2 s): the sweep needs G_j = exp(s_j |x - c_j|^2) without A_j
+    for (int j = threadIdx.x; j < nb * kBlobStride; j += blockDim.x) sb[j] = m.blobs64[j];
     stage_exp_table(sT);
     for (int j = 0; j < nb; ++j) tb[j * blockDim.x + threadIdx.x] = 0.0;
     __syncthreads();
@@ -239,9 +240,14 @@ cudaError_t launch_adjoint(const MediumParams &m, int64_t n, double omega, doubl
     S.partials = (double *)base;
     S.stage = S.partials + blocks * nb;
     S.G = S.stage + every * 4 * kStageVals * n;
+    // thetabar columns (dynamic) next to the blob rows and the exp table (static, 19 KiB)
     const size_t smem = (size_t)nb * kAdjBlock * sizeof(double);
+    cudaError_t e;
 #define GF_ADJ(K)                                                                                         \
     case K:                                                                                               \
+        if ((e = cudaFuncSetAttribute(adjoint_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                      (int)smem)) != cudaSuccess)                                         \
+            return e;                                                                                     \
         adjoint_kernel<K><<<(unsigned)blocks, kAdjBlock, smem, s>>>(m, n, omega, dt, n_steps, every,      \
                                                                     ckpt, steps_done, lambda, ld, dy0, S); \
         break;
@@ -254,7 +260,7 @@ cudaError_t launch_adjoint(const MediumParams &m, int64_t n, double omega, doubl
         return cudaErrorInvalidValue;
     }
 #undef GF_ADJ
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     adjoint_reduce_kernel<<<(nb + 63) / 64, 64, 0, s>>>(S.partials, blocks, nb, dtheta);
     return cudaGetLastError();

@@ -1,6 +1,7 @@
 // gf_api.cu -- host side of the C ABI declared in include/gf.h: error
 // reporting, argument validation, medium objects and the RK4 / on-shell
 // entry points.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -81,7 +82,8 @@ static unsigned long long *g_work_counters = nullptr;
 unsigned long long *work_counters() { return g_work_counters; }
 
 const MediumParams &params_of(gf_medium m) { return m->p; }
-const double *medium_device_blobs(gf_medium m) { return m->d_blobs64; }
+// scaled FP64 rows (what the FP64 evaluator reads)
+const double *medium_device_blobs(gf_medium m) { return m->p.blobs64s; }
 int device_of(gf_medium m) { return m->device; }
 
 static gf_status check_medium(gf_medium m)
@@ -108,6 +110,7 @@ static void free_medium(gf_medium m)
     delete m;
 }
 
+// A_j in the plain rows (double and float) and A_j, -2 sigma_j A_j in the scaled rows.
 __global__ void set_amplitudes_kernel(double *b64, float *b32, const double *A, int nb)
 {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -115,6 +118,9 @@ __global__ void set_amplitudes_kernel(double *b64, float *b32, const double *A, 
         double a = A[j];
         b64[kBlobStride * j] = a;
         b32[kBlobStride * j] = (float)a;
+        double *sc = b64 + kBlobStride * (nb + j);
+        sc[4] = a;
+        sc[5] = (-2.0 * sc[0]) * a;
     }
 }
 
@@ -178,8 +184,12 @@ gf_status gf_medium_create(const gf_medium_desc *d, gf_medium *out)
         set_error("gf_medium_create: spline needs a grid with 4 <= grid_n <= 2048");
         return GF_ERR_INVALID_ARG;
     }
-    std::vector<double> t64(kBlobStride * (size_t)d->n_blobs);
-    std::vector<float> t32(t64.size());
+    // plain rows, then scaled rows (t64); plain float rows, then FP32 pre-test rows (t32)
+    const size_t nbl = (size_t)d->n_blobs;
+    std::vector<double> t64(2 * kBlobStride * nbl);
+    std::vector<float> t32(kBlobStride * nbl + 4 * nbl);
+    double pre_span = 0.0;   // max over blobs of sigma, and of sigma |c_i|
+    double sig_max = 0.0;
     for (int j = 0; j < d->n_blobs; ++j) {
         const double *b = d->blobs + 5 * j;
         double w = b[4];
@@ -189,11 +199,28 @@ gf_status gf_medium_create(const gf_medium_desc *d, gf_medium *out)
             return GF_ERR_INVALID_ARG;
         }
         const double sj = -1.0 / (2.0 * w * w);
-        double row[kBlobStride] = {b[0], b[1], b[2], b[3], sj, 2.0 * sj};
+        const double sig = std::sqrt(-sj);
+        if (!(sj < 0) || !std::isfinite(sj) || !(sig > 0) || !std::isfinite(-2.0 * sig * b[0])) {
+            set_error("gf_medium_create: blob %d: width %g out of range", j, w);
+            return GF_ERR_INVALID_ARG;
+        }
+        const double row[kBlobStride] = {b[0], b[1], b[2], b[3], sj, 2.0 * sj};
+        const double srow[kBlobStride] = {sig, -(sig * b[1]), -(sig * b[2]), -(sig * b[3]), b[0],
+                                          (-2.0 * sig) * b[0]};
         for (int c = 0; c < kBlobStride; ++c) {
             t64[kBlobStride * j + c] = row[c];
+            t64[kBlobStride * (nbl + j) + c] = srow[c];
             t32[kBlobStride * j + c] = (float)row[c];
         }
+        for (int c = 0; c < 4; ++c) t32[kBlobStride * nbl + 4 * j + c] = (float)srow[c];
+        sig_max = std::max(sig_max, sig);
+        for (int c = 1; c < 4; ++c) pre_span = std::max(pre_span, std::fabs(srow[c]));
+    }
+    // FP32 pre-test valid while sigma (2 max|x_i| + max|c_i|) <= 1e5 for every blob
+    float pre_lim = -1.0f;
+    if (d->n_blobs > 0) {
+        const double lim = (1e5 - pre_span) / (2.0 * sig_max);
+        if (lim > 0) pre_lim = (float)std::min(lim, 1e30);
     }
     gf_medium m = new gf_medium_s();
     cudaGetDevice(&m->device);
@@ -201,6 +228,7 @@ gf_status gf_medium_create(const gf_medium_desc *d, gf_medium *out)
     p.kind = d->kind;
     p.n_blobs = d->n_blobs;
     p.grid_n = d->grid_n;
+    p.pre_lim = pre_lim;
     p.n_h2 = d->n_h * d->n_h;
     p.n02 = d->n0 * d->n0;
     p.n02a2 = d->n0 * d->n0 * d->a * d->a;
@@ -208,9 +236,9 @@ gf_status gf_medium_create(const gf_medium_desc *d, gf_medium *out)
     for (int i = 0; i < 2 * GF_MAX_SPECIES; ++i) p.species[i] = i < 2 * p.n_species ? d->species[i] : 0.0;
     for (int i = 0; i < 4; ++i) p.prof[i] = d->kind == GF_MED_COLD ? d->profile[i] : 0.0;
     gf_status s = GF_OK;
-    size_t nb = t64.size() ? t64.size() : 1;
-    if ((s = cuda_status(cudaMalloc(&m->d_blobs64, nb * sizeof(double)), "cudaMalloc(blobs)")) != GF_OK ||
-        (s = cuda_status(cudaMalloc(&m->d_blobs32, nb * sizeof(float)), "cudaMalloc(blobs)")) != GF_OK) {
+    const size_t n64 = std::max<size_t>(t64.size(), 1), n32 = std::max<size_t>(t32.size(), 1);
+    if ((s = cuda_status(cudaMalloc(&m->d_blobs64, n64 * sizeof(double)), "cudaMalloc(blobs)")) != GF_OK ||
+        (s = cuda_status(cudaMalloc(&m->d_blobs32, n32 * sizeof(float)), "cudaMalloc(blobs)")) != GF_OK) {
         free_medium(m);
         return s;
     }
@@ -225,6 +253,8 @@ gf_status gf_medium_create(const gf_medium_desc *d, gf_medium *out)
     }
     p.blobs64 = m->d_blobs64;
     p.blobs32 = m->d_blobs32;
+    p.blobs64s = m->d_blobs64 + kBlobStride * nbl;
+    p.pre32 = m->d_blobs32 + kBlobStride * nbl;
     if (d->kind == GF_MED_SPLINE) {
         size_t nodes = (size_t)d->grid_n * d->grid_n * d->grid_n;
         for (size_t i = 0; i < nodes * 8; ++i)
@@ -348,9 +378,7 @@ gf_status gf_trace_rk4(gf_medium m, gf_precision prec, const gf_rays *rays, doub
         }
         if (rays->n > 0 && (s = check_device_ptr(ckpt, "ckpt")) != GF_OK) return s;
     }
-    if (rays->n == 0 || n_steps == 0) {
-        if (rays->n == 0) return GF_OK;
-    }
+    if (rays->n == 0) return GF_OK;
     return cuda_status(launch_rk4(m->p, prec, *rays, omega, dt, n_steps, radius,
                                   ckpt ? checkpoint_every : 1, ckpt, (cudaStream_t)stream),
                        "gf_trace_rk4 launch");

@@ -170,7 +170,7 @@ __device__ __forceinline__ void blobs_df(const float *__restrict__ sd, int nb, c
     for (int j = 0; j < nb; ++j) {
         const float *b = sd + kDfBlobStride * j;
         const float ex = X0.hi - b[0], ey = X1.hi - b[1], ez = X2.hi - b[2];
-        if ((ex * ex + ey * ey + ez * ez) * b[6] < kBlobCullF) continue;
+        if ((ex * ex + ey * ey + ez * ez) * b[6] < -kBlobCullQF) continue;
         const dfl d0 = df_add(X0, dfl{-b[0], -b[3]});
         const dfl d1 = df_add(X1, dfl{-b[1], -b[4]});
         const dfl d2 = df_add(X2, dfl{-b[2], -b[5]});

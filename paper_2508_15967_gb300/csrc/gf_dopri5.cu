@@ -6,7 +6,6 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <map>
 #include <string>
 #include <vector>
 
@@ -39,7 +38,7 @@ struct Ctl {
 // Device view of a batch.
 struct BatchView {
     int32_t n_media, nb_max, n_items, pad;
-    const double *blobs;        // n_media x nb_max x kBlobStride
+    const double *blobs;        // n_media x nb_max scaled rows (kBlobStride values each)
     const int32_t *nb;          // n_media
     const double *base;         // n_media x 3: n_h2, n02, n02a2
     const int32_t *item_medium; // n_items
@@ -72,7 +71,7 @@ struct LaneRhs {
 };
 
 // Load ray `ray` of medium `med` into lane L and its per-thread shared-memory
-// blob slot (field f of blob j at sm[(5 j + f) * stride]).  Returns false if
+// blob slot (field f of blob j at sm[(kBlobStride j + f) * stride]).  Returns false if
 // the ray is not active.
 template <int KIND>
 __device__ __forceinline__ bool lane_load(Lane &L, const BatchView &B, const RaysView<double> &r,
@@ -324,7 +323,6 @@ struct gf_batch_s {
     GraphCache graphs[2];
     bool tuned = false;
     gf_tune tune{};
-    std::vector<int> media_kind_nb;  // per medium blob count (host)
 };
 
 namespace gf {

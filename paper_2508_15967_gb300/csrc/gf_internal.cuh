@@ -15,15 +15,22 @@ namespace gf {
 enum : int { K_HOMOG = GF_MED_HOMOG, K_LUNEBURG = GF_MED_LUNEBURG, K_GRIN = GF_MED_GRIN,
              K_QUADRATIC = GF_MED_QUADRATIC, K_SPLINE = GF_MED_SPLINE, K_COLD = GF_MED_COLD };
 
-constexpr int kBlobStride = 6;   // device blob row: A, cx, cy, cz, s = -1 / (2 w^2), 2 s
+// Device blob rows, 6 values each:
+//   plain  (FP32 path, adjoint, double-float path): A, cx, cy, cz, s = -1 / (2 w^2), 2 s
+//   scaled (FP64 evaluator): sigma, -sigma cx, -sigma cy, -sigma cz, A, -2 sigma A
+// with sigma = sqrt(-s), so that A exp(s |x - c|^2) = A exp(-|u|^2), u = sigma x - sigma c.
+constexpr int kBlobStride = 6;
 
 // Medium as the kernels see it (passed by value as a kernel argument).
 struct MediumParams {
-    int32_t kind, n_blobs, grid_n, pad;
+    int32_t kind, n_blobs, grid_n;
+    float pre_lim;               // FP32 pre-test valid while max_i |x_i| <= pre_lim
     double n_h2;                 // homogeneous n^2
     double n02, n02a2;           // GRIN: n0^2 and n0^2 a^2
-    const double *blobs64;       // n_blobs x kBlobStride
-    const float *blobs32;        // float copy of the same table
+    const double *blobs64;       // n_blobs plain rows
+    const float *blobs32;        // float copy of the plain rows
+    const double *blobs64s;      // n_blobs scaled rows
+    const float *pre32;          // n_blobs x 4 floats: sigma, -sigma cx, -sigma cy, -sigma cz
     const float4 *grid;          // grid_n^3 nodes x 2 float4
     int32_t n_species, pad2;     // cold plasma
     double species[2 * GF_MAX_SPECIES];
@@ -47,8 +54,8 @@ struct RaysView {
 struct gf_medium_s {
     gf::MediumParams p{};
     int device = -1;
-    double *d_blobs64 = nullptr;
-    float *d_blobs32 = nullptr;
+    double *d_blobs64 = nullptr;     // plain rows, then scaled rows (2 x n_blobs rows)
+    float *d_blobs32 = nullptr;      // plain float rows, then pre-test rows
     float4 *d_grid = nullptr;
     cudaLibrary_t jit_lib = nullptr;
     cudaKernel_t jit_kernel = nullptr;
@@ -85,46 +92,38 @@ cudaError_t launch_onshell(const MediumParams &m, gf_precision prec, const gf_ra
 
 #include "gf_exp_table.inc"
 
-constexpr int kExpTabN = 256;
+constexpr int kExpTabN = 2048;
 
-// 2^(j/256), j = 0..255 (one copy per translation unit; staged into shared memory).
-static __constant__ double c_exp2_tab[kExpTabN] = {
-#define GF_T8(i) kExp2Tab[i], kExp2Tab[i + 1], kExp2Tab[i + 2], kExp2Tab[i + 3], \
-                 kExp2Tab[i + 4], kExp2Tab[i + 5], kExp2Tab[i + 6], kExp2Tab[i + 7]
-#define GF_T64(i) GF_T8(i), GF_T8(i + 8), GF_T8(i + 16), GF_T8(i + 24), GF_T8(i + 32), GF_T8(i + 40), \
-                  GF_T8(i + 48), GF_T8(i + 56)
-    GF_T64(0), GF_T64(64), GF_T64(128), GF_T64(192)
-#undef GF_T64
-#undef GF_T8
-};
+// 2^(j/2048), j = 0..2047 (one copy per translation unit in global memory,
+// staged into shared memory by every block that evaluates blob terms in FP64).
+static __device__ double g_exp2_tab[kExpTabN] = {GF_EXP2_TAB_VALUES};
 
 __device__ __forceinline__ void stage_exp_table(double *sT)
 {
-    for (int j = threadIdx.x; j < kExpTabN; j += blockDim.x) sT[j] = c_exp2_tab[j];
+    for (int j = threadIdx.x; j < kExpTabN; j += blockDim.x) sT[j] = g_exp2_tab[j];
 }
 
 // exp(a) for a <= 0 (finite or -inf; a <= -708 returns 0, below the smallest
 // normal double), table-driven after Tang (ACM TOMS 1989): with
-// k = round(256 a / ln2), r = a - k ln2/256 (Cody-Waite two-part ln2/256),
-// |r| <= ln2/512, exp(a) = 2^(k >> 8) * 2^((k & 255)/256) * (1 + expm1(r)) and
-// expm1(r) by its degree-4 Taylor polynomial (truncation < r^5/120 < 4e-17).
-// Nine FP64 operations; the rounding to the integer k, the table index and
+// k = round(2048 a / ln2), r = a - k ln2/2048 (Cody-Waite two-part ln2/2048),
+// |r| <= ln2/4096, exp(a) = 2^(k >> 11) * 2^((k & 2047)/2048) * (1 + expm1(r))
+// and expm1(r) = r + r^2 (1/2 + r/6) (truncation < r^4/24 < 3.5e-17).
+// Eight FP64 operations; the rounding to the integer k, the table index and
 // the power-of-two scaling are integer operations on the bit patterns.
+// Error against exp(a): < 0.5 ulp (table) + 0.5 ulp (last fma) + 0.16 ulp.
 __device__ __forceinline__ double exp_tang(double a, const double *__restrict__ T)
 {
     const double shifter = 6755399441055744.0;   // 1.5 * 2^52: fma(a, c, shifter) rounds to integer
     const double t = fma(a, kInvLn2xN, shifter);
     const int k = __double2loint(t);
     const double kd = t - shifter;
-    double r = fma(kd, -kLn2ByNHi, a);
+    double r = fma(kd, -kLn2ByNHi, a);           // exact
     r = fma(kd, -kLn2ByNLo, r);
-    double p = fma(r, 1.0 / 24.0, 1.0 / 6.0);
-    p = fma(p, r, 0.5);
-    p = fma(p, r, 1.0);
-    p = p * r;                                   // expm1(r)
+    const double c = fma(r, 1.0 / 6.0, 0.5);
+    const double p = fma(r * r, c, r);           // expm1(r)
     const double Tj = T[k & (kExpTabN - 1)];
     const double v = fma(Tj, p, Tj);
-    const int hi = __double2hiint(v) + ((k >> 8) << 20);
+    const int hi = __double2hiint(v) + ((k >> 11) << 20);
     const unsigned ahi = (unsigned)__double2hiint(a);
     // a <= -708 (sign set, |a| >= 708: hi word >= that of -708.0) flushes to 0
     return ahi >= 0xC0862000u ? 0.0 : __hiloint2double(hi, __double2loint(v));
@@ -149,11 +148,13 @@ __device__ __forceinline__ float dev_exp<float>(float a) { return expf(a); }
 template <typename R>
 __device__ __forceinline__ const R *blob_table(const MediumParams &m);
 template <>
-__device__ __forceinline__ const double *blob_table<double>(const MediumParams &m) { return m.blobs64; }
+__device__ __forceinline__ const double *blob_table<double>(const MediumParams &m) { return m.blobs64s; }
 template <>
 __device__ __forceinline__ const float *blob_table<float>(const MediumParams &m) { return m.blobs32; }
 
-// Stage the blob table into shared memory (all threads of the block call it).
+// Stage the blob rows the evaluator of precision R reads (scaled rows for
+// double, plain float rows for float) into shared memory (all threads of the
+// block call it).
 template <typename R>
 __device__ __forceinline__ void stage_blobs(const MediumParams &m, R *sb)
 {
@@ -165,43 +166,41 @@ __device__ __forceinline__ void stage_blobs(const MediumParams &m, R *sb)
 // contribution A e^{-40.5} < 2.6e-18 |A| to n^2 (and < 3e-17 |A| / w to
 // grad n^2 for the widths in use) is far below the rounding of the sums.
 constexpr double kBlobCull = -40.5;
-// FP32 pre-test for the FP64 path: a term whose exponent, computed in FP32
-// from rounded x, c and s, is below -41 has an exact exponent below -40.5
-// (the FP32 error is < 1e-3 for |s| <= 200 and |x - c| < 4), so it is skipped
-// before any FP64 work; the FP64 test then decides the remaining terms
-// exactly as without the pre-test.
-constexpr float kBlobCullF = -41.0f;
+// FP32 pre-test of the FP64 evaluator: a term whose |u|^2, computed in FP32
+// from rounded x, sigma and sigma c, exceeds 41 has an exact exponent below
+// -40.5.  With relative rounding 2^-24 on each FP32 input and on the fma, the
+// error of each u_i is below 6e-8 (2 sigma |x_i| + sigma |c_i| + |u_i|), and
+// that of |u|^2 (|u| < 6.5 near the threshold) below 22 times that; the host
+// sets pre_lim so that sigma (2 max|x_i| + max|c_i|) <= 1e5 for every blob,
+// which keeps the error below 0.14, under the 0.5 margin.  The FP64 test then
+// decides the remaining terms exactly as without the pre-test; rays beyond
+// pre_lim skip the pre-test.
+constexpr float kBlobCullQF = 41.0f;
 
-// Evaluation context: the shared exp table, the FP32 copy of the blob
-// centres and exponent factors (cx, cy, cz, s per blob; FP64 path with a
-// block-shared table only), and a live-term counter.
+// Evaluation context: the shared exp table, the FP32 pre-test rows (FP64
+// path with a block-shared table only), the double-float tables (GF_F64X) and
+// a live-term counter.
 template <typename R>
 struct EvalCtx {
-    const double *T = nullptr;   // 2^(j/64) table (FP64 path)
-    const float *pre = nullptr;  // FP32 pre-test table, 4 floats per blob, or NULL
+    const double *T = nullptr;   // 2^(j/2048) table (FP64 path)
+    const float *pre = nullptr;  // FP32 pre-test rows, 4 floats per blob, or NULL
     const float *dfb = nullptr;  // double-float blob rows (GF_F64X mode)
     const float *dfT = nullptr;  // double-float 2^(j/64) table (GF_F64X mode)
     int live = 0;                // blob terms evaluated (work counter)
 };
 
-// Stage the FP32 pre-test table (cx, cy, cz, s) from the float blob rows.
+// Stage the FP32 pre-test rows (sigma, -sigma c).
 __device__ __forceinline__ void stage_pretest(const MediumParams &m, float *sp)
 {
-    for (int j = threadIdx.x; j < m.n_blobs * 4; j += blockDim.x) sp[j] = m.blobs32[(j >> 2) * kBlobStride + 1 + (j & 3)];
+    for (int j = threadIdx.x; j < m.n_blobs * 4; j += blockDim.x) sp[j] = m.pre32[j];
 }
-
-template <typename R>
-__device__ __forceinline__ R blob_exp(R a, const EvalCtx<R> &cx);
-template <>
-__device__ __forceinline__ double blob_exp<double>(double a, const EvalCtx<double> &cx) { return exp_tang(a, cx.T); }
-template <>
-__device__ __forceinline__ float blob_exp<float>(float a, const EvalCtx<float> &) { return expf(a); }
 
 // Squared index n^2 and its gradient for an isotropic medium of kind KIND plus
 // the Gaussian blobs in sb:  n^2 += A exp(s q),  grad += 2 s A exp(s q) (x - c),
-// with q = |x - c|^2 and s = -1 / (2 w^2).  Field f of blob j is read from
-// sb[(kBlobStride * j + f) * stride] (stride 1: a table shared by the block;
-// stride = block size: one table per thread).
+// with q = |x - c|^2 and s = -1 / (2 w^2).  sb holds the rows stage_blobs<R>
+// stages; field f of blob j is read from sb[(kBlobStride * j + f) * stride]
+// (stride 1: a table shared by the block; stride = block size: one table per
+// thread).
 template <typename R, int KIND>
 __device__ __forceinline__ void iso_index(const MediumParams &m, const R *__restrict__ sb, int nb,
                                           const R *x, R &n2, R *g, EvalCtx<R> &cx, int stride = 1)
@@ -233,35 +232,56 @@ __device__ __forceinline__ void iso_index(const MediumParams &m, const R *__rest
         g[1] = (R)-2 * c * x[1];
         g[2] = (R)-2 * c * x[2];
     }
-    float xf0 = 0.f, xf1 = 0.f, xf2 = 0.f;
-    if (cx.pre != nullptr) {
-        xf0 = (float)x[0];
-        xf1 = (float)x[1];
-        xf2 = (float)x[2];
-    }
-#pragma unroll 2
-    for (int j = 0; j < nb; ++j) {
+    if constexpr (sizeof(R) == 8) {
+        // scaled rows: u = sigma x - sigma c, G = exp(-|u|^2),
+        // n^2 += A G, grad n^2 += (-2 sigma A) G u   (19 FP64 operations per live term)
+        float xf0 = 0.f, xf1 = 0.f, xf2 = 0.f;
+        bool pre = false;
         if (cx.pre != nullptr) {
-            const float *bp = cx.pre + 4 * j;
-            const float ex = xf0 - bp[0], ey = xf1 - bp[1], ez = xf2 - bp[2];
-            if ((ex * ex + ey * ey + ez * ez) * bp[3] < kBlobCullF) continue;
+            xf0 = (float)x[0];
+            xf1 = (float)x[1];
+            xf2 = (float)x[2];
+            pre = fmaxf(fabsf(xf0), fmaxf(fabsf(xf1), fabsf(xf2))) <= m.pre_lim;
         }
-        const R *b = sb + kBlobStride * j * stride;
-        const R dx = x[0] - b[stride], dy = x[1] - b[2 * stride], dz = x[2] - b[3 * stride];
-        const R a = (dx * dx + dy * dy + dz * dz) * b[4 * stride];
-        bool live;
-        if constexpr (sizeof(R) == 8)
-            live = !below_cull(a);
-        else
-            live = a >= (R)kBlobCull;
-        if (live) {
-            const R Ae = b[0] * blob_exp<R>(a, cx);
-            n2 += Ae;
-            const R c = b[5 * stride] * Ae;      // 2 s A e
-            g[0] += c * dx;
-            g[1] += c * dy;
-            g[2] += c * dz;
-            ++cx.live;
+#pragma unroll 2
+        for (int j = 0; j < nb; ++j) {
+            if (pre) {
+                const float *bp = cx.pre + 4 * j;
+                const float v0 = fmaf(bp[0], xf0, bp[1]), v1 = fmaf(bp[0], xf1, bp[2]),
+                            v2 = fmaf(bp[0], xf2, bp[3]);
+                if (v0 * v0 + v1 * v1 + v2 * v2 > kBlobCullQF) continue;
+            }
+            const double *b = sb + kBlobStride * j * stride;
+            const double sg = b[0];
+            const double u0 = fma(sg, x[0], b[stride]), u1 = fma(sg, x[1], b[2 * stride]),
+                         u2 = fma(sg, x[2], b[3 * stride]);
+            const double a = fma(-u2, u2, fma(-u1, u1, -(u0 * u0)));
+            if (!below_cull(a)) {
+                const double G = exp_tang(a, cx.T);
+                n2 = fma(b[4 * stride], G, n2);
+                const double c = b[5 * stride] * G;
+                g[0] = fma(c, u0, g[0]);
+                g[1] = fma(c, u1, g[1]);
+                g[2] = fma(c, u2, g[2]);
+                ++cx.live;
+            }
+        }
+    } else {
+        // plain rows: A exp(s |x - c|^2) and its gradient 2 s A exp(.) (x - c)
+#pragma unroll 2
+        for (int j = 0; j < nb; ++j) {
+            const R *b = sb + kBlobStride * j * stride;
+            const R dx = x[0] - b[stride], dy = x[1] - b[2 * stride], dz = x[2] - b[3 * stride];
+            const R a = (dx * dx + dy * dy + dz * dz) * b[4 * stride];
+            if (a >= (R)kBlobCull) {
+                const R Ae = b[0] * dev_exp<R>(a);
+                n2 += Ae;
+                const R c = b[5 * stride] * Ae;      // 2 s A e
+                g[0] += c * dx;
+                g[1] += c * dy;
+                g[2] += c * dz;
+                ++cx.live;
+            }
         }
     }
 }

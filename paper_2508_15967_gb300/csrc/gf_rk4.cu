@@ -122,24 +122,27 @@ __device__ __forceinline__ void add_work(unsigned long long *counters, long long
 }
 
 template <typename R, int KIND, bool DF>
-__global__ void __launch_bounds__(kRk4Block, (KIND == K_SPLINE || sizeof(R) == 4) ? 1 : 5)
+__global__ void __launch_bounds__(kRk4Block, (KIND == K_SPLINE || KIND == K_COLD || sizeof(R) == 4) ? 1 : 5)
 rk4_kernel(const MediumParams m, const RaysView<R> r, const Omega<R> om, const R dt, const double dt64,
            const int64_t n_steps, const R radius2, const int64_t every, double *__restrict__ ckpt,
            unsigned long long *counters)
 {
+    // FP64 blob terms: scaled rows, the FP32 pre-test rows and the exp table
+    constexpr bool kBlobs64 = sizeof(R) == 8 && KIND != K_SPLINE && KIND != K_COLD && !DF;
     __shared__ R sb[kBlobStride * GF_MAX_BLOBS];
-    __shared__ double sT[kExpTabN];
-    __shared__ float sp[4 * GF_MAX_BLOBS];
+    __shared__ double sT[kBlobs64 ? kExpTabN : 1];
+    __shared__ float sp[kBlobs64 ? 4 * GF_MAX_BLOBS : 1];
     __shared__ float sdf[DF ? kDfBlobStride * GF_MAX_BLOBS : 1];
     __shared__ float sdT[DF ? 128 : 1];
     if constexpr (KIND != K_SPLINE && !DF) stage_blobs<R>(m, sb);
-    constexpr bool kPretest = sizeof(R) == 8 && KIND != K_SPLINE && !DF;
-    if constexpr (kPretest) stage_pretest(m, sp);
+    if constexpr (kBlobs64) {
+        stage_pretest(m, sp);
+        stage_exp_table(sT);
+    }
     if constexpr (DF) {
         stage_df_blobs(m, sdf);
         stage_dfexp_table(sdT);
     }
-    stage_exp_table(sT);
     __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int st = GF_RAY_DONE;   // lanes without an active ray skip the loop
@@ -147,8 +150,10 @@ rk4_kernel(const MediumParams m, const RaysView<R> r, const Omega<R> om, const R
     R dm = (R)0;
     if (i < r.n) st = r.status[i];
     EvalCtx<R> cx;
-    cx.T = sT;
-    if constexpr (kPretest) cx.pre = sp;
+    if constexpr (kBlobs64) {
+        cx.T = sT;
+        cx.pre = sp;
+    }
     if constexpr (DF) {
         cx.dfb = sdf;
         cx.dfT = sdT;
@@ -216,9 +221,9 @@ __global__ void __launch_bounds__(kRk4Block) onshell_kernel(const MediumParams m
                                                             const R *__restrict__ dir, const R omega)
 {
     __shared__ R sb[kBlobStride * GF_MAX_BLOBS];
-    __shared__ double sT[kExpTabN];
+    __shared__ double sT[sizeof(R) == 8 ? kExpTabN : 1];
     if constexpr (KIND != K_SPLINE) stage_blobs<R>(m, sb);
-    stage_exp_table(sT);
+    if constexpr (sizeof(R) == 8) stage_exp_table(sT);
     __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= r.n) return;
@@ -259,9 +264,9 @@ __global__ void __launch_bounds__(kRk4Block) newton_kx_kernel(const MediumParams
                                                               const R omega, const R tol, const int max_iter)
 {
     __shared__ R sb[kBlobStride * GF_MAX_BLOBS];
-    __shared__ double sT[kExpTabN];
+    __shared__ double sT[sizeof(R) == 8 ? kExpTabN : 1];
     if constexpr (KIND != K_SPLINE) stage_blobs<R>(m, sb);
-    stage_exp_table(sT);
+    if constexpr (sizeof(R) == 8) stage_exp_table(sT);
     __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= r.n) return;

@@ -18,8 +18,6 @@ Variables: x0, x1, x2 (position), k0, k1, k2 (wave vector), w (frequency).
 from __future__ import annotations
 
 import math
-from typing import Callable
-
 import numpy as np
 
 # ------------------------------------------------------------------ the graph

@@ -222,6 +222,27 @@ def test_set_amplitudes_changes_the_medium():
     assert_parity(GpuResult(rays), o, 1e-9)
 
 
+def test_narrow_blobs_far_from_origin_skip_the_fp32_pretest():
+    """Blobs of width 1e-3 centred near x = 100: sigma (2|x| + |c|) exceeds the
+    FP32 pre-test's validity bound (pre-test off, every term decided in FP64),
+    and the blobs deflect the rays strongly.  300 rays, 1500 steps."""
+    rng = np.random.default_rng(250815967 + 71)
+    n = 300
+    blobs = np.array([[0.05, 100.0, 0.0, 0.0, 1e-3],
+                      [-0.04, 100.004, 3e-4, -2e-4, 2e-3],
+                      [0.03, 100.012, -5e-4, 4e-4, 1.5e-3]])
+    spec = dict(kind="homog", n_h=1.0, blobs=blobs)
+    x0 = np.column_stack([np.full(n, 99.99), rng.uniform(-3e-3, 3e-3, n), rng.uniform(-3e-3, 3e-3, n)])
+    d = np.column_stack([np.ones(n), rng.uniform(-0.05, 0.05, n), rng.uniform(-0.05, 0.05, n)])
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    k0 = _onshell(spec, x0, d)
+    g = gpu_rk4(spec, x0, k0, 1.0, 2e-5, 1500)
+    o, _ = oracle_rk4(spec, x0, k0, 1.0, 2e-5, 1500)
+    assert_parity(g, o, 1e-9)
+    deflection = np.linalg.norm(o.y[:, 4:] - k0[:, 1:], axis=1)
+    assert np.median(deflection) > 1e-2
+
+
 def test_host_pointer_is_rejected_before_launch():
     m = gf.gf_medium_create("homog", n_h=1.0)
     host = np.zeros((6, 4))
