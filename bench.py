@@ -17,6 +17,7 @@ host cores on a bounded sample of the same workload instead.
 from __future__ import annotations
 
 import argparse
+import inspect
 import json
 import os
 import statistics
@@ -44,7 +45,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gf", "reference"], default="gf")
     ap.add_argument("--rays", type=int, default=1 << 20)
-    ap.add_argument("--nsteps", type=int, default=10000)
+    ap.add_argument("--nsteps", type=int, default=10000,
+                    help="RK4 steps of the headline trace (aniso workload: at most its 4000)")
     ap.add_argument("--precision", choices=["f64", "f32", "f64x"], default="f64",
                     help="f64: IEEE double throughout (the headline); f32; f64x: double state and "
                          "integrator with double-float blob sums")
@@ -53,8 +55,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the batched-DOPRI5 and adjoint measurements")
-    ap.add_argument("--workload", choices=["grin", "batched", "aniso", "adjoint", "generated"],
+                    help="skip the secondary measurements (f64x, luneburg, aniso, adjoint, batched)")
+    ap.add_argument("--workload", choices=["grin", "luneburg", "batched", "aniso", "adjoint", "generated"],
                     default="grin", help="grin: the headline line; others print that measurement alone")
     ap.add_argument("--media", type=int, default=4096, help="batched: number of media")
     return ap.parse_args()
@@ -231,28 +233,54 @@ def measure_batched(gf, torch, tune_cache: str | None = None, n_media: int = 409
 FLOPS_SPLINE_EVAL = 2 * 1344 + 60 + 60
 
 
-def measure_aniso(gf, torch, peak_tflops: float) -> dict:
+def measure_aniso(gf, torch, peak_tflops: float, n_steps: int | None = None) -> dict:
     """Anisotropic tricubic B-spline workload (262,144 rays, 128^3 grid, RK4
-    dt = 1e-3 x 4000, FP64), one warm-up trace of 100 steps then one timed."""
+    dt = 1e-3 x 4000, FP64; n_steps shortens the trace), one warm-up trace of
+    up to 100 steps then one timed."""
     wl = W.aniso()
+    n_steps = wl.n_steps if n_steps is None else n_steps
     m = gf.gf_medium_create(**wl.medium)
     init = gf.Rays.from_numpy(wl.x0, None)
     gf.gf_rays_onshell(m, init, torch.from_numpy(np.ascontiguousarray(wl.d.T)).cuda(), 1.0)
     rays = init.clone()
-    gf.gf_trace_rk4(m, rays, 1.0, wl.dt, 100)
+    gf.gf_trace_rk4(m, rays, 1.0, wl.dt, min(100, n_steps))
     rays = init.clone()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    gf.gf_trace_rk4(m, rays, 1.0, wl.dt, wl.n_steps)
+    gf.gf_trace_rk4(m, rays, 1.0, wl.dt, n_steps)
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     units = int(rays.steps.to(torch.int64).sum().item())
     flops = (4 * units + wl.n) * FLOPS_SPLINE_EVAL
-    return {"workload": f"{wl.n} rays, 128^3 tricubic spline grid (64 MiB FP32), RK4 dt=1e-3 x {wl.n_steps}, FP64",
+    return {"workload": f"{wl.n} rays, 128^3 tricubic spline grid (64 MiB FP32), RK4 dt=1e-3 x {n_steps}, FP64",
             "ms": ms, "ray_steps_per_s": units / (ms / 1e3),
             "achieved_tflops": flops / (ms / 1e3) / 1e12, "frac_fp64_peak": flops / (ms / 1e3) / 1e12 / peak_tflops,
             "max_abs_D": rays.d_max.max().item()}
+
+
+def measure_luneburg(gf, torch) -> dict:
+    """Luneburg lens workload (1,024 rays, RK4 dt = 1e-3 x 2000, FP64): far
+    less than one wave of the GPU (152 SMs x 5 blocks of 128), so it is bound
+    by the latency of one ray's 2000 sequential steps; time only.  Median of
+    five traces after one warm-up."""
+    wl = W.luneburg()
+    m = gf.gf_medium_create(**wl.medium)
+    init = gf.Rays.from_numpy(wl.x0, None)
+    gf.gf_rays_onshell(m, init, torch.from_numpy(np.ascontiguousarray(wl.d.T)).cuda(), 1.0)
+    ms = []
+    for it in range(6):
+        rays = init.clone()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        gf.gf_trace_rk4(m, rays, 1.0, wl.dt, wl.n_steps)
+        e1.record()
+        torch.cuda.synchronize()
+        if it > 0:
+            ms.append(e0.elapsed_time(e1))
+    t = statistics.median(ms)
+    return {"workload": f"{wl.n} rays, Luneburg lens, RK4 dt={wl.dt} x {wl.n_steps}, FP64",
+            "ms": t, "ray_steps_per_s": wl.n * wl.n_steps / (t / 1e3), "us_per_step": 1e3 * t / wl.n_steps}
 
 
 def measure_f64x(gf, torch, wl, m, x0, dirs, rays) -> dict:
@@ -490,6 +518,7 @@ def run_gpu(a):
     if world == 1 and not a.no_extras:
         if a.precision == "f64":
             line["f64x"] = measure_f64x(gf, torch, wl, m, x0, dirs, rays)
+        line["luneburg"] = measure_luneburg(gf, torch)
         line["aniso"] = measure_aniso(gf, torch, peak)
         line["adjoint"] = measure_adjoint(gf, torch)
         line["batched"] = measure_batched(gf, torch)
@@ -512,8 +541,11 @@ def run_workload(a):
     peak = SMS * 2 * 2 * sm * 1e6 / 1e12
     if a.workload == "batched":
         res = measure_batched(gf, torch, n_media=a.media)
+    elif a.workload == "luneburg":
+        res = measure_luneburg(gf, torch)
     elif a.workload == "aniso":
-        res = measure_aniso(gf, torch, peak)
+        full = inspect.signature(W.aniso).parameters["n_steps"].default
+        res = measure_aniso(gf, torch, peak, min(a.nsteps, full))
     elif a.workload == "adjoint":
         res = measure_adjoint(gf, torch)
     else:

@@ -96,7 +96,8 @@ typedef struct {
     const float *grid;          /* host, grid_n^3 nodes x 8 floats, x fastest, node
                                    (ix, iy, iz) at (-1 + ix h, ...), h = 2 / grid_n, holding
                                    (M11, M12, M13, M22, M23, M33, eps, unused); the values
-                                   are B-spline control coefficients (no prefilter)       */
+                                   are B-spline control coefficients (no prefilter), all
+                                   finite; subnormal values are read as zero              */
     /* GF_MED_COLD: species s has squared plasma frequency w_p,s^2 f(x) and signed
        cyclotron frequency Omega_s g(x), with f(x) = profile[0] + profile[1] x_0 (the
        density, e.g. the linear gradient 0.1 x + 1 of Eq. 4) and g(x) = profile[2] +
@@ -149,7 +150,8 @@ int32_t gf_version(void);
  * desc: host description (read during the call only).  out: receives a handle
  * owned by the caller until gf_medium_destroy.  Synchronous (blocking copy).
  * Errors: GF_ERR_INVALID_ARG (unknown kind, n_blobs out of range, non-positive
- * width or index, missing grid, reserved != 0), GF_ERR_OOM, GF_ERR_CUDA.
+ * width or index, missing grid, non-finite grid value, reserved != 0),
+ * GF_ERR_OOM, GF_ERR_CUDA.
  */
 gf_status gf_medium_create(const gf_medium_desc *desc, gf_medium *out);
 

@@ -69,17 +69,20 @@ __device__ __forceinline__ void base_hess_vec(const MediumParams &m, const doubl
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(kAdjBlock) adjoint_kernel(
+__global__ void __launch_bounds__(kAdjBlock, 1) adjoint_kernel(
     const MediumParams m, const int64_t n, const double omega, const double dt, const int64_t n_steps,
     const int64_t every, const double *__restrict__ ckpt, const int32_t *__restrict__ steps_done,
     const double *__restrict__ lambda, const int64_t ld, double *__restrict__ dy0, const AdjScratch S)
 {
-    __shared__ double sb[kBlobStride * GF_MAX_BLOBS];
+    __shared__ double sb[kBlobStride * GF_MAX_BLOBS];    // plain rows (reverse sweep)
+    __shared__ double sbs[kBlobStride * GF_MAX_BLOBS];   // scaled rows (recompute, as the forward kernel)
     __shared__ double sT[kExpTabN];
     extern __shared__ double tb[];   // thetabar columns: tb[j * blockDim + tid]
     const int nb = m.n_blobs;
-    // plain rows (A, c, s, 2 s): the sweep needs G_j = exp(s_j |x - c_j|^2) without A_j
-    for (int j = threadIdx.x; j < nb * kBlobStride; j += blockDim.x) sb[j] = m.blobs64[j];
+    for (int j = threadIdx.x; j < nb * kBlobStride; j += blockDim.x) {
+        sb[j] = m.blobs64[j];
+        sbs[j] = m.blobs64s[j];
+    }
     stage_exp_table(sT);
     for (int j = 0; j < nb; ++j) tb[j * blockDim.x + threadIdx.x] = 0.0;
     __syncthreads();
@@ -111,23 +114,12 @@ __global__ void __launch_bounds__(kAdjBlock) adjoint_kernel(
                     for (int c = 0; c < 6; ++c) Y[c] = st == 0 ? y[c] : y[c] + aa[st] * K[c];
                     double n2, g[3];
                     base_index<KIND>(m, Y, n2, g);
+                    // blob terms with the forward evaluator's arithmetic (scaled rows);
+                    // negligible terms (see kBlobCull) are stored as G = 0
                     double *Gs = S.G + ((int64_t)(s * 4 + st) * nb) * n + i;
-                    for (int j = 0; j < nb; ++j) {
-                        const double *b = sb + kBlobStride * j;
-                        const double dx = Y[0] - b[1], dy = Y[1] - b[2], dz = Y[2] - b[3];
-                        const double arg = (dx * dx + dy * dy + dz * dz) * b[4];
-                        double G = 0.0;   // negligible terms (see kBlobCull) are stored as 0
-                        if (!below_cull(arg)) {
-                            G = exp_tang(arg, sT);
-                            const double AG = b[0] * G;
-                            n2 += AG;
-                            const double cc = b[5] * AG;
-                            g[0] += cc * dx;
-                            g[1] += cc * dy;
-                            g[2] += cc * dz;
-                        }
-                        Gs[(int64_t)j * n] = G;
-                    }
+                    int live = 0;
+                    for (int j = 0; j < nb; ++j)
+                        Gs[(int64_t)j * n] = blob_term_scaled(sbs + kBlobStride * j, 1, Y, n2, g, sT, live);
                     double *Ss = S.stage + ((int64_t)(s * 4 + st) * kStageVals) * n + i;
 #pragma unroll
                     for (int c = 0; c < 6; ++c) Ss[c * n] = Y[c];
@@ -240,7 +232,7 @@ cudaError_t launch_adjoint(const MediumParams &m, int64_t n, double omega, doubl
     S.partials = (double *)base;
     S.stage = S.partials + blocks * nb;
     S.G = S.stage + every * 4 * kStageVals * n;
-    // thetabar columns (dynamic) next to the blob rows and the exp table (static, 19 KiB)
+    // thetabar columns (dynamic) next to the blob rows and the exp table (static, 22 KiB)
     const size_t smem = (size_t)nb * kAdjBlock * sizeof(double);
     cudaError_t e;
 #define GF_ADJ(K)                                                                                         \

@@ -257,14 +257,26 @@ gf_status gf_medium_create(const gf_medium_desc *d, gf_medium *out)
     p.pre32 = m->d_blobs32 + kBlobStride * nbl;
     if (d->kind == GF_MED_SPLINE) {
         size_t nodes = (size_t)d->grid_n * d->grid_n * d->grid_n;
-        for (size_t i = 0; i < nodes * 8; ++i)
+        // finite values only; subnormals (|v| < FLT_MIN) are stored as zero of the same
+        // sign (through a flushed host copy, made only when there is one)
+        bool subnormal = false;
+        for (size_t i = 0; i < nodes * 8; ++i) {
             if (!std::isfinite(d->grid[i])) {
                 set_error("gf_medium_create: grid value %zu is not finite", i);
                 free_medium(m);
                 return GF_ERR_INVALID_ARG;
             }
+            subnormal = subnormal || std::fpclassify(d->grid[i]) == FP_SUBNORMAL;
+        }
+        std::vector<float> flushed;
+        if (subnormal) {
+            flushed.assign(d->grid, d->grid + nodes * 8);
+            for (float &v : flushed)
+                if (std::fpclassify(v) == FP_SUBNORMAL) v = std::copysign(0.0f, v);
+        }
+        const float *src = subnormal ? flushed.data() : d->grid;
         if ((s = cuda_status(cudaMalloc(&m->d_grid, nodes * 8 * sizeof(float)), "cudaMalloc(grid)")) != GF_OK ||
-            (s = cuda_status(cudaMemcpy(m->d_grid, d->grid, nodes * 8 * sizeof(float),
+            (s = cuda_status(cudaMemcpy(m->d_grid, src, nodes * 8 * sizeof(float),
                                         cudaMemcpyHostToDevice), "cudaMemcpy(grid)")) != GF_OK) {
             free_medium(m);
             return s;

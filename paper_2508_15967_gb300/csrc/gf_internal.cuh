@@ -184,6 +184,7 @@ template <typename R>
 struct EvalCtx {
     const double *T = nullptr;   // 2^(j/2048) table (FP64 path)
     const float *pre = nullptr;  // FP32 pre-test rows, 4 floats per blob, or NULL
+    int pre_stride = 1;          // field f of blob j at pre[(4 j + f) * pre_stride]
     const float *dfb = nullptr;  // double-float blob rows (GF_F64X mode)
     const float *dfT = nullptr;  // double-float 2^(j/64) table (GF_F64X mode)
     int live = 0;                // blob terms evaluated (work counter)
@@ -193,6 +194,28 @@ struct EvalCtx {
 __device__ __forceinline__ void stage_pretest(const MediumParams &m, float *sp)
 {
     for (int j = threadIdx.x; j < m.n_blobs * 4; j += blockDim.x) sp[j] = m.pre32[j];
+}
+
+// One Gaussian-blob term on a scaled row b (field f at b[f * stride]):
+// u = sigma x - sigma c, G = exp(-|u|^2) = exp(s |x - c|^2); for a term that is
+// not negligible (exponent >= -40.5) adds A G to n2 and (-2 sigma A) G u to g
+// and counts it in live.  Returns G, or 0 for a negligible term.
+__device__ __forceinline__ double blob_term_scaled(const double *__restrict__ b, int stride, const double *x,
+                                                   double &n2, double *g, const double *__restrict__ T, int &live)
+{
+    const double sg = b[0];
+    const double u0 = fma(sg, x[0], b[stride]), u1 = fma(sg, x[1], b[2 * stride]),
+                 u2 = fma(sg, x[2], b[3 * stride]);
+    const double a = fma(-u2, u2, fma(-u1, u1, -(u0 * u0)));
+    if (below_cull(a)) return 0.0;
+    const double G = exp_tang(a, T);
+    n2 = fma(b[4 * stride], G, n2);
+    const double c = b[5 * stride] * G;
+    g[0] = fma(c, u0, g[0]);
+    g[1] = fma(c, u1, g[1]);
+    g[2] = fma(c, u2, g[2]);
+    ++live;
+    return G;
 }
 
 // Squared index n^2 and its gradient for an isotropic medium of kind KIND plus
@@ -246,25 +269,13 @@ __device__ __forceinline__ void iso_index(const MediumParams &m, const R *__rest
 #pragma unroll 2
         for (int j = 0; j < nb; ++j) {
             if (pre) {
-                const float *bp = cx.pre + 4 * j;
-                const float v0 = fmaf(bp[0], xf0, bp[1]), v1 = fmaf(bp[0], xf1, bp[2]),
-                            v2 = fmaf(bp[0], xf2, bp[3]);
+                const int ps = cx.pre_stride;
+                const float *bp = cx.pre + 4 * j * ps;
+                const float v0 = fmaf(bp[0], xf0, bp[ps]), v1 = fmaf(bp[0], xf1, bp[2 * ps]),
+                            v2 = fmaf(bp[0], xf2, bp[3 * ps]);
                 if (v0 * v0 + v1 * v1 + v2 * v2 > kBlobCullQF) continue;
             }
-            const double *b = sb + kBlobStride * j * stride;
-            const double sg = b[0];
-            const double u0 = fma(sg, x[0], b[stride]), u1 = fma(sg, x[1], b[2 * stride]),
-                         u2 = fma(sg, x[2], b[3 * stride]);
-            const double a = fma(-u2, u2, fma(-u1, u1, -(u0 * u0)));
-            if (!below_cull(a)) {
-                const double G = exp_tang(a, cx.T);
-                n2 = fma(b[4 * stride], G, n2);
-                const double c = b[5 * stride] * G;
-                g[0] = fma(c, u0, g[0]);
-                g[1] = fma(c, u1, g[1]);
-                g[2] = fma(c, u2, g[2]);
-                ++cx.live;
-            }
+            blob_term_scaled(sb + kBlobStride * j * stride, stride, x, n2, g, cx.T, cx.live);
         }
     } else {
         // plain rows: A exp(s |x - c|^2) and its gradient 2 s A exp(.) (x - c)
@@ -336,6 +347,26 @@ __device__ __forceinline__ void bspline_w(R f, R inv_h, R *B, R *dB)
     dB[3] = (R)0.5 * f2 * inv_h;
 }
 
+// Grid value as R.  For double the widening float -> double is done on the
+// bit pattern with integer operations (exact: the exponent is re-biased by
+// 1023 - 127 and the significand gains 29 zero bits), which keeps the 28
+// conversions of every grid row off the FP64 pipe.  Valid for zeros and
+// normal floats: the device copy of the grid holds no subnormal, infinite or
+// NaN value (gf_medium_create rejects non-finite values and flushes
+// subnormals to zero).
+template <typename R>
+__device__ __forceinline__ R grid_value(float v);
+template <>
+__device__ __forceinline__ float grid_value<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ double grid_value<double>(float v)
+{
+    const unsigned b = __float_as_uint(v);
+    const unsigned mag = b & 0x7FFFFFFFu;
+    const unsigned hi = (b & 0x80000000u) | ((mag >> 3) + (mag != 0u ? (1023u - 127u) << 20 : 0u));
+    return __hiloint2double((int)hi, (int)(b << 29));
+}
+
 template <typename R>
 __device__ __forceinline__ void spline_fields(const MediumParams &m, const R *x, R *val, R (*grad)[3])
 {
@@ -377,7 +408,8 @@ __device__ __forceinline__ void spline_fields(const MediumParams &m, const R *x,
             for (int a = 0; a < 4; ++a) {
                 float4 lo = __ldg(row + 2 * ix[a]);
                 float4 hi = __ldg(row + 2 * ix[a] + 1);
-                R v[7] = {(R)lo.x, (R)lo.y, (R)lo.z, (R)lo.w, (R)hi.x, (R)hi.y, (R)hi.z};
+                R v[7] = {grid_value<R>(lo.x), grid_value<R>(lo.y), grid_value<R>(lo.z), grid_value<R>(lo.w),
+                          grid_value<R>(hi.x), grid_value<R>(hi.y), grid_value<R>(hi.z)};
 #pragma unroll
                 for (int ch = 0; ch < 7; ++ch) {
                     sx[ch] += B[0][a] * v[ch];
