@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--workload", choices=["grin", "luneburg", "batched", "aniso", "adjoint", "generated"],
                     default="grin", help="grin: the headline line; others print that measurement alone")
     ap.add_argument("--media", type=int, default=4096, help="batched: number of media")
+    ap.add_argument("--tune-cache", default=None,
+                    help="batched: autotuner cache file (written after tuning, reused when it holds the shape)")
     return ap.parse_args()
 
 
@@ -540,7 +542,7 @@ def run_workload(a):
     sm = 2070.0
     peak = SMS * 2 * 2 * sm * 1e6 / 1e12
     if a.workload == "batched":
-        res = measure_batched(gf, torch, n_media=a.media)
+        res = measure_batched(gf, torch, tune_cache=a.tune_cache, n_media=a.media)
     elif a.workload == "luneburg":
         res = measure_luneburg(gf, torch)
     elif a.workload == "aniso":

@@ -54,6 +54,16 @@ gf_status gf_bench_exp(const double *in, double *out_lib, double *out_cuda, int6
  */
 gf_status gf_bench_exp_df(const double *in, double *out, int64_t n, void *stream);
 
+/*
+ * gf_bench_recip -- evaluate the FP64 evaluator's reciprocal of n^2 (an FP32
+ * seed refined by one cubic Newton step; out_recip[i] = 1/in[i] for in[i] > 0,
+ * 0 otherwise) and its double -> float truncation of positions (out_narrow)
+ * on n device doubles `in`, so that tests can bound their errors.
+ * Stream-ordered on `stream`.  Errors: GF_ERR_INVALID_ARG (n < 0, non-device
+ * pointers), GF_ERR_CUDA.
+ */
+gf_status gf_bench_recip(const double *in, double *out_recip, float *out_narrow, int64_t n, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -88,6 +88,7 @@ def lib() -> C.CDLL:
             "gf_bench_set_counters": ([P], I32),
             "gf_bench_exp": ([P, P, P, I64, P], I32),
             "gf_bench_exp_df": ([P, P, I64, P], I32),
+            "gf_bench_recip": ([P, P, P, I64, P], I32),
             "gf_adjoint_scratch_bytes": ([P, I64, I64], C.c_size_t),
             "gf_trace_adjoint": ([P, I64, D, D, I64, I64, P, P, P, I64, P, P, P, C.c_size_t, P], I32),
             "gf_trace_adjoint_static": ([P, I64, D, D, I64, I64, P, P, P, I64, P, P, P], I32),
@@ -469,6 +470,15 @@ def gf_bench_exp_df(a: torch.Tensor) -> torch.Tensor:
     o = torch.empty_like(a)
     _check("gf_bench_exp_df", lib().gf_bench_exp_df(_ptr(a), _ptr(o), a.numel(), _stream(None)))
     return o
+
+
+def gf_bench_recip(a: torch.Tensor):
+    """(FP64 evaluator's 1/a for a > 0 else 0, float truncation of a) of a float64 device tensor."""
+    a = a.contiguous()
+    o1 = torch.empty_like(a)
+    o2 = torch.empty(a.shape, dtype=torch.float32, device=a.device)
+    _check("gf_bench_recip", lib().gf_bench_recip(_ptr(a), _ptr(o1), _ptr(o2), a.numel(), _stream(None)))
+    return o1, o2
 
 
 def medium_from_workload(spec: dict) -> Medium:

@@ -77,12 +77,14 @@ __global__ void __launch_bounds__(kAdjBlock, 1) adjoint_kernel(
     __shared__ double sb[kBlobStride * GF_MAX_BLOBS];    // plain rows (reverse sweep)
     __shared__ double sbs[kBlobStride * GF_MAX_BLOBS];   // scaled rows (recompute, as the forward kernel)
     __shared__ double sT[kExpTabN];
+    __shared__ float sp[4 * GF_MAX_BLOBS];               // FP32 pre-test rows (recompute)
     extern __shared__ double tb[];   // thetabar columns: tb[j * blockDim + tid]
     const int nb = m.n_blobs;
     for (int j = threadIdx.x; j < nb * kBlobStride; j += blockDim.x) {
         sb[j] = m.blobs64[j];
         sbs[j] = m.blobs64s[j];
     }
+    for (int j = threadIdx.x; j < nb * 4; j += blockDim.x) sp[j] = m.pre32[j];
     stage_exp_table(sT);
     for (int j = 0; j < nb; ++j) tb[j * blockDim.x + threadIdx.x] = 0.0;
     __syncthreads();
@@ -114,12 +116,15 @@ __global__ void __launch_bounds__(kAdjBlock, 1) adjoint_kernel(
                     for (int c = 0; c < 6; ++c) Y[c] = st == 0 ? y[c] : y[c] + aa[st] * K[c];
                     double n2, g[3];
                     base_index<KIND>(m, Y, n2, g);
-                    // blob terms with the forward evaluator's arithmetic (scaled rows);
-                    // negligible terms (see kBlobCull) are stored as G = 0
+                    // blob terms with the forward evaluator's arithmetic (scaled rows,
+                    // FP32 pre-test); negligible terms (see kBlobCull) are stored as G = 0
                     double *Gs = S.G + ((int64_t)(s * 4 + st) * nb) * n + i;
+                    const PreX px = pretest_point(m, Y);
                     int live = 0;
                     for (int j = 0; j < nb; ++j)
-                        Gs[(int64_t)j * n] = blob_term_scaled(sbs + kBlobStride * j, 1, Y, n2, g, sT, live);
+                        Gs[(int64_t)j * n] = (px.on && pretest_negligible(sp + 4 * j, 1, px))
+                                                 ? 0.0
+                                                 : blob_term_scaled(sbs + kBlobStride * j, 1, Y, n2, g, sT, live);
                     double *Ss = S.stage + ((int64_t)(s * 4 + st) * kStageVals) * n + i;
 #pragma unroll
                     for (int c = 0; c < 6; ++c) Ss[c * n] = Y[c];
@@ -127,7 +132,7 @@ __global__ void __launch_bounds__(kAdjBlock, 1) adjoint_kernel(
                     Ss[7 * n] = g[0];
                     Ss[8 * n] = g[1];
                     Ss[9 * n] = g[2];
-                    const double inv = 1.0 / n2;
+                    const double inv = recip_pos(n2);
                     const double a = inv / omega, bq = 0.5 * omega * inv;
                     K[0] = a * Y[3];
                     K[1] = a * Y[4];
@@ -154,7 +159,7 @@ __global__ void __launch_bounds__(kAdjBlock, 1) adjoint_kernel(
 #pragma unroll
                     for (int c = 0; c < 6; ++c) Y[c] = Ss[c * n];
                     const double n2 = Ss[6 * n], g0 = Ss[7 * n], g1 = Ss[8 * n], g2 = Ss[9 * n];
-                    const double u = 1.0 / n2;
+                    const double u = recip_pos(n2);
                     const double a = u / omega, bq = 0.5 * omega * u;
                     const double C = -u * (a * (Y[3] * Kb[0] + Y[4] * Kb[1] + Y[5] * Kb[2]) +
                                            bq * (g0 * Kb[3] + g1 * Kb[4] + g2 * Kb[5]));
@@ -162,9 +167,10 @@ __global__ void __launch_bounds__(kAdjBlock, 1) adjoint_kernel(
                     base_hess_vec<KIND>(m, Y, Kb + 3, HK);
                     const double *Gs = S.G + ((int64_t)(s * 4 + st) * nb) * n + i;
                     for (int j = 0; j < nb; ++j) {
+                        const double G = Gs[(int64_t)j * n];
+                        if (G == 0.0) continue;   // negligible term: no contribution
                         const double *b = sb + kBlobStride * j;
                         const double dx = Y[0] - b[1], dy = Y[1] - b[2], dz = Y[2] - b[3];
-                        const double G = Gs[(int64_t)j * n];
                         const double dK = dx * Kb[3] + dy * Kb[4] + dz * Kb[5];
                         const double s2 = b[5];
                         acc_t[j * B] += G * (C + bq * s2 * dK);
@@ -232,7 +238,7 @@ cudaError_t launch_adjoint(const MediumParams &m, int64_t n, double omega, doubl
     S.partials = (double *)base;
     S.stage = S.partials + blocks * nb;
     S.G = S.stage + every * 4 * kStageVals * n;
-    // thetabar columns (dynamic) next to the blob rows and the exp table (static, 22 KiB)
+    // thetabar columns (dynamic) next to the blob rows, pre-test rows and exp table (static, 23 KiB)
     const size_t smem = (size_t)nb * kAdjBlock * sizeof(double);
     cudaError_t e;
 #define GF_ADJ(K)                                                                                         \

@@ -72,7 +72,34 @@ __global__ void exp_check_kernel(const double *in, double *out_lib, double *out_
     out_cuda[i] = exp(in[i]);
 }
 
+__global__ void recip_check_kernel(const double *in, double *out_recip, float *out_narrow, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = in[i];
+    out_recip[i] = v > 0.0 ? recip_pos(v) : 0.0;
+    out_narrow[i] = narrow_trunc(v);
+}
+
 }  // namespace gf
+
+extern "C" gf_status gf_bench_recip(const double *in, double *out_recip, float *out_narrow, int64_t n,
+                                    void *stream)
+{
+    if (n < 0) {
+        gf::set_error("gf_bench_recip: n < 0");
+        return GF_ERR_INVALID_ARG;
+    }
+    if (n == 0) return GF_OK;
+    gf_status s;
+    if ((s = gf::check_device_ptr(in, "in")) != GF_OK ||
+        (s = gf::check_device_ptr(out_recip, "out_recip")) != GF_OK ||
+        (s = gf::check_device_ptr(out_narrow, "out_narrow")) != GF_OK)
+        return s;
+    gf::recip_check_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(in, out_recip,
+                                                                                         out_narrow, n);
+    return gf::cuda_status(cudaGetLastError(), "gf_bench_recip launch");
+}
 
 extern "C" gf_status gf_bench_exp(const double *in, double *out_lib, double *out_cuda, int64_t n,
                                   void *stream)

@@ -31,6 +31,7 @@ constexpr double e1 = 35.0 / 384.0 - 5179.0 / 57600.0, e3 = 500.0 / 1113.0 - 757
 
 struct Ctl {
     double rtol, atol, h0, t_max, r2, fac_min, fac_max, safety;
+    float safety_f;
     int64_t max_steps, max_attempts;
     Omega<double> om;
 };
@@ -39,6 +40,8 @@ struct Ctl {
 struct BatchView {
     int32_t n_media, nb_max, n_items, pad;
     const double *blobs;        // n_media x nb_max scaled rows (kBlobStride values each)
+    const float *pre;           // n_media x nb_max FP32 pre-test rows (4 floats each)
+    const float *pre_lim;       // n_media: validity bound of the pre-test (MediumParams::pre_lim)
     const int32_t *nb;          // n_media
     const double *base;         // n_media x 3: n_h2, n02, n02a2
     const int32_t *item_medium; // n_items
@@ -58,6 +61,7 @@ template <int KIND>
 struct LaneRhs {
     const Lane &L;
     const double *sm;
+    const float *pf;
     int stride;
     const Omega<double> &om;
     const double *T;
@@ -66,17 +70,20 @@ struct LaneRhs {
     {
         EvalCtx<double> cx;
         cx.T = T;
+        cx.pre = pf;
+        cx.pre_stride = stride;
         return rhs_iso<double, KIND, WANT_D>(L.mp, sm, L.nb, om, y, f, D, cx, stride);
     }
 };
 
 // Load ray `ray` of medium `med` into lane L and its per-thread shared-memory
-// blob slot (field f of blob j at sm[(kBlobStride j + f) * stride]).  Returns false if
-// the ray is not active.
+// blob slot (field f of blob j at sm[(kBlobStride j + f) * stride], FP32
+// pre-test field f at pf[(4 j + f) * stride]).  Returns false if the ray is
+// not active.
 template <int KIND>
 __device__ __forceinline__ bool lane_load(Lane &L, const BatchView &B, const RaysView<double> &r,
-                                          int med, int64_t ray, double *sm, int stride, const double *T,
-                                          const Ctl &c)
+                                          int med, int64_t ray, double *sm, float *pf, int stride,
+                                          const double *T, const Ctl &c)
 {
     L.status = r.status[ray];
     if (L.status != GF_RAY_ACTIVE) return false;
@@ -88,6 +95,11 @@ __device__ __forceinline__ bool lane_load(Lane &L, const BatchView &B, const Ray
     L.mp.n02a2 = B.base[3 * med + 2];
     const double *src = B.blobs + (int64_t)med * B.nb_max * kBlobStride;
     for (int j = 0; j < L.nb * kBlobStride; ++j) sm[j * stride] = src[j];
+    if (pf != nullptr) {
+        L.mp.pre_lim = B.pre_lim[med];
+        const float *psrc = B.pre + (int64_t)med * B.nb_max * 4;
+        for (int j = 0; j < L.nb * 4; ++j) pf[j * stride] = psrc[j];
+    }
 #pragma unroll
     for (int c2 = 0; c2 < 6; ++c2) L.y[c2] = r.y[c2 * r.ld + ray];
     L.t = r.t[ray];
@@ -98,7 +110,7 @@ __device__ __forceinline__ bool lane_load(Lane &L, const BatchView &B, const Ray
     L.h = c.h0;
     L.fmax = c.fac_max;
     double D;
-    const LaneRhs<KIND> f{L, sm, stride, c.om, T};
+    const LaneRhs<KIND> f{L, sm, pf, stride, c.om, T};
     bool ok = f.eval(L.y, L.K1, D);
     L.dm = fmax(L.dm, fabs(D));
     if (!ok) L.status = GF_RAY_CUTOFF;
@@ -108,10 +120,11 @@ __device__ __forceinline__ bool lane_load(Lane &L, const BatchView &B, const Ray
 // Final residual and store of a lane whose ray stopped.
 template <int KIND>
 __device__ __forceinline__ void lane_store(const Lane &L, const RaysView<double> &r, int32_t *rejects,
-                                           const double *sm, int stride, const double *T, const Ctl &c)
+                                           const double *sm, const float *pf, int stride, const double *T,
+                                           const Ctl &c)
 {
     double K[6], D;
-    const LaneRhs<KIND> f{L, sm, stride, c.om, T};
+    const LaneRhs<KIND> f{L, sm, pf, stride, c.om, T};
     f.eval(L.y, K, D);
     const double dm = fmax(L.dm, fabs(D));
     const int64_t i = L.ray;
@@ -128,8 +141,8 @@ __device__ __forceinline__ void lane_store(const Lane &L, const RaysView<double>
 // One attempted DOPRI5 step of an active lane (the step-size controller of
 // Hairer-Norsett-Wanner I, Sec. II.4).  Leaves L.status != ACTIVE when the ray stops.
 template <int KIND>
-__device__ __forceinline__ void lane_attempt(Lane &L, const double *sm, int stride, const double *T,
-                                             const Ctl &c)
+__device__ __forceinline__ void lane_attempt(Lane &L, const double *sm, const float *pf, int stride,
+                                             const double *T, const Ctl &c)
 {
     using namespace dp;
     if (L.steps >= c.max_steps || L.attempts >= c.max_attempts) { L.status = GF_RAY_MAX_STEPS; return; }
@@ -139,7 +152,7 @@ __device__ __forceinline__ void lane_attempt(Lane &L, const double *sm, int stri
     bool last = false;
     if (L.t + hs >= c.t_max) { hs = c.t_max - L.t; last = true; }
     if (hs < 1e-14 * fmax(1.0, fabs(L.t))) { L.status = GF_RAY_STEP_UNDERFLOW; return; }
-    const LaneRhs<KIND> f{L, sm, stride, c.om, T};
+    const LaneRhs<KIND> f{L, sm, pf, stride, c.om, T};
     const double *y = L.y, *K1 = L.K1;
     double K2[6], K3[6], K4[6], K5[6], K6[6], K7[6], Y[6], D;
 #pragma unroll
@@ -167,16 +180,21 @@ __device__ __forceinline__ void lane_attempt(Lane &L, const double *sm, int stri
 #pragma unroll
     for (int i = 0; i < 6; ++i) fin = fin && isfinite(Y[i]) && isfinite(K7[i]);
     if (!fin) { L.status = GF_RAY_NONFINITE; return; }
-    double err = 0.0;
+    // The embedded error estimate e (FP64: a small difference of O(1) terms)
+    // is scaled and normed in FP32, as is the step factor: the controller is
+    // a heuristic, and the FP32 norm differs from an FP64 one by ~1e-7
+    // relative, which can only flip an accept decision for err within that of 1.
+    float err2 = 0.0f;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        double e = hs * (e1 * K1[i] + e3 * K3[i] + e4 * K4[i] + e5 * K5[i] + e6 * K6[i] + e7 * K7[i]);
-        double sc = c.atol + c.rtol * fmax(fabs(y[i]), fabs(Y[i]));
-        double q = e / sc;
-        err += q * q;
+        const double e = hs * (e1 * K1[i] + e3 * K3[i] + e4 * K4[i] + e5 * K5[i] + e6 * K6[i] + e7 * K7[i]);
+        const double sc = c.atol + c.rtol * fmax(fabs(y[i]), fabs(Y[i]));
+        const float q = (float)e / (float)sc;
+        err2 = fmaf(q, q, err2);
     }
-    err = sqrt(err / 6.0);
-    const double fac = err > 0.0 ? c.safety * pow(err, -0.2) : L.fmax;
+    const float errf = sqrtf(err2 * (1.0f / 6.0f));
+    const double err = errf;
+    const double fac = errf > 0.0f ? (double)(c.safety_f * powf(errf, -0.2f)) : L.fmax;
     if (err <= 1.0) {
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
@@ -210,12 +228,14 @@ __global__ void __launch_bounds__(128) dopri5_medium_kernel(const BatchView B, c
     __syncthreads();
     const int stride = blockDim.x;
     double *sm = sm_dyn + threadIdx.x;
+    float *pf = B.pre ? reinterpret_cast<float *>(sm_dyn + (size_t)B.nb_max * kBlobStride * stride) + threadIdx.x
+                      : nullptr;
     const int64_t ray = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (ray >= hi) return;
     Lane L;
-    if (!lane_load<KIND>(L, B, r, med, ray, sm, stride, sT, c)) return;
-    while (L.status == GF_RAY_ACTIVE) lane_attempt<KIND>(L, sm, stride, sT, c);
-    lane_store<KIND>(L, r, rejects, sm, stride, sT, c);
+    if (!lane_load<KIND>(L, B, r, med, ray, sm, pf, stride, sT, c)) return;
+    while (L.status == GF_RAY_ACTIVE) lane_attempt<KIND>(L, sm, pf, stride, sT, c);
+    lane_store<KIND>(L, r, rejects, sm, pf, stride, sT, c);
 }
 
 // ------------------------------------------------------------- persistent
@@ -235,6 +255,7 @@ __global__ void dopri5_persistent_kernel(const BatchView B, const RaysView<doubl
     stage_exp_table(sT);
     __syncthreads();
     const int stride = blockDim.x * RPT;
+    float *pf_base = B.pre ? reinterpret_cast<float *>(sm_dyn + (size_t)B.nb_max * kBlobStride * stride) : nullptr;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
     Lane L[RPT];
@@ -248,6 +269,7 @@ __global__ void dopri5_persistent_kernel(const BatchView B, const RaysView<doubl
 #pragma unroll
         for (int s = 0; s < RPT; ++s) {
             double *sm = sm_dyn + s * blockDim.x + threadIdx.x;
+            float *pf = pf_base ? pf_base + s * blockDim.x + threadIdx.x : nullptr;
             unsigned freem = __ballot_sync(0xffffffffu, !active[s]);
             while (freem != 0u && !exhausted) {
                 if (cur >= end) {
@@ -266,11 +288,11 @@ __global__ void dopri5_persistent_kernel(const BatchView B, const RaysView<doubl
                 const int take = (int)min((int64_t)nfree, end - cur);
                 const int rank = __popc(freem & lt_mask);
                 if (!active[s] && rank < take) {
-                    if (lane_load<KIND>(L[s], B, r, cur_med, cur + rank, sm, stride, sT, c)) {
+                    if (lane_load<KIND>(L[s], B, r, cur_med, cur + rank, sm, pf, stride, sT, c)) {
                         if (L[s].status == GF_RAY_ACTIVE)
                             active[s] = true;
                         else
-                            lane_store<KIND>(L[s], r, rejects, sm, stride, sT, c);
+                            lane_store<KIND>(L[s], r, rejects, sm, pf, stride, sT, c);
                     }
                 }
                 cur += take;
@@ -286,9 +308,10 @@ __global__ void dopri5_persistent_kernel(const BatchView B, const RaysView<doubl
             for (int s = 0; s < RPT; ++s) {
                 if (active[s]) {
                     double *sm = sm_dyn + s * blockDim.x + threadIdx.x;
-                    lane_attempt<KIND>(L[s], sm, stride, sT, c);
+                    float *pf = pf_base ? pf_base + s * blockDim.x + threadIdx.x : nullptr;
+                    lane_attempt<KIND>(L[s], sm, pf, stride, sT, c);
                     if (L[s].status != GF_RAY_ACTIVE) {
-                        lane_store<KIND>(L[s], r, rejects, sm, stride, sT, c);
+                        lane_store<KIND>(L[s], r, rejects, sm, pf, stride, sT, c);
                         active[s] = false;
                     }
                 }
@@ -313,6 +336,7 @@ struct gf_batch_s {
     int kind = 0, n_media = 0, nb_max = 0;
     std::vector<int64_t> offsets;
     double *d_blobs = nullptr, *d_base = nullptr;
+    float *d_pre = nullptr, *d_pre_lim = nullptr;
     int32_t *d_nb = nullptr;
     int *d_head = nullptr;
     // work items for the current chunk size
@@ -332,6 +356,8 @@ const double *medium_device_blobs(gf_medium m);
 static void batch_free(gf_batch b)
 {
     cudaFree(b->d_blobs);
+    cudaFree(b->d_pre);
+    cudaFree(b->d_pre_lim);
     cudaFree(b->d_base);
     cudaFree(b->d_nb);
     cudaFree(b->d_head);
@@ -379,10 +405,21 @@ static gf_status build_items(gf_batch b, int chunk)
     return GF_OK;
 }
 
-static BatchView view_of(gf_batch b)
+// Device view of a batch; pre = false leaves the pre-test tables out (the
+// kernels then decide every blob term in FP64).
+static BatchView view_of(gf_batch b, bool pre)
 {
-    return BatchView{b->n_media, b->nb_max, b->n_items, 0, b->d_blobs, b->d_nb, b->d_base,
-                     b->d_item_medium, b->d_item_begin, b->d_item_end};
+    return BatchView{b->n_media, b->nb_max, b->n_items, 0, b->d_blobs,
+                     pre ? b->d_pre : nullptr, pre ? b->d_pre_lim : nullptr, b->d_nb,
+                     b->d_base, b->d_item_medium, b->d_item_begin, b->d_item_end};
+}
+
+// Every table a launch reads must exist (a view over missing tables would
+// make the kernels read through null pointers).
+static bool view_complete(gf_batch b, bool pre, gf_schedule sched)
+{
+    return b->d_blobs && b->d_nb && b->d_base && (!pre || (b->d_pre && b->d_pre_lim)) &&
+           (sched != GF_SCHED_PERSISTENT || (b->d_head && b->d_item_medium && b->d_item_begin && b->d_item_end));
 }
 
 static Ctl ctl_of(const gf_step_ctl *c, double omega)
@@ -397,6 +434,7 @@ static Ctl ctl_of(const gf_step_ctl *c, double omega)
     k.fac_min = c->fac_min;
     k.fac_max = c->fac_max;
     k.safety = c->safety;
+    k.safety_f = (float)c->safety;
     k.max_steps = c->max_steps;
     // rejections shrink h geometrically to h_min, so attempts are bounded; this
     // cap only guards against a controller that never converges
@@ -430,12 +468,30 @@ static gf_status check_tune(const gf_tune *t)
 
 static const gf_tune kDefaultTune = {128, 1, 4, 64};
 
+// Shared memory of one lane slot: scaled FP64 rows, and FP32 pre-test rows
+// when `pre`.
+static size_t lane_slot_bytes(int nb_max, bool pre)
+{
+    return (size_t)nb_max * (kBlobStride * sizeof(double) + (pre ? 4 * sizeof(float) : 0));
+}
+
+// Lane slots of a launch may take this much dynamic shared memory; a shape
+// whose slots with pre-test rows would exceed it runs without the pre-test.
+constexpr size_t kMaxLaneSmem = 200 * 1024;
+
 // Launch shape resolved outside any stream capture (function attributes and
 // occupancy queries are not stream work).
 struct LaunchPlan {
     int grid = 0, block = 128, rpt = 1;
     size_t smem = 0;
+    bool pre = true;   // lane slots hold the FP32 pre-test rows
 };
+
+static void size_slots(gf_batch b, int lanes, LaunchPlan &p)
+{
+    p.pre = lane_slot_bytes(b->nb_max, true) * lanes <= kMaxLaneSmem;
+    p.smem = lane_slot_bytes(b->nb_max, p.pre) * lanes;
+}
 
 template <int KIND, int RPT>
 static cudaError_t plan_persistent_rpt(gf_batch b, const gf_tune &t, LaunchPlan &p)
@@ -443,7 +499,7 @@ static cudaError_t plan_persistent_rpt(gf_batch b, const gf_tune &t, LaunchPlan 
     auto k = dopri5_persistent_kernel<KIND, RPT>;
     p.block = t.block;
     p.rpt = RPT;
-    p.smem = (size_t)b->nb_max * kBlobStride * sizeof(double) * t.block * RPT;
+    size_slots(b, t.block * RPT, p);
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -464,7 +520,7 @@ static cudaError_t plan(gf_batch b, gf_schedule sched, const gf_tune &t, LaunchP
         return t.rays_per_thread == 1 ? plan_persistent_rpt<KIND, 1>(b, t, p)
                                       : plan_persistent_rpt<KIND, 2>(b, t, p);
     p.block = 128;
-    p.smem = (size_t)b->nb_max * kBlobStride * sizeof(double) * p.block;
+    size_slots(b, p.block, p);
     return cudaFuncSetAttribute(dopri5_medium_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)p.smem);
 }
@@ -474,7 +530,7 @@ static cudaError_t launch(gf_batch b, gf_schedule sched, const gf_tune &t, const
                           const RaysView<double> &r, int32_t *rejects, double omega, const Ctl &c,
                           cudaStream_t s)
 {
-    const BatchView B = view_of(b);
+    const BatchView B = view_of(b, p.pre);
     if (sched == GF_SCHED_PERSISTENT) {
         cudaError_t e = cudaMemsetAsync(b->d_head, 0, sizeof(int), s);
         if (e != cudaSuccess) return e;
@@ -540,6 +596,10 @@ static gf_status run_dopri5(gf_batch b, const gf_rays *rays, int32_t *rejects, d
     const Ctl c = ctl_of(ctl, omega);
     LaunchPlan p;
     if ((s = cuda_status(plan_any(b, sched, t, p), "gf_trace_dopri5 launch plan")) != GF_OK) return s;
+    if (!view_complete(b, p.pre, sched)) {
+        set_error("gf_trace_dopri5: batch tables missing");
+        return GF_ERR_INVALID_ARG;
+    }
     if (!use_graph)
         return cuda_status(enqueue(b, sched, t, p, r, rejects, omega, c, stream), "gf_trace_dopri5 launch");
     GraphCache &g = b->graphs[sched];
@@ -674,10 +734,13 @@ gf_status gf_batch_create(const gf_medium *media, int32_t n_media, const int64_t
     b->nb_max = std::max(nb_max, 1);
     b->offsets.assign(offsets, offsets + n_media + 1);
     std::vector<double> base(3 * (size_t)n_media);
+    std::vector<float> pre_lim(n_media);
     std::vector<int32_t> nb(n_media);
     gf_status s = GF_OK;
-    const size_t row = (size_t)b->nb_max * kBlobStride;
+    const size_t row = (size_t)b->nb_max * kBlobStride, prow = (size_t)b->nb_max * 4;
     if ((s = cuda_status(cudaMalloc(&b->d_blobs, row * n_media * sizeof(double)), "cudaMalloc(batch)")) != GF_OK ||
+        (s = cuda_status(cudaMalloc(&b->d_pre, prow * n_media * sizeof(float)), "cudaMalloc(batch)")) != GF_OK ||
+        (s = cuda_status(cudaMalloc(&b->d_pre_lim, pre_lim.size() * sizeof(float)), "cudaMalloc(batch)")) != GF_OK ||
         (s = cuda_status(cudaMalloc(&b->d_base, base.size() * sizeof(double)), "cudaMalloc(batch)")) != GF_OK ||
         (s = cuda_status(cudaMalloc(&b->d_nb, nb.size() * sizeof(int32_t)), "cudaMalloc(batch)")) != GF_OK ||
         (s = cuda_status(cudaMalloc(&b->d_head, sizeof(int)), "cudaMalloc(batch)")) != GF_OK) {
@@ -689,16 +752,21 @@ gf_status gf_batch_create(const gf_medium *media, int32_t n_media, const int64_t
         base[3 * m] = p.n_h2;
         base[3 * m + 1] = p.n02;
         base[3 * m + 2] = p.n02a2;
+        pre_lim[m] = p.pre_lim;
         nb[m] = p.n_blobs;
         if (p.n_blobs > 0 &&
-            (s = cuda_status(cudaMemcpy(b->d_blobs + row * m, medium_device_blobs(media[m]),
-                                        p.n_blobs * kBlobStride * sizeof(double), cudaMemcpyDeviceToDevice),
-                             "cudaMemcpy(batch blobs)")) != GF_OK) {
+            ((s = cuda_status(cudaMemcpy(b->d_blobs + row * m, medium_device_blobs(media[m]),
+                                         p.n_blobs * kBlobStride * sizeof(double), cudaMemcpyDeviceToDevice),
+                              "cudaMemcpy(batch blobs)")) != GF_OK ||
+             (s = cuda_status(cudaMemcpy(b->d_pre + prow * m, p.pre32, p.n_blobs * 4 * sizeof(float),
+                                         cudaMemcpyDeviceToDevice), "cudaMemcpy(batch blobs)")) != GF_OK)) {
             batch_free(b);
             return s;
         }
     }
     if ((s = cuda_status(cudaMemcpy(b->d_base, base.data(), base.size() * sizeof(double),
+                                    cudaMemcpyHostToDevice), "cudaMemcpy(batch)")) != GF_OK ||
+        (s = cuda_status(cudaMemcpy(b->d_pre_lim, pre_lim.data(), pre_lim.size() * sizeof(float),
                                     cudaMemcpyHostToDevice), "cudaMemcpy(batch)")) != GF_OK ||
         (s = cuda_status(cudaMemcpy(b->d_nb, nb.data(), nb.size() * sizeof(int32_t), cudaMemcpyHostToDevice),
                          "cudaMemcpy(batch)")) != GF_OK) {
@@ -788,6 +856,8 @@ gf_status gf_dopri5_autotune(gf_batch b, const gf_rays *rays, double omega, cons
     sub.offsets.assign(b->offsets.begin(), b->offsets.begin() + m_end + 1);
     for (auto &o : sub.offsets) o -= lo;
     sub.d_blobs = b->d_blobs;
+    sub.d_pre = b->d_pre;
+    sub.d_pre_lim = b->d_pre_lim;
     sub.d_base = b->d_base;
     sub.d_nb = b->d_nb;
     if ((s = cuda_status(cudaMalloc(&sub.d_head, sizeof(int)), "cudaMalloc(tune)")) != GF_OK) {
@@ -818,7 +888,7 @@ gf_status gf_dopri5_autotune(gf_batch b, const gf_rays *rays, double omega, cons
             for (int cp : comps)
                 for (int ch : chunks) {
                     gf_tune cand{bl, rp, cp, ch};
-                    if ((size_t)b->nb_max * kBlobStride * sizeof(double) * bl * rp > 200 * 1024) continue;
+                    if (lane_slot_bytes(b->nb_max, false) * bl * rp > kMaxLaneSmem) continue;
                     reset();
                     cudaEventRecord(e0);
                     gf_status rs = run_dopri5(&sub, &scratch, nullptr, omega, ctl, GF_SCHED_PERSISTENT,
@@ -843,6 +913,7 @@ gf_status gf_dopri5_autotune(gf_batch b, const gf_rays *rays, double omega, cons
     cudaFree(sub.d_item_begin);
     cudaFree(sub.d_item_end);
     sub.d_blobs = nullptr;
+    sub.d_pre = sub.d_pre_lim = nullptr;
     sub.d_base = nullptr;
     sub.d_nb = nullptr;
     sub.d_head = nullptr;

@@ -129,6 +129,35 @@ __device__ __forceinline__ double exp_tang(double a, const double *__restrict__ 
     return ahi >= 0xC0862000u ? 0.0 : __hiloint2double(hi, __double2loint(v));
 }
 
+// x rounded toward zero to float, on the bit pattern with integer operations
+// (the FP64 pipe also executes the hardware conversion): exact sign, exponent
+// and leading 23 fraction bits for 2^-126 <= |x| < 2^128 (relative error
+// below 2^-23); smaller |x| gives 0, larger |x|, inf and NaN give inf.
+__device__ __forceinline__ float narrow_trunc(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned mag = hi & 0x7fffffffu;
+    unsigned f = ((mag - ((1023u - 127u) << 20)) << 3) | (lo >> 29);
+    f = mag < ((1023u - 126u) << 20) ? 0u : (mag >= ((1023u + 128u) << 20) ? 0x7f800000u : f);
+    return __uint_as_float((hi & 0x80000000u) | f);
+}
+
+// 1/v for v > 0: the FP32 reciprocal of v's leading 24 bits, widened on the
+// bit pattern, is a seed r with relative error |d| < 2^-22; one Newton step
+// of cubic order, r (1 + e + e^2) with e = 1 - v r, leaves |d|^3 < 2^-66
+// before the final rounding (within one ulp of 1/v), in 3 FP64 operations.
+// Outside 2^-120 <= v < 2^120 (or for inf, NaN) the IEEE division is used.
+__device__ __forceinline__ double recip_pos(double v)
+{
+    const unsigned hi = (unsigned)__double2hiint(v);
+    if (hi - ((1023u - 120u) << 20) >= (240u << 20)) return 1.0 / v;
+    const float vf = __uint_as_float(((hi - ((1023u - 127u) << 20)) << 3) | ((unsigned)__double2loint(v) >> 29));
+    const unsigned rb = __float_as_uint(__frcp_rn(vf));
+    const double r = __hiloint2double((int)((rb >> 3) + ((1023u - 127u) << 20)), (int)(rb << 29));
+    const double e = fma(-v, r, 1.0);
+    return fma(r, fma(e, e, e), r);
+}
+
 // a < -40.5 for a double, decided on the bit pattern with integer compares
 // (for negative a, larger magnitude means a larger unsigned pattern; NaN with
 // the sign bit set also counts as negligible).  Same decision as the FP64
@@ -137,13 +166,6 @@ __device__ __forceinline__ bool below_cull(double a)
 {
     return (unsigned long long)__double_as_longlong(a) > 0xC044400000000000ull;   // bits of -40.5
 }
-
-template <typename R>
-__device__ __forceinline__ R dev_exp(R a);
-template <>
-__device__ __forceinline__ double dev_exp<double>(double a) { return exp(a); }
-template <>
-__device__ __forceinline__ float dev_exp<float>(float a) { return expf(a); }
 
 template <typename R>
 __device__ __forceinline__ const R *blob_table(const MediumParams &m);
@@ -167,12 +189,12 @@ __device__ __forceinline__ void stage_blobs(const MediumParams &m, R *sb)
 // grad n^2 for the widths in use) is far below the rounding of the sums.
 constexpr double kBlobCull = -40.5;
 // FP32 pre-test of the FP64 evaluator: a term whose |u|^2, computed in FP32
-// from rounded x, sigma and sigma c, exceeds 41 has an exact exponent below
-// -40.5.  With relative rounding 2^-24 on each FP32 input and on the fma, the
-// error of each u_i is below 6e-8 (2 sigma |x_i| + sigma |c_i| + |u_i|), and
-// that of |u|^2 (|u| < 6.5 near the threshold) below 22 times that; the host
-// sets pre_lim so that sigma (2 max|x_i| + max|c_i|) <= 1e5 for every blob,
-// which keeps the error below 0.14, under the 0.5 margin.  The FP64 test then
+// from x (truncated, relative error 2^-23) and rounded sigma, sigma c
+// (2^-24), exceeds 41 has an exact exponent below -40.5.  The error of each
+// u_i is below 6e-8 (3 sigma |x_i| + sigma |c_i| + |u_i|), that of |u|^2
+// (|u| < 6.5 near the threshold) below 22 times that; the host sets pre_lim so
+// that sigma (2 max|x_i| + max|c_i|) <= 1e5 for every blob, which keeps the
+// error below 0.2, under the 0.5 margin.  The FP64 test then
 // decides the remaining terms exactly as without the pre-test; rays beyond
 // pre_lim skip the pre-test.
 constexpr float kBlobCullQF = 41.0f;
@@ -194,6 +216,31 @@ struct EvalCtx {
 __device__ __forceinline__ void stage_pretest(const MediumParams &m, float *sp)
 {
     for (int j = threadIdx.x; j < m.n_blobs * 4; j += blockDim.x) sp[j] = m.pre32[j];
+}
+
+// The point of an FP32 pre-test: truncated coordinates, and whether the
+// pre-test is valid there (max_i |x_i| <= pre_lim).
+struct PreX {
+    float x0, x1, x2;
+    bool on;
+};
+
+__device__ __forceinline__ PreX pretest_point(const MediumParams &m, const double *x)
+{
+    PreX p;
+    p.x0 = narrow_trunc(x[0]);
+    p.x1 = narrow_trunc(x[1]);
+    p.x2 = narrow_trunc(x[2]);
+    p.on = fmaxf(fabsf(p.x0), fmaxf(fabsf(p.x1), fabsf(p.x2))) <= m.pre_lim;
+    return p;
+}
+
+// True if the blob whose pre-test row is bp (field f at bp[f * ps]) is
+// certainly negligible at p (see kBlobCullQF); p.on must hold.
+__device__ __forceinline__ bool pretest_negligible(const float *__restrict__ bp, int ps, const PreX &p)
+{
+    const float v0 = fmaf(bp[0], p.x0, bp[ps]), v1 = fmaf(bp[0], p.x1, bp[2 * ps]), v2 = fmaf(bp[0], p.x2, bp[3 * ps]);
+    return v0 * v0 + v1 * v1 + v2 * v2 > kBlobCullQF;
 }
 
 // One Gaussian-blob term on a scaled row b (field f at b[f * stride]):
@@ -258,23 +305,11 @@ __device__ __forceinline__ void iso_index(const MediumParams &m, const R *__rest
     if constexpr (sizeof(R) == 8) {
         // scaled rows: u = sigma x - sigma c, G = exp(-|u|^2),
         // n^2 += A G, grad n^2 += (-2 sigma A) G u   (19 FP64 operations per live term)
-        float xf0 = 0.f, xf1 = 0.f, xf2 = 0.f;
-        bool pre = false;
-        if (cx.pre != nullptr) {
-            xf0 = (float)x[0];
-            xf1 = (float)x[1];
-            xf2 = (float)x[2];
-            pre = fmaxf(fabsf(xf0), fmaxf(fabsf(xf1), fabsf(xf2))) <= m.pre_lim;
-        }
+        PreX px = {0.f, 0.f, 0.f, false};
+        if (cx.pre != nullptr) px = pretest_point(m, x);
 #pragma unroll 2
         for (int j = 0; j < nb; ++j) {
-            if (pre) {
-                const int ps = cx.pre_stride;
-                const float *bp = cx.pre + 4 * j * ps;
-                const float v0 = fmaf(bp[0], xf0, bp[ps]), v1 = fmaf(bp[0], xf1, bp[2 * ps]),
-                            v2 = fmaf(bp[0], xf2, bp[3 * ps]);
-                if (v0 * v0 + v1 * v1 + v2 * v2 > kBlobCullQF) continue;
-            }
+            if (px.on && pretest_negligible(cx.pre + 4 * j * cx.pre_stride, cx.pre_stride, px)) continue;
             blob_term_scaled(sb + kBlobStride * j * stride, stride, x, n2, g, cx.T, cx.live);
         }
     } else {
@@ -285,7 +320,7 @@ __device__ __forceinline__ void iso_index(const MediumParams &m, const R *__rest
             const R dx = x[0] - b[stride], dy = x[1] - b[2 * stride], dz = x[2] - b[3 * stride];
             const R a = (dx * dx + dy * dy + dz * dz) * b[4 * stride];
             if (a >= (R)kBlobCull) {
-                const R Ae = b[0] * dev_exp<R>(a);
+                const R Ae = b[0] * expf(a);
                 n2 += Ae;
                 const R c = b[5 * stride] * Ae;      // 2 s A e
                 g[0] += c * dx;
@@ -314,7 +349,11 @@ __device__ __forceinline__ bool rhs_iso(const MediumParams &m, const R *__restri
     iso_index<R, KIND>(m, sb, nb, y, n2, g, cx, stride);
     if constexpr (WANT_D) D = y[3] * y[3] + y[4] * y[4] + y[5] * y[5] - om.w * om.w * n2;
     if (!(n2 > (R)0)) return false;
-    const R inv = (R)1 / n2;
+    R inv;
+    if constexpr (sizeof(R) == 8)
+        inv = recip_pos(n2);
+    else
+        inv = (R)1 / n2;
     const R a = inv * om.inv_w;
     const R b = om.half_w * inv;
     f[0] = a * y[3];

@@ -20,6 +20,57 @@
 
 namespace gf {
 
+// Table-driven exponential available to generated code as gf_exp(a): the
+// library's method (Tang's 2^(j/2048) table, staged in shared memory by the
+// kernel below, Cody-Waite reduction, degree-3 polynomial, < 1.16 ulp) for
+// |a| < 708, CUDA's exp outside (overflow, underflow, inf, NaN).  The table
+// and constants are printed into the source as exact hex literals.
+static const char *kJitExp = R"JIT(
+__shared__ double gf_T[2048];
+__device__ __forceinline__ double gf_exp(double a)
+{
+    const unsigned ahi = (unsigned)__double2hiint(a) & 0x7fffffffu;
+    if (ahi >= 0x40862000u) return exp(a);           // |a| >= 708, inf, NaN
+    const double shifter = 6755399441055744.0;
+    const double t = fma(a, GF_INV_LN2_N, shifter);
+    const int k = __double2loint(t);
+    const double kd = t - shifter;
+    double r = fma(kd, -GF_LN2_N_HI, a);
+    r = fma(kd, -GF_LN2_N_LO, r);
+    const double c = fma(r, 1.0 / 6.0, 0.5);
+    const double p = fma(r * r, c, r);
+    const double Tj = gf_T[k & 2047];
+    const double v = fma(Tj, p, Tj);
+    return __hiloint2double(__double2hiint(v) + ((k >> 11) << 20), __double2loint(v));
+}
+)JIT";
+
+static const double kHostExpTab[kExpTabN] = {GF_EXP2_TAB_VALUES};
+
+// The exp table as a device array initialiser plus the reduction constants.
+static const std::string &jit_prelude()
+{
+    static const std::string text = [] {
+        std::string t;
+        char buf[64];
+        snprintf(buf, sizeof buf, "#define GF_INV_LN2_N %a\n", kInvLn2xN);
+        t += buf;
+        snprintf(buf, sizeof buf, "#define GF_LN2_N_HI %a\n", kLn2ByNHi);
+        t += buf;
+        snprintf(buf, sizeof buf, "#define GF_LN2_N_LO %a\n", kLn2ByNLo);
+        t += buf;
+        t += "__device__ const double gf_exp2_tab[2048] = {\n";
+        for (int j = 0; j < kExpTabN; ++j) {
+            snprintf(buf, sizeof buf, "%a,%s", kHostExpTab[j], (j % 4 == 3) ? "\n" : " ");
+            t += buf;
+        }
+        t += "};\n";
+        t += kJitExp;
+        return t;
+    }();
+    return text;
+}
+
 // RK4 ray kernel around the generated gf_user_dispersion(y, w, out):
 // out = (D, D_x0, D_x1, D_x2, D_k0, D_k1, D_k2, D_w).  Same update, statuses
 // and residual bookkeeping as the built-in kernel; the right-hand side is the
@@ -42,6 +93,8 @@ extern "C" __global__ void __launch_bounds__(128) gf_jit_rk4(
     long long n, long long ld, double *y, double *t, int *status, int *steps, double *dres,
     double *dmax, double w, double dt, long long n_steps, double r2)
 {
+    for (int j = threadIdx.x; j < 2048; j += blockDim.x) gf_T[j] = gf_exp2_tab[j];
+    __syncthreads();
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || status[i] != 0) return;
     double s[6];
@@ -134,7 +187,7 @@ static gf_status compile(const char *source, const char *arch, std::vector<char>
     Nvrtc *nv = nullptr;
     gf_status s = load_nvrtc(&nv);
     if (s != GF_OK) return s;
-    const std::string full = std::string(source) + "\n" + kJitKernel;
+    const std::string full = jit_prelude() + std::string(source) + "\n" + kJitKernel;
     nvrtcProgram prog;
     nvrtcResult r = nv->create(&prog, full.c_str(), "gf_generated_medium.cu", 0, nullptr, nullptr);
     if (r != NVRTC_SUCCESS) {

@@ -390,7 +390,7 @@ def to_cuda(outs: list[Node], name: str = "gf_user_dispersion") -> str:
         elif op == "pow":
             e = " * ".join([a[0]] * n.value)
         elif op == "exp":
-            e = f"exp({a[0]})"
+            e = f"gf_exp({a[0]})"
         elif op == "sqrt":
             e = f"sqrt({a[0]})"
         elif op == "where":

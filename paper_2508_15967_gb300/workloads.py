@@ -52,6 +52,34 @@ def plane_disk_rays(rng: np.random.Generator, n: int, radius: float, x_plane: fl
     return x0, d
 
 
+def morton_order(p: np.ndarray) -> np.ndarray:
+    """Permutation listing 2-D points p (n, 2) along a Z-order (Morton) curve of
+    a 2^16 x 2^16 grid over their bounding box: consecutive points are
+    neighbours, as when a launcher sweeps its aperture, so that a warp traces
+    rays that stay close together (the same set of rays in another order)."""
+    if len(p) == 0:
+        return np.zeros(0, dtype=np.int64)
+    lo = p.min(axis=0)
+    span = np.maximum(p.max(axis=0) - lo, 1e-300)
+    q = np.minimum((p - lo) / span * 65536.0, 65535.0).astype(np.uint64)
+
+    def spread(v):   # bit i of v moves to bit 2 i
+        v = (v | (v << np.uint64(8))) & np.uint64(0x00FF00FF)
+        v = (v | (v << np.uint64(4))) & np.uint64(0x0F0F0F0F)
+        v = (v | (v << np.uint64(2))) & np.uint64(0x33333333)
+        return (v | (v << np.uint64(1))) & np.uint64(0x55555555)
+
+    code = spread(q[:, 0]) | (spread(q[:, 1]) << np.uint64(1))
+    return np.argsort(code, kind="stable")
+
+
+def aperture_rays(rng: np.random.Generator, n: int, radius: float):
+    """plane_disk_rays listed in Morton order of their launch points (y0, z0)."""
+    x0, d = plane_disk_rays(rng, n, radius)
+    o = morton_order(x0[:, 1:])
+    return x0[o], d[o]
+
+
 def cone_directions(rng: np.random.Generator, n: int, half_angle_deg: float):
     """Unit vectors uniform in solid angle on the cap of the given half-angle about +x."""
     cmin = math.cos(math.radians(half_angle_deg))
@@ -154,9 +182,10 @@ class Workload:
 
 
 def luneburg(n: int = 1024, n_steps: int = 2000, dt: float = 1e-3) -> Workload:
-    """Luneburg lens, no blobs; launch plane x = -1, disk radius 0.9, along +x."""
+    """Luneburg lens, no blobs; launch plane x = -1, disk radius 0.9, along +x
+    (rays in Morton order of their launch points)."""
     rng = rng_for(LUNEBURG)
-    x0, d = plane_disk_rays(rng, n, 0.9)
+    x0, d = aperture_rays(rng, n, 0.9)
     return Workload("luneburg", dict(kind="luneburg"), x0, d, 1.0, dt, n_steps)
 
 
@@ -194,8 +223,9 @@ def batched(n_media: int = 4096, n_blobs: int = 8, e_lo: int = 4, e_hi: int = 14
     """Many Luneburg+blob media with power-of-two ray counts 2^U{e_lo..e_hi}.
 
     Rays of medium m occupy [offsets[m], offsets[m+1]) and launch as in the
-    Luneburg workload.  ``scale_counts`` < 1 shrinks every count (at least 1 ray)
-    for test-sized cases while keeping the unevenness.
+    Luneburg workload (each medium's rays in Morton order of their launch
+    points).  ``scale_counts`` < 1 shrinks every count (at least 1 ray) for
+    test-sized cases while keeping the unevenness.
     """
     rng = rng_for(BATCHED)
     exps = rng.integers(e_lo, e_hi + 1, n_media)
@@ -205,6 +235,10 @@ def batched(n_media: int = 4096, n_blobs: int = 8, e_lo: int = 4, e_hi: int = 14
     offsets[1:] = np.cumsum(counts)
     rr = rng_for(BATCHED, 7)
     x0, d = plane_disk_rays(rr, int(offsets[-1]), 0.9)
+    for m in range(n_media):
+        lo, hi = int(offsets[m]), int(offsets[m + 1])
+        o = morton_order(x0[lo:hi, 1:])
+        x0[lo:hi], d[lo:hi] = x0[lo:hi][o], d[lo:hi][o]
     wl = Workload("batched", dict(kind="luneburg"), x0, d, 1.0, 1e-3, 0, 1.5)
     wl.extra = dict(blobs=blobs, offsets=offsets, counts=counts,
                     rtol=1e-9, atol=1e-9, h0=1e-3, t_max=10.0, max_steps=100000)
@@ -216,13 +250,14 @@ def adjoint(n: int = 65536, n_steps: int = 4000, dt: float = 1e-3, n_blobs: int 
     """Luneburg base + n_blobs Gaussian blobs whose amplitudes theta are the parameters.
 
     theta ~ N(0, 0.01) (seed 250815967+5), hidden theta* from seed + 1000;
-    centres and widths are shared by both.
+    centres and widths are shared by both.  Rays launch as in the Luneburg
+    workload, in Morton order of their launch points.
     """
     rng = rng_for(ADJOINT)
     blobs = blob_table(rng, n_blobs, 0.01)
     theta_star = rng_for(ADJOINT, 1000).normal(0.0, 0.01, n_blobs)
     rr = rng_for(ADJOINT, 7)
-    x0, d = plane_disk_rays(rr, n, 0.9)
+    x0, d = aperture_rays(rr, n, 0.9)
     wl = Workload("adjoint", dict(kind="luneburg", blobs=blobs), x0, d, 1.0, dt, n_steps)
     wl.extra = dict(theta=blobs[:, 0].copy(), theta_star=theta_star,
                     checkpoint_every=checkpoint_every)
