@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gf", "reference"], default="gf")
-    ap.add_argument("--rays", type=int, default=1 << 20)
+    ap.add_argument("--rays", type=int, default=1 << 20,
+                    help="rays of the headline trace (adjoint workload: at most its 65,536)")
     ap.add_argument("--nsteps", type=int, default=10000,
                     help="RK4 steps of the headline trace (aniso workload: at most its 4000)")
     ap.add_argument("--precision", choices=["f64", "f32", "f64x"], default="f64",
@@ -337,11 +338,12 @@ def measure_generated(gf, torch, n_rays: int, n_steps: int) -> dict:
             "max_abs_state_difference": dev}
 
 
-def measure_adjoint(gf, torch) -> dict:
+def measure_adjoint(gf, torch, n: int | None = None, n_steps: int | None = None) -> dict:
     """Adjoint workload (65,536 rays, Luneburg + 64 blobs, RK4 dt 1e-3 x 4000,
-    checkpoints every 64): forward with checkpoints and backward through the
-    autograd Function, plus a plain forward, each timed after a warm-up."""
-    wl = W.adjoint()
+    checkpoints every 64; n and n_steps shrink it): forward with checkpoints
+    and backward through the autograd Function, plus a plain forward, each
+    timed after a warm-up."""
+    wl = W.adjoint(**({} if n is None else {"n": n}), **({} if n_steps is None else {"n_steps": n_steps}))
     m = gf.gf_medium_create(**wl.medium)
     init = gf.Rays.empty(wl.n)
     init.y[:3].copy_(torch.from_numpy(np.ascontiguousarray(wl.x0.T)).cuda())
@@ -377,7 +379,8 @@ def measure_adjoint(gf, torch) -> dict:
     res["backward_over_forward"] = res["backward_ms"] / res["forward_ckpt_ms"]
     res["total_over_plain_forward"] = (res["forward_ckpt_ms"] + res["backward_ms"]) / res["plain_forward_ms"]
     res["loss"] = loss.item()
-    res["workload"] = "65536 rays, Luneburg + 64 blobs, RK4 dt=1e-3 x 4000, checkpoint every 64"
+    res["workload"] = (f"{wl.n} rays, Luneburg + {len(wl.extra['theta'])} blobs, RK4 dt={wl.dt} x {wl.n_steps}, "
+                       f"checkpoint every {wl.extra['checkpoint_every']}")
     return res
 
 
@@ -496,10 +499,18 @@ def run_gpu(a):
     k_sec = statistics.mean(kern_ms) / 1e3
     achieved = flops / k_sec / 1e12
     sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
-    # FP64 non-tensor peak from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flops
-    peak = SMS * 2 * 2 * sm_mhz * 1e6 / 1e12 if dtype == torch.float64 else SMS * 128 * 2 * sm_mhz * 1e6 / 1e12
+    # non-tensor peaks from unit counts and clock: 152 SMs x 2 DFMA/clk (FP64) or
+    # 128 FFMA/clk (FP32) x 2 flops
+    peak64 = SMS * 2 * 2 * sm_mhz * 1e6 / 1e12
+    peak = peak64 if dtype == torch.float64 else SMS * 128 * 2 * sm_mhz * 1e6 / 1e12
+    basis = (f"152 SM x 2 DFMA/clk x 2 flop x {sm_mhz:.0f} MHz (sampled)" if dtype == torch.float64
+             else f"152 SM x 128 FFMA/clk x 2 flop x {sm_mhz:.0f} MHz (sampled)")
+    kname = {"f64": "rk4_kernel<double, GRIN>", "f32": "rk4_kernel<float, GRIN>",
+             "f64x": "rk4_kernel<double, GRIN, double-float blob sums>"}[a.precision]
+    metric = {"f64": METRIC, "f32": METRIC.replace("FP64", "FP32"),
+              "f64x": METRIC.replace("FP64", "FP64 state / double-float blob sums")}[a.precision]
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": 1e3 * t_max / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"f64": "f64", "f32": "f32", "f64x": "f64 state, f32x2 blob sums"}[a.precision],
@@ -510,10 +521,10 @@ def run_gpu(a):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      "traffic": TRAFFIC_BYTES_1M if (wl.n == 1 << 20 and a.precision == "f64") else None,
-                     "kernel": "rk4_kernel<double, GRIN>", "kernel_ms": 1e3 * k_sec,
+                     "kernel": kname, "kernel_ms": 1e3 * k_sec,
                      "flops_per_launch": flops, "evaluations": evals, "blob_terms_live": live,
                      "blob_terms_total": evals * n_blobs,
-                     "peak_basis": f"152 SM x 2 DFMA/clk x 2 flop x {sm_mhz:.0f} MHz (sampled)",
+                     "peak_basis": basis,
                      "fma_peak_measured_tflops": {"f64": peak64, "f32": peak32}},
         "clocks": clk, "gpu_launches": 2 * a.steps, "e2e": e2e, "wall_s": wall,
     }
@@ -521,7 +532,7 @@ def run_gpu(a):
         if a.precision == "f64":
             line["f64x"] = measure_f64x(gf, torch, wl, m, x0, dirs, rays)
         line["luneburg"] = measure_luneburg(gf, torch)
-        line["aniso"] = measure_aniso(gf, torch, peak)
+        line["aniso"] = measure_aniso(gf, torch, peak64)
         line["adjoint"] = measure_adjoint(gf, torch)
         line["batched"] = measure_batched(gf, torch)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -549,7 +560,8 @@ def run_workload(a):
         full = inspect.signature(W.aniso).parameters["n_steps"].default
         res = measure_aniso(gf, torch, peak, min(a.nsteps, full))
     elif a.workload == "adjoint":
-        res = measure_adjoint(gf, torch)
+        d = inspect.signature(W.adjoint).parameters
+        res = measure_adjoint(gf, torch, min(a.rays, d["n"].default), min(a.nsteps, d["n_steps"].default))
     else:
         res = measure_generated(gf, torch, min(a.rays, 1 << 18), min(a.nsteps, 2000))
     print(json.dumps({"workload": a.workload, **res}), flush=True)

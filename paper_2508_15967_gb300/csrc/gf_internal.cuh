@@ -313,14 +313,16 @@ __device__ __forceinline__ void iso_index(const MediumParams &m, const R *__rest
             blob_term_scaled(sb + kBlobStride * j * stride, stride, x, n2, g, cx.T, cx.live);
         }
     } else {
-        // plain rows: A exp(s |x - c|^2) and its gradient 2 s A exp(.) (x - c)
+        // plain rows: A exp(s |x - c|^2) and its gradient 2 s A exp(.) (x - c); the
+        // FP32 path takes the fast exponential (__expf, relative error below 1e-5
+        // for exponents down to the culling threshold, far inside the FP32 gate)
 #pragma unroll 2
         for (int j = 0; j < nb; ++j) {
             const R *b = sb + kBlobStride * j * stride;
             const R dx = x[0] - b[stride], dy = x[1] - b[2 * stride], dz = x[2] - b[3 * stride];
             const R a = (dx * dx + dy * dy + dz * dz) * b[4 * stride];
             if (a >= (R)kBlobCull) {
-                const R Ae = b[0] * expf(a);
+                const R Ae = b[0] * __expf(a);
                 n2 += Ae;
                 const R c = b[5 * stride] * Ae;      // 2 s A e
                 g[0] += c * dx;
@@ -353,7 +355,7 @@ __device__ __forceinline__ bool rhs_iso(const MediumParams &m, const R *__restri
     if constexpr (sizeof(R) == 8)
         inv = recip_pos(n2);
     else
-        inv = (R)1 / n2;
+        inv = __frcp_rn(n2);   // correctly rounded, as (R)1 / n2
     const R a = inv * om.inv_w;
     const R b = om.half_w * inv;
     f[0] = a * y[3];

@@ -339,15 +339,29 @@ static RaysView<R> view(const gf_rays &r)
     return RaysView<R>{r.n, r.ld, (R *)r.y, r.t, r.status, r.steps, r.d_res, r.d_max};
 }
 
+// Threads per block of the RK4 kernel: 128 when the rays fill every SM; a
+// launch with fewer rays than SMs x 128 uses warps of its own (32-thread
+// blocks), spreading them over up to four times as many SMs -- each ray's
+// steps are bound by the FP64 pipe of the SM it runs on.
+static int rk4_block(int64_t n)
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return kRk4Block;
+    return n >= (int64_t)sms * kRk4Block ? kRk4Block : 32;
+}
+
 template <typename R, int KIND, bool DF = false>
 static cudaError_t rk4_launch(const MediumParams &m, const gf_rays &r, double omega, double dt,
                               int64_t n_steps, double radius, int64_t every, double *ckpt,
                               cudaStream_t s)
 {
-    const int64_t blocks = (r.n + kRk4Block - 1) / kRk4Block;
+    const int block = rk4_block(r.n);
+    const int64_t blocks = (r.n + block - 1) / block;
     const R r2 = radius > 0 ? (R)(radius * radius) : (R)0;
-    rk4_kernel<R, KIND, DF><<<(unsigned)blocks, kRk4Block, 0, s>>>(m, view<R>(r), make_omega<R>(omega), (R)dt,
-                                                                   dt, n_steps, r2, every, ckpt, work_counters());
+    rk4_kernel<R, KIND, DF><<<(unsigned)blocks, block, 0, s>>>(m, view<R>(r), make_omega<R>(omega), (R)dt,
+                                                               dt, n_steps, r2, every, ckpt, work_counters());
     return cudaGetLastError();
 }
 

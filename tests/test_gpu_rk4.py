@@ -243,6 +243,31 @@ def test_narrow_blobs_far_from_origin_skip_the_fp32_pretest():
     assert np.median(deflection) > 1e-2
 
 
+def test_spline_subnormal_coefficients_read_as_zero():
+    """Grid values below FLT_MIN are stored as zero (the FP64 evaluator widens
+    floats on their bit pattern): a grid holding subnormal off-diagonal M
+    entries traces bit for bit like the same grid with zeros there, and both
+    match the oracle on the zeroed grid."""
+    rng = np.random.default_rng(250815967 + 72)
+    g = 16
+    base = W.aniso_grid(rng, g, 8)
+    sub = base.copy()
+    mask = rng.random(base.shape[:3]) < 0.3
+    sub[..., 1][mask] = np.float32(3e-39) * np.sign(rng.standard_normal(mask.sum())).astype(np.float32)
+    zero = sub.copy()
+    zero[..., 1][mask] = 0.0
+    assert (np.abs(sub[..., 1][mask]) < np.finfo(np.float32).tiny).all() and (sub[..., 1][mask] != 0).all()
+    n = 200
+    x0 = rng.uniform(-1, 1, (n, 3))
+    d = W.sphere_directions(rng, n)
+    k0 = _onshell(dict(kind="spline", grid=zero), x0, d)
+    a = gpu_rk4(dict(kind="spline", grid=sub), x0, k0, 1.0, 1e-3, 300)
+    b = gpu_rk4(dict(kind="spline", grid=zero), x0, k0, 1.0, 1e-3, 300)
+    assert np.array_equal(a.y, b.y) and np.array_equal(a.status, b.status)
+    o, _ = oracle_rk4(dict(kind="spline", grid=zero), x0, k0, 1.0, 1e-3, 300)
+    assert_parity(b, o, 1e-9)
+
+
 def test_host_pointer_is_rejected_before_launch():
     m = gf.gf_medium_create("homog", n_h=1.0)
     host = np.zeros((6, 4))
