@@ -459,10 +459,13 @@ def run_gpu(a):
     kern_ms = [s.elapsed_time(e) for s, e in kev]
     t_dev = sum(step_ms) / 1e3
     t_max = torch.tensor([t_dev], dtype=torch.float64, device="cuda")
+    units_all = torch.tensor([units], dtype=torch.int64, device="cuda")   # ray-steps of one trace, all ranks
     if world > 1:
         dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        dist.all_reduce(units_all, op=dist.ReduceOp.SUM)
     t_max = t_max.item()
-    value = world * units * a.steps / t_max
+    units_all = int(units_all.item())
+    value = units_all * a.steps / t_max
 
     # end to end through the public API with host buffers (pinned), copies timed
     e2e = None
@@ -484,7 +487,7 @@ def run_gpu(a):
         te = torch.tensor([time.perf_counter() - e0], dtype=torch.float64, device="cuda")
         if world > 1:
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * units * a.steps / te.item(), "unit": UNIT,
+        e2e = {"value": units_all * a.steps / te.item(), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     # exact work of one trace launch (untimed pass with counters)

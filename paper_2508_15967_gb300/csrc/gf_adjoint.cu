@@ -31,7 +31,7 @@ constexpr int kAdjBlock = 64;
 constexpr int kStageVals = 10;   // Y (6), n^2, g (3)
 
 struct AdjScratch {
-    double *partials;   // n_blocks x nb
+    double *tb;         // nb x n: thetabar_j of every ray, reduced over rays at the end
     double *stage;      // every x 4 x kStageVals x n
     double *G;          // every x 4 x nb x n
 };
@@ -69,7 +69,9 @@ __device__ __forceinline__ void base_hess_vec(const MediumParams &m, const doubl
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(kAdjBlock, 1) adjoint_kernel(
+// 7 resident blocks of 64 per SM (registers capped at 146): the 65,536-ray
+// adjoint workload (2,048 warps) is resident in one wave on 152 SMs.
+__global__ void __launch_bounds__(kAdjBlock, 7) adjoint_kernel(
     const MediumParams m, const int64_t n, const double omega, const double dt, const int64_t n_steps,
     const int64_t every, const double *__restrict__ ckpt, const int32_t *__restrict__ steps_done,
     const double *__restrict__ lambda, const int64_t ld, double *__restrict__ dy0, const AdjScratch S)
@@ -78,7 +80,6 @@ __global__ void __launch_bounds__(kAdjBlock, 1) adjoint_kernel(
     __shared__ double sbs[kBlobStride * GF_MAX_BLOBS];   // scaled rows (recompute, as the forward kernel)
     __shared__ double sT[kExpTabN];
     __shared__ float sp[4 * GF_MAX_BLOBS];               // FP32 pre-test rows (recompute)
-    extern __shared__ double tb[];   // thetabar columns: tb[j * blockDim + tid]
     const int nb = m.n_blobs;
     for (int j = threadIdx.x; j < nb * kBlobStride; j += blockDim.x) {
         sb[j] = m.blobs64[j];
@@ -86,12 +87,11 @@ __global__ void __launch_bounds__(kAdjBlock, 1) adjoint_kernel(
     }
     for (int j = threadIdx.x; j < nb * 4; j += blockDim.x) sp[j] = m.pre32[j];
     stage_exp_table(sT);
-    for (int j = 0; j < nb; ++j) tb[j * blockDim.x + threadIdx.x] = 0.0;
     __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
-        double *acc_t = tb + threadIdx.x;
-        const int B = blockDim.x;
+        double *acc_t = S.tb + i;   // thetabar_j of this ray at acc_t[j * n]
+        for (int j = 0; j < nb; ++j) acc_t[(int64_t)j * n] = 0.0;
         const int sd = steps_done[i];
         double lam[6];
 #pragma unroll
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(kAdjBlock, 1) adjoint_kernel(
                         const double dx = Y[0] - b[1], dy = Y[1] - b[2], dz = Y[2] - b[3];
                         const double dK = dx * Kb[3] + dy * Kb[4] + dz * Kb[5];
                         const double s2 = b[5];
-                        acc_t[j * B] += G * (C + bq * s2 * dK);
+                        acc_t[(int64_t)j * n] += G * (C + bq * s2 * dK);
                         const double t = s2 * b[0] * G;
                         const double w = s2 * dK;
                         HK[0] += t * (w * dx + Kb[3]);
@@ -202,29 +202,31 @@ __global__ void __launch_bounds__(kAdjBlock, 1) adjoint_kernel(
             for (int c = 0; c < 6; ++c) dy0[c * ld + i] = lam[c];
         }
     }
-    __syncthreads();
-    // block reduction of the thetabar columns, fixed order
-    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-        double sum = 0.0;
-        for (int t = 0; t < (int)blockDim.x; ++t) sum += tb[j * blockDim.x + t];
-        S.partials[(int64_t)blockIdx.x * nb + j] = sum;
-    }
 }
 
-__global__ void adjoint_reduce_kernel(const double *__restrict__ partials, int64_t n_blocks, int nb,
-                                      double *__restrict__ out)
+// dL/dtheta_j = sum over rays of thetabar_j, one block per blob in a fixed
+// order (each thread a strided partial sum, then a tree): deterministic.
+constexpr int kRedBlock = 256;
+
+__global__ void __launch_bounds__(kRedBlock) adjoint_reduce_kernel(const double *__restrict__ tb, int64_t n,
+                                                                   double *__restrict__ out)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= nb) return;
+    __shared__ double part[kRedBlock];
+    const int j = blockIdx.x;
     double sum = 0.0;
-    for (int64_t b = 0; b < n_blocks; ++b) sum += partials[b * nb + j];
-    out[j] = sum;
+    for (int64_t i = threadIdx.x; i < n; i += kRedBlock) sum += tb[(int64_t)j * n + i];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int w = kRedBlock / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[j] = part[0];
 }
 
 size_t adjoint_scratch_bytes(int nb, int64_t n, int64_t every)
 {
-    const int64_t blocks = (n + kAdjBlock - 1) / kAdjBlock;
-    return sizeof(double) * ((size_t)blocks * nb + (size_t)every * 4 * (kStageVals + nb) * (size_t)n) + 256;
+    return sizeof(double) * ((size_t)nb * n + (size_t)every * 4 * (kStageVals + nb) * (size_t)n) + 256;
 }
 
 cudaError_t launch_adjoint(const MediumParams &m, int64_t n, double omega, double dt, int64_t n_steps,
@@ -235,19 +237,13 @@ cudaError_t launch_adjoint(const MediumParams &m, int64_t n, double omega, doubl
     const int64_t blocks = (n + kAdjBlock - 1) / kAdjBlock;
     char *base = (char *)(((uintptr_t)scratch + 255) & ~(uintptr_t)255);
     AdjScratch S;
-    S.partials = (double *)base;
-    S.stage = S.partials + blocks * nb;
+    S.tb = (double *)base;
+    S.stage = S.tb + (int64_t)nb * n;
     S.G = S.stage + every * 4 * kStageVals * n;
-    // thetabar columns (dynamic) next to the blob rows, pre-test rows and exp table (static, 23 KiB)
-    const size_t smem = (size_t)nb * kAdjBlock * sizeof(double);
-    cudaError_t e;
-#define GF_ADJ(K)                                                                                         \
-    case K:                                                                                               \
-        if ((e = cudaFuncSetAttribute(adjoint_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
-                                      (int)smem)) != cudaSuccess)                                         \
-            return e;                                                                                     \
-        adjoint_kernel<K><<<(unsigned)blocks, kAdjBlock, smem, s>>>(m, n, omega, dt, n_steps, every,      \
-                                                                    ckpt, steps_done, lambda, ld, dy0, S); \
+#define GF_ADJ(K)                                                                                      \
+    case K:                                                                                            \
+        adjoint_kernel<K><<<(unsigned)blocks, kAdjBlock, 0, s>>>(m, n, omega, dt, n_steps, every, ckpt, \
+                                                                 steps_done, lambda, ld, dy0, S);     \
         break;
     switch (m.kind) {
         GF_ADJ(K_HOMOG)
@@ -258,9 +254,9 @@ cudaError_t launch_adjoint(const MediumParams &m, int64_t n, double omega, doubl
         return cudaErrorInvalidValue;
     }
 #undef GF_ADJ
-    e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    adjoint_reduce_kernel<<<(nb + 63) / 64, 64, 0, s>>>(S.partials, blocks, nb, dtheta);
+    if (nb > 0) adjoint_reduce_kernel<<<nb, kRedBlock, 0, s>>>(S.tb, n, dtheta);
     return cudaGetLastError();
 }
 
