@@ -170,7 +170,7 @@ FLOPS_LIVE_TERM, FLOPS_CULLED_TERM, FLOPS_EVAL, FLOPS_STEP = 36, 9, 51, 18
 # 1,048,576 rays, from an ncu capture of the same launch shape (the kernel
 # loads and stores the ray state once, so the count does not depend on the
 # number of steps).  Valid only for the FP64 GRIN kernel as captured.
-TRAFFIC_BYTES_1M = 76_061_952 + 23_438_592
+TRAFFIC_BYTES_1M = 75_756_800 + 23_393_792
 
 
 def algorithmic_flops(evals: int, live: int, n_blobs: int, ray_steps: int) -> int:

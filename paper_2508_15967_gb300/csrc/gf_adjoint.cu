@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kAdjBlock, 7) adjoint_kernel(
     const double *__restrict__ lambda, const int64_t ld, double *__restrict__ dy0, const AdjScratch S)
 {
     __shared__ double sb[kBlobStride * GF_MAX_BLOBS];    // plain rows (reverse sweep)
-    __shared__ double sbs[kBlobStride * GF_MAX_BLOBS];   // scaled rows (recompute, as the forward kernel)
+    __shared__ double sbs[kBlobStride * GF_MAX_BLOBS];   // scaled rows (recompute)
     __shared__ double sT[kExpTabN];
     __shared__ float sp[4 * GF_MAX_BLOBS];               // FP32 pre-test rows (recompute)
     const int nb = m.n_blobs;

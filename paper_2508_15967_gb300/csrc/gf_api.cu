@@ -110,17 +110,19 @@ static void free_medium(gf_medium m)
     delete m;
 }
 
-// A_j in the plain rows (double and float) and A_j, -2 sigma_j A_j in the scaled rows.
+// A_j in the plain rows and A_j, -2 sigma_j A_j in the scaled rows (double
+// and float).
 __global__ void set_amplitudes_kernel(double *b64, float *b32, const double *A, int nb)
 {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j < nb) {
         double a = A[j];
         b64[kBlobStride * j] = a;
-        b32[kBlobStride * j] = (float)a;
         double *sc = b64 + kBlobStride * (nb + j);
         sc[4] = a;
         sc[5] = (-2.0 * sc[0]) * a;
+        b32[kBlobStride * j + 4] = (float)sc[4];
+        b32[kBlobStride * j + 5] = (float)sc[5];
     }
 }
 
@@ -184,7 +186,7 @@ gf_status gf_medium_create(const gf_medium_desc *d, gf_medium *out)
         set_error("gf_medium_create: spline needs a grid with 4 <= grid_n <= 2048");
         return GF_ERR_INVALID_ARG;
     }
-    // plain rows, then scaled rows (t64); plain float rows, then FP32 pre-test rows (t32)
+    // plain rows, then scaled rows (t64); float scaled rows, then FP32 pre-test rows (t32)
     const size_t nbl = (size_t)d->n_blobs;
     std::vector<double> t64(2 * kBlobStride * nbl);
     std::vector<float> t32(kBlobStride * nbl + 4 * nbl);
@@ -210,7 +212,7 @@ gf_status gf_medium_create(const gf_medium_desc *d, gf_medium *out)
         for (int c = 0; c < kBlobStride; ++c) {
             t64[kBlobStride * j + c] = row[c];
             t64[kBlobStride * (nbl + j) + c] = srow[c];
-            t32[kBlobStride * j + c] = (float)row[c];
+            t32[kBlobStride * j + c] = (float)srow[c];
         }
         for (int c = 0; c < 4; ++c) t32[kBlobStride * nbl + 4 * j + c] = (float)srow[c];
         sig_max = std::max(sig_max, sig);

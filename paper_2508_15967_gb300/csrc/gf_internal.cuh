@@ -16,8 +16,9 @@ enum : int { K_HOMOG = GF_MED_HOMOG, K_LUNEBURG = GF_MED_LUNEBURG, K_GRIN = GF_M
              K_QUADRATIC = GF_MED_QUADRATIC, K_SPLINE = GF_MED_SPLINE, K_COLD = GF_MED_COLD };
 
 // Device blob rows, 6 values each:
-//   plain  (FP32 path, adjoint, double-float path): A, cx, cy, cz, s = -1 / (2 w^2), 2 s
-//   scaled (FP64 evaluator): sigma, -sigma cx, -sigma cy, -sigma cz, A, -2 sigma A
+//   plain  (adjoint sweep, double-float path): A, cx, cy, cz, s = -1 / (2 w^2), 2 s
+//   scaled (FP64 evaluator; a float copy for the FP32 evaluator):
+//          sigma, -sigma cx, -sigma cy, -sigma cz, A, -2 sigma A
 // with sigma = sqrt(-s), so that A exp(s |x - c|^2) = A exp(-|u|^2), u = sigma x - sigma c.
 constexpr int kBlobStride = 6;
 
@@ -28,7 +29,7 @@ struct MediumParams {
     double n_h2;                 // homogeneous n^2
     double n02, n02a2;           // GRIN: n0^2 and n0^2 a^2
     const double *blobs64;       // n_blobs plain rows
-    const float *blobs32;        // float copy of the plain rows
+    const float *blobs32;        // float copy of the scaled rows
     const double *blobs64s;      // n_blobs scaled rows
     const float *pre32;          // n_blobs x 4 floats: sigma, -sigma cx, -sigma cy, -sigma cz
     const float4 *grid;          // grid_n^3 nodes x 2 float4
@@ -55,7 +56,7 @@ struct gf_medium_s {
     gf::MediumParams p{};
     int device = -1;
     double *d_blobs64 = nullptr;     // plain rows, then scaled rows (2 x n_blobs rows)
-    float *d_blobs32 = nullptr;      // plain float rows, then pre-test rows
+    float *d_blobs32 = nullptr;      // float scaled rows, then pre-test rows
     float4 *d_grid = nullptr;
     cudaLibrary_t jit_lib = nullptr;
     cudaKernel_t jit_kernel = nullptr;
@@ -174,9 +175,8 @@ __device__ __forceinline__ const double *blob_table<double>(const MediumParams &
 template <>
 __device__ __forceinline__ const float *blob_table<float>(const MediumParams &m) { return m.blobs32; }
 
-// Stage the blob rows the evaluator of precision R reads (scaled rows for
-// double, plain float rows for float) into shared memory (all threads of the
-// block call it).
+// Stage the scaled blob rows the evaluator of precision R reads into shared
+// memory (all threads of the block call it).
 template <typename R>
 __device__ __forceinline__ void stage_blobs(const MediumParams &m, R *sb)
 {
@@ -313,21 +313,25 @@ __device__ __forceinline__ void iso_index(const MediumParams &m, const R *__rest
             blob_term_scaled(sb + kBlobStride * j * stride, stride, x, n2, g, cx.T, cx.live);
         }
     } else {
-        // plain rows: A exp(s |x - c|^2) and its gradient 2 s A exp(.) (x - c); the
-        // FP32 path takes the fast exponential (__expf, relative error below 1e-5
-        // for exponents down to the culling threshold, far inside the FP32 gate)
+        // the same scaled form in FP32 with the fast exponential (__expf,
+        // relative error below 1e-5 down to the culling threshold).  Near a
+        // blob centre u = sigma x - sigma c loses ~ulp(sigma x) to cancellation,
+        // a relative error of ~4e-6 in G there: below one float ulp of n^2 for
+        // the amplitudes in use, far inside the FP32 gate.
 #pragma unroll 2
         for (int j = 0; j < nb; ++j) {
-            const R *b = sb + kBlobStride * j * stride;
-            const R dx = x[0] - b[stride], dy = x[1] - b[2 * stride], dz = x[2] - b[3 * stride];
-            const R a = (dx * dx + dy * dy + dz * dz) * b[4 * stride];
-            if (a >= (R)kBlobCull) {
-                const R Ae = b[0] * __expf(a);
-                n2 += Ae;
-                const R c = b[5 * stride] * Ae;      // 2 s A e
-                g[0] += c * dx;
-                g[1] += c * dy;
-                g[2] += c * dz;
+            const float *b = sb + kBlobStride * j * stride;
+            const float sg = b[0];
+            const float u0 = fmaf(sg, x[0], b[stride]), u1 = fmaf(sg, x[1], b[2 * stride]),
+                        u2 = fmaf(sg, x[2], b[3 * stride]);
+            const float a = fmaf(-u2, u2, fmaf(-u1, u1, -(u0 * u0)));
+            if (a >= (float)kBlobCull) {
+                const float G = __expf(a);
+                n2 = fmaf(b[4 * stride], G, n2);
+                const float c = b[5 * stride] * G;
+                g[0] = fmaf(c, u0, g[0]);
+                g[1] = fmaf(c, u1, g[1]);
+                g[2] = fmaf(c, u2, g[2]);
                 ++cx.live;
             }
         }
