@@ -10,7 +10,8 @@
 //   (Dekker 1971), and the double-word algorithms of Joldes, Muller & Popescu,
 //   "Tight and rigorous error bounds for basic building blocks of double-word
 //   arithmetic", ACM TOMS 44 (2017): AccurateDWPlusDW (relative error
-//   <= 3u^2 + 13u^3), DWPlusFP, DWTimesDW2 (<= 5u^2), DWTimesFP2, u = 2^-24.
+//   <= 3u^2 + 13u^3), SloppyDWPlusDW (where no cancellation matters),
+//   DWPlusFP, DWTimesDW2 (<= 5u^2), DWTimesFP2, u = 2^-24.
 // Every operation uses explicitly rounded intrinsics so that the compiler
 // neither contracts nor reassociates them.
 #pragma once
@@ -53,6 +54,17 @@ __device__ __forceinline__ dfl df_add(dfl x, dfl y)
     const dfl t = two_sum(x.lo, y.lo);
     const dfl v = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
     return fast_two_sum(v.hi, __fadd_rn(t.lo, v.lo));
+}
+
+// SloppyDWPlusDW: 11 operations against 20; no relative error bound when x
+// and y nearly cancel, but |error| <= ~2 u^2 (|x| + |y|) always, so it serves
+// sums whose absolute error is what matters (sums of squares, accumulations
+// into a running total of larger magnitude).
+__device__ __forceinline__ dfl df_add_sloppy(dfl x, dfl y)
+{
+    const dfl s = two_sum(x.hi, y.hi);
+    const float v = __fadd_rn(x.lo, y.lo);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, v));
 }
 
 // DWPlusFP
@@ -110,14 +122,16 @@ __device__ __forceinline__ dfl df_exp(dfl a, const float *__restrict__ sT)
     r = fast_two_sum(r.hi, __fmaf_rn(-kf, kDfL4, r.lo));
     const dfl r2 = df_sqr(r);
     const dfl r3 = df_mul(r2, r);
-    dfl p = df_add(r, dfl{__fmul_rn(0.5f, r2.hi), __fmul_rn(0.5f, r2.lo)});
-    p = df_add(p, df_mul(r3, dfl{kDfSixthHi, kDfSixthLo}));
+    // no cancellation in the polynomial (|r^2/2| < 3e-3 |r|) or in T + T p
+    // (|p| < 6e-3): the sloppy double-word sum keeps its 2 u^2 error there
+    dfl p = df_add_sloppy(r, dfl{__fmul_rn(0.5f, r2.hi), __fmul_rn(0.5f, r2.lo)});
+    p = df_add_sloppy(p, df_mul(r3, dfl{kDfSixthHi, kDfSixthLo}));
     const float r4 = __fmul_rn(r2.hi, r2.hi);
     p = df_add_f(p, __fmul_rn(r4, __fmaf_rn(r.hi, 1.0f / 120.0f, 1.0f / 24.0f)));
     const int k = (int)kf;
     const int j = k & 63;
     const dfl T = {sT[2 * j], sT[2 * j + 1]};
-    const dfl G = df_add(T, df_mul(T, p));
+    const dfl G = df_add_sloppy(T, df_mul(T, p));
     const float sc = __int_as_float((127 + (k >> 6)) << 23);      // 2^(k >> 6), k >> 6 >= -64
     return {__fmul_rn(G.hi, sc), __fmul_rn(G.lo, sc)};
 }
@@ -174,16 +188,16 @@ __device__ __forceinline__ void blobs_df(const float *__restrict__ sd, int nb, c
         const dfl d0 = df_add(X0, dfl{-b[0], -b[3]});
         const dfl d1 = df_add(X1, dfl{-b[1], -b[4]});
         const dfl d2 = df_add(X2, dfl{-b[2], -b[5]});
-        const dfl q = df_add(df_add(df_sqr(d0), df_sqr(d1)), df_sqr(d2));
+        const dfl q = df_add_sloppy(df_add_sloppy(df_sqr(d0), df_sqr(d1)), df_sqr(d2));   // no cancellation
         const dfl s = {b[6], b[7]};
         const dfl a = df_mul(s, q);
         if (a.hi < (float)kBlobCull) continue;
         const dfl AG = df_mul(dfl{b[8], b[9]}, df_exp(a, sT));
-        N = df_add(N, AG);
+        N = df_add_sloppy(N, AG);                                    // absolute error ~u^2 |N|, |AG|
         const dfl c = df_mul(dfl{2.f * s.hi, 2.f * s.lo}, AG);      // 2 s A G
-        G0 = df_add(G0, df_mul(c, d0));
-        G1 = df_add(G1, df_mul(c, d1));
-        G2 = df_add(G2, df_mul(c, d2));
+        G0 = df_add_sloppy(G0, df_mul(c, d0));
+        G1 = df_add_sloppy(G1, df_mul(c, d1));
+        G2 = df_add_sloppy(G2, df_mul(c, d2));
         ++live;
     }
     n2 += df_to_double(N);
