@@ -56,8 +56,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the secondary measurements (f64x, luneburg, aniso, adjoint, batched)")
-    ap.add_argument("--workload", choices=["grin", "luneburg", "batched", "aniso", "adjoint", "generated"],
+                    help="skip the secondary measurements (f64x, luneburg, cold, aniso, adjoint, batched)")
+    ap.add_argument("--workload", choices=["grin", "luneburg", "cold", "batched", "aniso", "adjoint", "generated"],
                     default="grin", help="grin: the headline line; others print that measurement alone")
     ap.add_argument("--media", type=int, default=4096, help="batched: number of media")
     ap.add_argument("--tune-cache", default=None,
@@ -222,8 +222,28 @@ def measure_batched(gf, torch, tune_cache: str | None = None, n_media: int = 409
         out[name] = {"ms": ms[-1], "accepted_ray_steps": steps,
                      "rejected": int(rej.to(torch.int64).sum().item()),
                      "ray_steps_per_s": steps / (ms[-1] / 1e3)}
+    # the same batch with double-float blob sums (GF_F64X), tuned for that mode
+    gf.gf_batch_set_precision(batch, gf.GF_F64X)
+    gf.gf_dopri5_autotune(batch, init, 1.0, ctl, None)
+    ms = []
+    for _ in range(2):
+        for src, dst in zip((init.y, init.t, init.status, init.steps, init.d_max),
+                            (rays.y, rays.t, rays.status, rays.steps, rays.d_max)):
+            dst.copy_(src)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        gf.gf_trace_dopri5(batch, rays, rej, 1.0, ctl, gf.GF_SCHED_PERSISTENT, None)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms.append(ev0.elapsed_time(ev1))
+    steps = int(rays.steps.to(torch.int64).sum().item())
+    out["persistent_f64x"] = {"ms": ms[-1], "accepted_ray_steps": steps,
+                              "rejected": int(rej.to(torch.int64).sum().item()),
+                              "ray_steps_per_s": steps / (ms[-1] / 1e3)}
+    gf.gf_batch_set_precision(batch, gf.GF_F64)
     return {"workload": f"{n_media} Luneburg+8-blob media, {wl.n} rays, DOPRI5 rtol=atol=1e-9, exit r=1.5",
             "persistent": out["persistent"], "per_medium": out["per_medium"],
+            "persistent_f64x": out["persistent_f64x"],
             "speedup_persistent_vs_per_medium": out["per_medium"]["ms"] / out["persistent"]["ms"],
             "tune": {"block": tune.block, "rays_per_thread": tune.rays_per_thread,
                      "compaction": tune.compaction, "chunk": tune.chunk, "seconds": tune_s}}
@@ -284,6 +304,34 @@ def measure_luneburg(gf, torch) -> dict:
     t = statistics.median(ms)
     return {"workload": f"{wl.n} rays, Luneburg lens, RK4 dt={wl.dt} x {wl.n_steps}, FP64",
             "ms": t, "ray_steps_per_s": wl.n * wl.n_steps / (t / 1e3), "us_per_step": 1e3 * t / wl.n_steps}
+
+
+def measure_cold(gf, torch) -> dict:
+    """Cold-plasma workload (1,048,576 rays in the magnetised slab of Sec. 4.1
+    with the Eq. 4 density gradient, O branch, RK4 dt = 1e-2 x 1500, FP64),
+    the counterpart of the paper's own benchmark (1e6 cold-plasma rays, timed
+    without setup): Newton on k_x, then one warm-up and one timed trace."""
+    wl = W.cold()
+    m = gf.gf_medium_create(**wl.medium)
+    init = gf.Rays.from_numpy(wl.x0, wl.extra["k_start"])
+    gf.gf_rays_newton_kx(m, init, wl.omega)
+    torch.cuda.synchronize()
+    ok = int((init.status == 0).sum().item())
+    ms = []
+    for _ in range(2):
+        rays = init.clone()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        gf.gf_trace_rk4(m, rays, wl.omega, wl.dt, wl.n_steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    units = int(rays.steps.to(torch.int64).sum().item())
+    return {"workload": f"{wl.n} rays, cold plasma slab (electrons + ions, f = 1 + 0.1 x), O branch, "
+                        f"RK4 dt={wl.dt} x {wl.n_steps}, FP64",
+            "ms": ms[-1], "ray_steps_per_s": units / (ms[-1] / 1e3), "newton_converged": ok,
+            "reflected": int(((rays.y[3] < 0) & (init.status == 0)).sum().item()),
+            "max_abs_D": rays.d_max[init.status == 0].max().item()}
 
 
 def measure_f64x(gf, torch, wl, m, x0, dirs, rays) -> dict:
@@ -535,6 +583,7 @@ def run_gpu(a):
         if a.precision == "f64":
             line["f64x"] = measure_f64x(gf, torch, wl, m, x0, dirs, rays)
         line["luneburg"] = measure_luneburg(gf, torch)
+        line["cold"] = measure_cold(gf, torch)
         line["aniso"] = measure_aniso(gf, torch, peak64)
         line["adjoint"] = measure_adjoint(gf, torch)
         line["batched"] = measure_batched(gf, torch)
@@ -559,6 +608,8 @@ def run_workload(a):
         res = measure_batched(gf, torch, tune_cache=a.tune_cache, n_media=a.media)
     elif a.workload == "luneburg":
         res = measure_luneburg(gf, torch)
+    elif a.workload == "cold":
+        res = measure_cold(gf, torch)
     elif a.workload == "aniso":
         full = inspect.signature(W.aniso).parameters["n_steps"].default
         res = measure_aniso(gf, torch, peak, min(a.nsteps, full))

@@ -367,7 +367,9 @@ gf_status gf_batch_destroy(gf_batch b);
  * Prince 1980 and Hairer-Norsett-Wanner I, Sec. II.4): err = RMS over the 6
  * components of e_i / (atol + rtol max(|y_i|, |y_new,i|)), accept iff err <= 1,
  * h <- h min(fac_max, max(fac_min, safety err^(-1/5))), no growth on the step
- * after a rejection.  rays->steps counts accepted steps; rejects (device, n,
+ * after a rejection (the norm and the step factor are evaluated in FP32 from
+ * the FP64 estimate e).  The blob sums are IEEE double, or double-float after
+ * gf_batch_set_precision(b, GF_F64X).  rays->steps counts accepted steps; rejects (device, n,
  * may be NULL) counts rejected ones.  Every ray starts from h = ctl->h0.
  * Results of a ray do not depend on the schedule: both schedules return bit-
  * identical buffers.  sched selects the launch structure; tune (may be NULL:
@@ -380,6 +382,18 @@ gf_status gf_batch_destroy(gf_batch b);
 gf_status gf_trace_dopri5(gf_batch b, const gf_rays *rays, int32_t *rejects, double omega,
                           const gf_step_ctl *ctl, gf_schedule sched, const gf_tune *tune,
                           void *stream);
+
+/*
+ * gf_batch_set_precision -- evaluation mode of the batch's later
+ * gf_trace_dopri5 and gf_dopri5_autotune calls: GF_F64 (default: IEEE double
+ * throughout) or GF_F64X (state, stages, controller and base index law in
+ * IEEE double; the Gaussian-blob sums in double-float on the FP32 pipes, as
+ * gf_trace_rk4's GF_F64X).  No paper counterpart (a GB300 evaluation mode).
+ * Both schedules stay bit-identical to each other in either mode.  Changing
+ * the mode forgets the batch's tuned launch shape.
+ * Errors: GF_ERR_INVALID_ARG (b NULL), GF_ERR_UNSUPPORTED (GF_F32).
+ */
+gf_status gf_batch_set_precision(gf_batch b, gf_precision prec);
 
 /*
  * gf_dopri5_autotune -- time the persistent schedule for block size x rays per

@@ -97,6 +97,7 @@ def lib() -> C.CDLL:
             "gf_batch_create": ([P, I32, P, P], I32),
             "gf_batch_destroy": ([P], I32),
             "gf_trace_dopri5": ([P, P, P, D, P, I32, P, P], I32),
+            "gf_batch_set_precision": ([P, I32], I32),
             "gf_dopri5_autotune": ([P, P, D, P, C.c_char_p, P], I32),
         }
         for name, (args, res) in sigs.items():
@@ -378,6 +379,11 @@ def gf_batch_create(media: list, offsets) -> Batch:
     h = C.c_void_p()
     _check("gf_batch_create", lib().gf_batch_create(arr, len(media), off.ctypes.data, C.byref(h)))
     return Batch(h.value, len(media), off)
+
+
+def gf_batch_set_precision(b: Batch, precision: int) -> None:
+    """GF_F64 (default) or GF_F64X (double-float blob sums) for later DOPRI5 calls."""
+    _check("gf_batch_set_precision", lib().gf_batch_set_precision(b.handle, precision))
 
 
 def gf_batch_destroy(b: Batch) -> None:

@@ -123,6 +123,10 @@ __global__ void set_amplitudes_kernel(double *b64, float *b32, const double *A, 
         sc[5] = (-2.0 * sc[0]) * a;
         b32[kBlobStride * j + 4] = (float)sc[4];
         b32[kBlobStride * j + 5] = (float)sc[5];
+        float *dfr = b32 + (kBlobStride + 4) * nb + kDfRowFloats * j;   // A_hi, A_lo
+        const float hi = __double2float_rn(a);
+        dfr[8] = hi;
+        dfr[9] = __double2float_rn(a - (double)hi);
     }
 }
 
@@ -186,10 +190,11 @@ gf_status gf_medium_create(const gf_medium_desc *d, gf_medium *out)
         set_error("gf_medium_create: spline needs a grid with 4 <= grid_n <= 2048");
         return GF_ERR_INVALID_ARG;
     }
-    // plain rows, then scaled rows (t64); float scaled rows, then FP32 pre-test rows (t32)
+    // plain rows, then scaled rows (t64); float scaled rows, FP32 pre-test rows and
+    // double-float rows (t32)
     const size_t nbl = (size_t)d->n_blobs;
     std::vector<double> t64(2 * kBlobStride * nbl);
-    std::vector<float> t32(kBlobStride * nbl + 4 * nbl);
+    std::vector<float> t32((kBlobStride + 4 + kDfRowFloats) * nbl);
     double pre_span = 0.0;   // max over blobs of sigma, and of sigma |c_i|
     double sig_max = 0.0;
     for (int j = 0; j < d->n_blobs; ++j) {
@@ -215,6 +220,17 @@ gf_status gf_medium_create(const gf_medium_desc *d, gf_medium *out)
             t32[kBlobStride * j + c] = (float)srow[c];
         }
         for (int c = 0; c < 4; ++c) t32[kBlobStride * nbl + 4 * j + c] = (float)srow[c];
+        // double-float row: c_hi[3], c_lo[3], s_hi, s_lo, A_hi, A_lo with hi = RN_float(v)
+        // and lo = RN_float(v - hi) (v - hi is exact in double)
+        float *dfr = t32.data() + (kBlobStride + 4) * nbl + kDfRowFloats * j;
+        const double vals[5] = {b[1], b[2], b[3], sj, b[0]};
+        for (int c = 0; c < 5; ++c) {
+            const float hi = (float)vals[c];
+            const float lo = (float)(vals[c] - (double)hi);
+            const int at = c < 3 ? c : 6 + 2 * (c - 3);
+            dfr[at] = hi;
+            dfr[c < 3 ? 3 + c : at + 1] = lo;
+        }
         sig_max = std::max(sig_max, sig);
         for (int c = 1; c < 4; ++c) pre_span = std::max(pre_span, std::fabs(srow[c]));
     }
@@ -257,6 +273,7 @@ gf_status gf_medium_create(const gf_medium_desc *d, gf_medium *out)
     p.blobs32 = m->d_blobs32;
     p.blobs64s = m->d_blobs64 + kBlobStride * nbl;
     p.pre32 = m->d_blobs32 + kBlobStride * nbl;
+    p.dfrows = m->d_blobs32 + (kBlobStride + 4) * nbl;
     if (d->kind == GF_MED_SPLINE) {
         size_t nodes = (size_t)d->grid_n * d->grid_n * d->grid_n;
         // finite values only; subnormals (|v| < FLT_MIN) are stored as zero of the same

@@ -149,50 +149,40 @@ __device__ __forceinline__ void stage_dfexp_table(float *sT)
     for (int j = threadIdx.x; j < 128; j += blockDim.x) sT[j] = c_dfexp2_tab[j];
 }
 
-// Double-float blob row in shared memory: c_hi[3], c_lo[3], s_hi, s_lo,
-// A_hi, A_lo (2 s is formed exactly by doubling s).
-constexpr int kDfBlobStride = 10;
+// Double-float blob row: c_hi[3], c_lo[3], s_hi, s_lo, A_hi, A_lo, each
+// value split exactly as hi = RN_float(v), lo = RN_float(v - hi) (2 s is
+// formed exactly by doubling s).  Built on the host with the medium.
+constexpr int kDfBlobStride = kDfRowFloats;
 
 __device__ __forceinline__ void stage_df_blobs(const MediumParams &m, float *sd)
 {
-    for (int j = threadIdx.x; j < m.n_blobs; j += blockDim.x) {
-        const double *b = m.blobs64 + kBlobStride * j;
-        float *o = sd + kDfBlobStride * j;
-        for (int c = 0; c < 3; ++c) {
-            const dfl v = df_from_double(b[1 + c]);
-            o[c] = v.hi;
-            o[3 + c] = v.lo;
-        }
-        const dfl s = df_from_double(b[4]);
-        const dfl A = df_from_double(b[0]);
-        o[6] = s.hi;
-        o[7] = s.lo;
-        o[8] = A.hi;
-        o[9] = A.lo;
-    }
+    for (int j = threadIdx.x; j < m.n_blobs * kDfBlobStride; j += blockDim.x) sd[j] = m.dfrows[j];
 }
 
 // Sum over blobs of A_j exp(s_j |x - c_j|^2) and of its gradient, in
-// double-float, added to n2 and g in double.  Terms whose exponent is below
-// -40.5 are skipped (as in the FP64 evaluator); a float pre-test with margin
-// removes most of them before any double-float work.
+// double-float, added to n2 and g in double.  Field f of blob j is read from
+// sd[(kDfBlobStride j + f) * stride] (stride 1: a block-shared table; stride
+// = lanes: one table per lane).  Terms whose exponent is below -40.5 are
+// skipped (as in the FP64 evaluator); a float pre-test with margin removes
+// most of them before any double-float work.
 __device__ __forceinline__ void blobs_df(const float *__restrict__ sd, int nb, const double *x, double &n2,
-                                         double *g, const float *__restrict__ sT, int &live)
+                                         double *g, const float *__restrict__ sT, int &live, int stride = 1)
 {
     const dfl X0 = df_from_double(x[0]), X1 = df_from_double(x[1]), X2 = df_from_double(x[2]);
     dfl N = {0.f, 0.f}, G0 = {0.f, 0.f}, G1 = {0.f, 0.f}, G2 = {0.f, 0.f};
     for (int j = 0; j < nb; ++j) {
-        const float *b = sd + kDfBlobStride * j;
-        const float ex = X0.hi - b[0], ey = X1.hi - b[1], ez = X2.hi - b[2];
-        if ((ex * ex + ey * ey + ez * ez) * b[6] < -kBlobCullQF) continue;
-        const dfl d0 = df_add(X0, dfl{-b[0], -b[3]});
-        const dfl d1 = df_add(X1, dfl{-b[1], -b[4]});
-        const dfl d2 = df_add(X2, dfl{-b[2], -b[5]});
+        const float *bp = sd + kDfBlobStride * j * stride;
+        const auto b = [&](int f) { return bp[f * stride]; };   // read where used
+        const float ex = X0.hi - b(0), ey = X1.hi - b(1), ez = X2.hi - b(2);
+        if ((ex * ex + ey * ey + ez * ez) * b(6) < -kBlobCullQF) continue;
+        const dfl d0 = df_add(X0, dfl{-b(0), -b(3)});
+        const dfl d1 = df_add(X1, dfl{-b(1), -b(4)});
+        const dfl d2 = df_add(X2, dfl{-b(2), -b(5)});
         const dfl q = df_add_sloppy(df_add_sloppy(df_sqr(d0), df_sqr(d1)), df_sqr(d2));   // no cancellation
-        const dfl s = {b[6], b[7]};
+        const dfl s = {b(6), b(7)};
         const dfl a = df_mul(s, q);
         if (a.hi < (float)kBlobCull) continue;
-        const dfl AG = df_mul(dfl{b[8], b[9]}, df_exp(a, sT));
+        const dfl AG = df_mul(dfl{b(8), b(9)}, df_exp(a, sT));
         N = df_add_sloppy(N, AG);                                    // absolute error ~u^2 |N|, |AG|
         const dfl c = df_mul(dfl{2.f * s.hi, 2.f * s.lo}, AG);      // 2 s A G
         G0 = df_add_sloppy(G0, df_mul(c, d0));
@@ -204,6 +194,31 @@ __device__ __forceinline__ void blobs_df(const float *__restrict__ sd, int nb, c
     g[0] += df_to_double(G0);
     g[1] += df_to_double(G1);
     g[2] += df_to_double(G2);
+}
+
+// Ray right-hand side of an isotropic medium with the blob sums in
+// double-float (GF_F64X): base index law, D and f in FP64 exactly as
+// rhs_iso, blob terms from blobs_df over the rows in sd (stride as there).
+template <int KIND, bool WANT_D>
+__device__ __forceinline__ bool rhs_df(const MediumParams &m, const float *__restrict__ sd, int nb, int stride,
+                                       const Omega<double> &om, const double *y, double *f, double &D,
+                                       const float *__restrict__ dT, int &live)
+{
+    double n2, g[3];
+    EvalCtx<double> base;
+    iso_index<double, KIND>(m, nullptr, 0, y, n2, g, base);
+    blobs_df(sd, nb, y, n2, g, dT, live, stride);
+    if constexpr (WANT_D) D = y[3] * y[3] + y[4] * y[4] + y[5] * y[5] - om.w * om.w * n2;
+    if (!(n2 > 0.0)) return false;
+    const double inv = 1.0 / n2;
+    const double a = inv * om.inv_w, b = om.half_w * inv;
+    f[0] = a * y[3];
+    f[1] = a * y[4];
+    f[2] = a * y[5];
+    f[3] = b * g[0];
+    f[4] = b * g[1];
+    f[5] = b * g[2];
+    return true;
 }
 
 }  // namespace gf

@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 
+#include "gf_dfloat.cuh"
 #include "gf_internal.cuh"
 
 namespace gf {
@@ -41,6 +42,7 @@ struct BatchView {
     int32_t n_media, nb_max, n_items, pad;
     const double *blobs;        // n_media x nb_max scaled rows (kBlobStride values each)
     const float *pre;           // n_media x nb_max FP32 pre-test rows (4 floats each)
+    const float *df;            // n_media x nb_max double-float rows (GF_F64X launches)
     const float *pre_lim;       // n_media: validity bound of the pre-test (MediumParams::pre_lim)
     const int32_t *nb;          // n_media
     const double *base;         // n_media x 3: n_h2, n02, n02a2
@@ -57,33 +59,49 @@ struct Lane {
     MediumParams mp;
 };
 
-template <int KIND>
+// A lane's blob slot in shared memory (field f of blob j at [(row j + f) * stride]):
+// scaled FP64 rows and FP32 pre-test rows (pf may be NULL), or double-float rows.
+struct Slot {
+    double *sm;
+    float *pf;
+    float *sf;
+};
+
+// Block-shared exponential tables: 2^(j/2048) (FP64) or the double-float 2^(j/64).
+struct Tabs {
+    const double *T;
+    const float *dT;
+};
+
+template <int KIND, bool DF>
 struct LaneRhs {
     const Lane &L;
-    const double *sm;
-    const float *pf;
+    const Slot &S;
     int stride;
     const Omega<double> &om;
-    const double *T;
+    const Tabs &tb;
     template <bool WANT_D = true>
     __device__ __forceinline__ bool eval(const double *y, double *f, double &D) const
     {
-        EvalCtx<double> cx;
-        cx.T = T;
-        cx.pre = pf;
-        cx.pre_stride = stride;
-        return rhs_iso<double, KIND, WANT_D>(L.mp, sm, L.nb, om, y, f, D, cx, stride);
+        if constexpr (DF) {
+            int live = 0;
+            return rhs_df<KIND, WANT_D>(L.mp, S.sf, L.nb, stride, om, y, f, D, tb.dT, live);
+        } else {
+            EvalCtx<double> cx;
+            cx.T = tb.T;
+            cx.pre = S.pf;
+            cx.pre_stride = stride;
+            return rhs_iso<double, KIND, WANT_D>(L.mp, S.sm, L.nb, om, y, f, D, cx, stride);
+        }
     }
 };
 
 // Load ray `ray` of medium `med` into lane L and its per-thread shared-memory
-// blob slot (field f of blob j at sm[(kBlobStride j + f) * stride], FP32
-// pre-test field f at pf[(4 j + f) * stride]).  Returns false if the ray is
-// not active.
-template <int KIND>
+// blob slot.  Returns false if the ray is not active.
+template <int KIND, bool DF>
 __device__ __forceinline__ bool lane_load(Lane &L, const BatchView &B, const RaysView<double> &r,
-                                          int med, int64_t ray, double *sm, float *pf, int stride,
-                                          const double *T, const Ctl &c)
+                                          int med, int64_t ray, const Slot &S, int stride, const Tabs &tb,
+                                          const Ctl &c)
 {
     L.status = r.status[ray];
     if (L.status != GF_RAY_ACTIVE) return false;
@@ -93,12 +111,17 @@ __device__ __forceinline__ bool lane_load(Lane &L, const BatchView &B, const Ray
     L.mp.n_h2 = B.base[3 * med];
     L.mp.n02 = B.base[3 * med + 1];
     L.mp.n02a2 = B.base[3 * med + 2];
-    const double *src = B.blobs + (int64_t)med * B.nb_max * kBlobStride;
-    for (int j = 0; j < L.nb * kBlobStride; ++j) sm[j * stride] = src[j];
-    if (pf != nullptr) {
-        L.mp.pre_lim = B.pre_lim[med];
-        const float *psrc = B.pre + (int64_t)med * B.nb_max * 4;
-        for (int j = 0; j < L.nb * 4; ++j) pf[j * stride] = psrc[j];
+    if constexpr (DF) {
+        const float *dsrc = B.df + (int64_t)med * B.nb_max * kDfBlobStride;
+        for (int j = 0; j < L.nb * kDfBlobStride; ++j) S.sf[j * stride] = dsrc[j];
+    } else {
+        const double *src = B.blobs + (int64_t)med * B.nb_max * kBlobStride;
+        for (int j = 0; j < L.nb * kBlobStride; ++j) S.sm[j * stride] = src[j];
+        if (S.pf != nullptr) {
+            L.mp.pre_lim = B.pre_lim[med];
+            const float *psrc = B.pre + (int64_t)med * B.nb_max * 4;
+            for (int j = 0; j < L.nb * 4; ++j) S.pf[j * stride] = psrc[j];
+        }
     }
 #pragma unroll
     for (int c2 = 0; c2 < 6; ++c2) L.y[c2] = r.y[c2 * r.ld + ray];
@@ -110,7 +133,7 @@ __device__ __forceinline__ bool lane_load(Lane &L, const BatchView &B, const Ray
     L.h = c.h0;
     L.fmax = c.fac_max;
     double D;
-    const LaneRhs<KIND> f{L, sm, pf, stride, c.om, T};
+    const LaneRhs<KIND, DF> f{L, S, stride, c.om, tb};
     bool ok = f.eval(L.y, L.K1, D);
     L.dm = fmax(L.dm, fabs(D));
     if (!ok) L.status = GF_RAY_CUTOFF;
@@ -118,13 +141,12 @@ __device__ __forceinline__ bool lane_load(Lane &L, const BatchView &B, const Ray
 }
 
 // Final residual and store of a lane whose ray stopped.
-template <int KIND>
+template <int KIND, bool DF>
 __device__ __forceinline__ void lane_store(const Lane &L, const RaysView<double> &r, int32_t *rejects,
-                                           const double *sm, const float *pf, int stride, const double *T,
-                                           const Ctl &c)
+                                           const Slot &S, int stride, const Tabs &tb, const Ctl &c)
 {
     double K[6], D;
-    const LaneRhs<KIND> f{L, sm, pf, stride, c.om, T};
+    const LaneRhs<KIND, DF> f{L, S, stride, c.om, tb};
     f.eval(L.y, K, D);
     const double dm = fmax(L.dm, fabs(D));
     const int64_t i = L.ray;
@@ -140,9 +162,8 @@ __device__ __forceinline__ void lane_store(const Lane &L, const RaysView<double>
 
 // One attempted DOPRI5 step of an active lane (the step-size controller of
 // Hairer-Norsett-Wanner I, Sec. II.4).  Leaves L.status != ACTIVE when the ray stops.
-template <int KIND>
-__device__ __forceinline__ void lane_attempt(Lane &L, const double *sm, const float *pf, int stride,
-                                             const double *T, const Ctl &c)
+template <int KIND, bool DF>
+__device__ __forceinline__ void lane_attempt(Lane &L, const Slot &S, int stride, const Tabs &tb, const Ctl &c)
 {
     using namespace dp;
     if (L.steps >= c.max_steps || L.attempts >= c.max_attempts) { L.status = GF_RAY_MAX_STEPS; return; }
@@ -152,7 +173,7 @@ __device__ __forceinline__ void lane_attempt(Lane &L, const double *sm, const fl
     bool last = false;
     if (L.t + hs >= c.t_max) { hs = c.t_max - L.t; last = true; }
     if (hs < 1e-14 * fmax(1.0, fabs(L.t))) { L.status = GF_RAY_STEP_UNDERFLOW; return; }
-    const LaneRhs<KIND> f{L, sm, pf, stride, c.om, T};
+    const LaneRhs<KIND, DF> f{L, S, stride, c.om, tb};
     const double *y = L.y, *K1 = L.K1;
     double K2[6], K3[6], K4[6], K5[6], K6[6], K7[6], Y[6], D;
 #pragma unroll
@@ -216,26 +237,47 @@ __device__ __forceinline__ void lane_attempt(Lane &L, const double *sm, const fl
 
 // ------------------------------------------------------- one launch per medium
 
-template <int KIND>
+// The exponential table of the evaluator (DF: double-float 2^(j/64), else 2^(j/2048)).
+template <bool DF>
+__device__ __forceinline__ Tabs stage_tables(double *sT, float *sdT)
+{
+    if constexpr (DF)
+        stage_dfexp_table(sdT);
+    else
+        stage_exp_table(sT);
+    return Tabs{sT, sdT};
+}
+
+// Lane slot s of this thread: FP64 rows then FP32 pre-test rows (if the view
+// carries them), or double-float rows; `stride` lanes per row field.
+template <bool DF>
+__device__ __forceinline__ Slot lane_slot(double *sm_dyn, const BatchView &B, int stride, int s)
+{
+    const int at = s * blockDim.x + threadIdx.x;
+    if constexpr (DF) return Slot{nullptr, nullptr, reinterpret_cast<float *>(sm_dyn) + at};
+    float *pf = B.pre ? reinterpret_cast<float *>(sm_dyn + (size_t)B.nb_max * kBlobStride * stride) + at : nullptr;
+    return Slot{sm_dyn + at, pf, nullptr};
+}
+
+template <int KIND, bool DF>
 __global__ void __launch_bounds__(128) dopri5_medium_kernel(const BatchView B, const int med,
                                                             const int64_t lo, const int64_t hi,
                                                             const RaysView<double> r, int32_t *rejects,
                                                             const Ctl c)
 {
     extern __shared__ double sm_dyn[];
-    __shared__ double sT[kExpTabN];
-    stage_exp_table(sT);
+    __shared__ double sT[DF ? 1 : kExpTabN];
+    __shared__ float sdT[DF ? 128 : 1];
+    const Tabs tb = stage_tables<DF>(sT, sdT);
     __syncthreads();
     const int stride = blockDim.x;
-    double *sm = sm_dyn + threadIdx.x;
-    float *pf = B.pre ? reinterpret_cast<float *>(sm_dyn + (size_t)B.nb_max * kBlobStride * stride) + threadIdx.x
-                      : nullptr;
+    const Slot S = lane_slot<DF>(sm_dyn, B, stride, 0);
     const int64_t ray = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (ray >= hi) return;
     Lane L;
-    if (!lane_load<KIND>(L, B, r, med, ray, sm, pf, stride, sT, c)) return;
-    while (L.status == GF_RAY_ACTIVE) lane_attempt<KIND>(L, sm, pf, stride, sT, c);
-    lane_store<KIND>(L, r, rejects, sm, pf, stride, sT, c);
+    if (!lane_load<KIND, DF>(L, B, r, med, ray, S, stride, tb, c)) return;
+    while (L.status == GF_RAY_ACTIVE) lane_attempt<KIND, DF>(L, S, stride, tb, c);
+    lane_store<KIND, DF>(L, r, rejects, S, stride, tb, c);
 }
 
 // ------------------------------------------------------------- persistent
@@ -245,17 +287,17 @@ __global__ void __launch_bounds__(128) dopri5_medium_kernel(const BatchView B, c
 // refills them with the next rays of its current item, popping new items as
 // items run dry; lanes may hold rays of different media (each lane has its own
 // blob slot in shared memory).  RPT ray slots per thread are interleaved.
-template <int KIND, int RPT>
+template <int KIND, int RPT, bool DF>
 __global__ void dopri5_persistent_kernel(const BatchView B, const RaysView<double> r,
                                          int32_t *rejects, const Ctl c,
                                          const int compaction, int *__restrict__ head)
 {
     extern __shared__ double sm_dyn[];
-    __shared__ double sT[kExpTabN];
-    stage_exp_table(sT);
+    __shared__ double sT[DF ? 1 : kExpTabN];
+    __shared__ float sdT[DF ? 128 : 1];
+    const Tabs tb = stage_tables<DF>(sT, sdT);
     __syncthreads();
     const int stride = blockDim.x * RPT;
-    float *pf_base = B.pre ? reinterpret_cast<float *>(sm_dyn + (size_t)B.nb_max * kBlobStride * stride) : nullptr;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
     Lane L[RPT];
@@ -268,8 +310,7 @@ __global__ void dopri5_persistent_kernel(const BatchView B, const RaysView<doubl
     for (;;) {
 #pragma unroll
         for (int s = 0; s < RPT; ++s) {
-            double *sm = sm_dyn + s * blockDim.x + threadIdx.x;
-            float *pf = pf_base ? pf_base + s * blockDim.x + threadIdx.x : nullptr;
+            const Slot S = lane_slot<DF>(sm_dyn, B, stride, s);
             unsigned freem = __ballot_sync(0xffffffffu, !active[s]);
             while (freem != 0u && !exhausted) {
                 if (cur >= end) {
@@ -288,11 +329,11 @@ __global__ void dopri5_persistent_kernel(const BatchView B, const RaysView<doubl
                 const int take = (int)min((int64_t)nfree, end - cur);
                 const int rank = __popc(freem & lt_mask);
                 if (!active[s] && rank < take) {
-                    if (lane_load<KIND>(L[s], B, r, cur_med, cur + rank, sm, pf, stride, sT, c)) {
+                    if (lane_load<KIND, DF>(L[s], B, r, cur_med, cur + rank, S, stride, tb, c)) {
                         if (L[s].status == GF_RAY_ACTIVE)
                             active[s] = true;
                         else
-                            lane_store<KIND>(L[s], r, rejects, sm, pf, stride, sT, c);
+                            lane_store<KIND, DF>(L[s], r, rejects, S, stride, tb, c);
                     }
                 }
                 cur += take;
@@ -307,11 +348,10 @@ __global__ void dopri5_persistent_kernel(const BatchView B, const RaysView<doubl
 #pragma unroll
             for (int s = 0; s < RPT; ++s) {
                 if (active[s]) {
-                    double *sm = sm_dyn + s * blockDim.x + threadIdx.x;
-                    float *pf = pf_base ? pf_base + s * blockDim.x + threadIdx.x : nullptr;
-                    lane_attempt<KIND>(L[s], sm, pf, stride, sT, c);
+                    const Slot S = lane_slot<DF>(sm_dyn, B, stride, s);
+                    lane_attempt<KIND, DF>(L[s], S, stride, tb, c);
                     if (L[s].status != GF_RAY_ACTIVE) {
-                        lane_store<KIND>(L[s], r, rejects, sm, pf, stride, sT, c);
+                        lane_store<KIND, DF>(L[s], r, rejects, S, stride, tb, c);
                         active[s] = false;
                     }
                 }
@@ -336,8 +376,9 @@ struct gf_batch_s {
     int kind = 0, n_media = 0, nb_max = 0;
     std::vector<int64_t> offsets;
     double *d_blobs = nullptr, *d_base = nullptr;
-    float *d_pre = nullptr, *d_pre_lim = nullptr;
+    float *d_pre = nullptr, *d_pre_lim = nullptr, *d_df = nullptr;
     int32_t *d_nb = nullptr;
+    gf_precision prec = GF_F64;   // GF_F64 or GF_F64X (gf_batch_set_precision)
     int *d_head = nullptr;
     // work items for the current chunk size
     int chunk = 0, n_items = 0;
@@ -358,6 +399,7 @@ static void batch_free(gf_batch b)
     cudaFree(b->d_blobs);
     cudaFree(b->d_pre);
     cudaFree(b->d_pre_lim);
+    cudaFree(b->d_df);
     cudaFree(b->d_base);
     cudaFree(b->d_nb);
     cudaFree(b->d_head);
@@ -406,19 +448,30 @@ static gf_status build_items(gf_batch b, int chunk)
 }
 
 // Device view of a batch; pre = false leaves the pre-test tables out (the
-// kernels then decide every blob term in FP64).
-static BatchView view_of(gf_batch b, bool pre)
+// kernels then decide every blob term in FP64), df adds the double-float rows.
+static BatchView view_of(gf_batch b, bool pre, bool df)
 {
-    return BatchView{b->n_media, b->nb_max, b->n_items, 0, b->d_blobs,
-                     pre ? b->d_pre : nullptr, pre ? b->d_pre_lim : nullptr, b->d_nb,
-                     b->d_base, b->d_item_medium, b->d_item_begin, b->d_item_end};
+    BatchView v{};   // fields by name: the kernels trust every pointer they read
+    v.n_media = b->n_media;
+    v.nb_max = b->nb_max;
+    v.n_items = b->n_items;
+    v.blobs = b->d_blobs;
+    v.pre = pre ? b->d_pre : nullptr;
+    v.pre_lim = pre ? b->d_pre_lim : nullptr;
+    v.df = df ? b->d_df : nullptr;
+    v.nb = b->d_nb;
+    v.base = b->d_base;
+    v.item_medium = b->d_item_medium;
+    v.item_begin = b->d_item_begin;
+    v.item_end = b->d_item_end;
+    return v;
 }
 
 // Every table a launch reads must exist (a view over missing tables would
 // make the kernels read through null pointers).
-static bool view_complete(gf_batch b, bool pre, gf_schedule sched)
+static bool view_complete(gf_batch b, bool pre, bool df, gf_schedule sched)
 {
-    return b->d_blobs && b->d_nb && b->d_base && (!pre || (b->d_pre && b->d_pre_lim)) &&
+    return b->d_blobs && b->d_nb && b->d_base && (!pre || (b->d_pre && b->d_pre_lim)) && (!df || b->d_df) &&
            (sched != GF_SCHED_PERSISTENT || (b->d_head && b->d_item_medium && b->d_item_begin && b->d_item_end));
 }
 
@@ -469,9 +522,10 @@ static gf_status check_tune(const gf_tune *t)
 static const gf_tune kDefaultTune = {128, 1, 4, 64};
 
 // Shared memory of one lane slot: scaled FP64 rows, and FP32 pre-test rows
-// when `pre`.
-static size_t lane_slot_bytes(int nb_max, bool pre)
+// when `pre`; or double-float rows (GF_F64X).
+static size_t lane_slot_bytes(int nb_max, bool pre, bool df = false)
 {
+    if (df) return (size_t)nb_max * kDfBlobStride * sizeof(float);
     return (size_t)nb_max * (kBlobStride * sizeof(double) + (pre ? 4 * sizeof(float) : 0));
 }
 
@@ -485,18 +539,20 @@ struct LaunchPlan {
     int grid = 0, block = 128, rpt = 1;
     size_t smem = 0;
     bool pre = true;   // lane slots hold the FP32 pre-test rows
+    bool df = false;   // double-float blob sums (GF_F64X)
 };
 
 static void size_slots(gf_batch b, int lanes, LaunchPlan &p)
 {
-    p.pre = lane_slot_bytes(b->nb_max, true) * lanes <= kMaxLaneSmem;
-    p.smem = lane_slot_bytes(b->nb_max, p.pre) * lanes;
+    p.df = b->prec == GF_F64X;
+    p.pre = !p.df && lane_slot_bytes(b->nb_max, true) * lanes <= kMaxLaneSmem;
+    p.smem = lane_slot_bytes(b->nb_max, p.pre, p.df) * lanes;
 }
 
-template <int KIND, int RPT>
+template <int KIND, int RPT, bool DF>
 static cudaError_t plan_persistent_rpt(gf_batch b, const gf_tune &t, LaunchPlan &p)
 {
-    auto k = dopri5_persistent_kernel<KIND, RPT>;
+    auto k = dopri5_persistent_kernel<KIND, RPT, DF>;
     p.block = t.block;
     p.rpt = RPT;
     size_slots(b, t.block * RPT, p);
@@ -516,13 +572,20 @@ static cudaError_t plan_persistent_rpt(gf_batch b, const gf_tune &t, LaunchPlan 
 template <int KIND>
 static cudaError_t plan(gf_batch b, gf_schedule sched, const gf_tune &t, LaunchPlan &p)
 {
-    if (sched == GF_SCHED_PERSISTENT)
-        return t.rays_per_thread == 1 ? plan_persistent_rpt<KIND, 1>(b, t, p)
-                                      : plan_persistent_rpt<KIND, 2>(b, t, p);
+    const bool df = b->prec == GF_F64X;
+    if (sched == GF_SCHED_PERSISTENT) {
+        if (df)
+            return t.rays_per_thread == 1 ? plan_persistent_rpt<KIND, 1, true>(b, t, p)
+                                          : plan_persistent_rpt<KIND, 2, true>(b, t, p);
+        return t.rays_per_thread == 1 ? plan_persistent_rpt<KIND, 1, false>(b, t, p)
+                                      : plan_persistent_rpt<KIND, 2, false>(b, t, p);
+    }
     p.block = 128;
     size_slots(b, p.block, p);
-    return cudaFuncSetAttribute(dopri5_medium_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)p.smem);
+    return df ? cudaFuncSetAttribute(dopri5_medium_kernel<KIND, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)p.smem)
+              : cudaFuncSetAttribute(dopri5_medium_kernel<KIND, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)p.smem);
 }
 
 template <int KIND>
@@ -530,23 +593,29 @@ static cudaError_t launch(gf_batch b, gf_schedule sched, const gf_tune &t, const
                           const RaysView<double> &r, int32_t *rejects, double omega, const Ctl &c,
                           cudaStream_t s)
 {
-    const BatchView B = view_of(b, p.pre);
+    const BatchView B = view_of(b, p.pre, p.df);
     if (sched == GF_SCHED_PERSISTENT) {
         cudaError_t e = cudaMemsetAsync(b->d_head, 0, sizeof(int), s);
         if (e != cudaSuccess) return e;
-        if (p.rpt == 1)
-            dopri5_persistent_kernel<KIND, 1><<<p.grid, p.block, p.smem, s>>>(B, r, rejects, c,
-                                                                             t.compaction, b->d_head);
-        else
-            dopri5_persistent_kernel<KIND, 2><<<p.grid, p.block, p.smem, s>>>(B, r, rejects, c,
-                                                                             t.compaction, b->d_head);
+#define GF_D5_PERSIST(RPT, DF)                                                                            \
+    dopri5_persistent_kernel<KIND, RPT, DF><<<p.grid, p.block, p.smem, s>>>(B, r, rejects, c, t.compaction, \
+                                                                          b->d_head)
+        if (p.df) {
+            if (p.rpt == 1) GF_D5_PERSIST(1, true); else GF_D5_PERSIST(2, true);
+        } else {
+            if (p.rpt == 1) GF_D5_PERSIST(1, false); else GF_D5_PERSIST(2, false);
+        }
+#undef GF_D5_PERSIST
         return cudaGetLastError();
     }
     for (int m = 0; m < b->n_media; ++m) {
         const int64_t lo = b->offsets[m], hi = b->offsets[m + 1];
         if (hi <= lo) continue;
         const unsigned blocks = (unsigned)((hi - lo + p.block - 1) / p.block);
-        dopri5_medium_kernel<KIND><<<blocks, p.block, p.smem, s>>>(B, m, lo, hi, r, rejects, c);
+        if (p.df)
+            dopri5_medium_kernel<KIND, true><<<blocks, p.block, p.smem, s>>>(B, m, lo, hi, r, rejects, c);
+        else
+            dopri5_medium_kernel<KIND, false><<<blocks, p.block, p.smem, s>>>(B, m, lo, hi, r, rejects, c);
     }
     return cudaGetLastError();
 }
@@ -572,12 +641,12 @@ static cudaError_t enqueue(gf_batch b, gf_schedule sched, const gf_tune &t, cons
     GF_D5_DISPATCH(launch, b, sched, t, p, r, rejects, omega, c, s)
 }
 
-static std::string graph_key(gf_schedule sched, const gf_tune &t, const gf_rays *rays, int32_t *rejects,
-                             double omega, const gf_step_ctl *c)
+static std::string graph_key(gf_precision prec, gf_schedule sched, const gf_tune &t, const gf_rays *rays,
+                             int32_t *rejects, double omega, const gf_step_ctl *c)
 {
     char buf[512];
-    snprintf(buf, sizeof buf, "%d|%d,%d,%d,%d|%lld,%lld,%p,%p,%p,%p,%p,%p,%p|%p|%.17g|%.17g,%.17g,%.17g,%.17g,%.17g,%.17g,%.17g,%.17g,%lld",
-             (int)sched, t.block, t.rays_per_thread, t.compaction, t.chunk, (long long)rays->n,
+    snprintf(buf, sizeof buf, "p%d|%d|%d,%d,%d,%d|%lld,%lld,%p,%p,%p,%p,%p,%p,%p|%p|%.17g|%.17g,%.17g,%.17g,%.17g,%.17g,%.17g,%.17g,%.17g,%lld",
+             (int)prec, (int)sched, t.block, t.rays_per_thread, t.compaction, t.chunk, (long long)rays->n,
              (long long)rays->ld, rays->y, (void *)rays->t, (void *)rays->status, (void *)rays->steps,
              (void *)rays->d_res, (void *)rays->d_max, (void *)rejects, (void *)rejects, omega, c->rtol,
              c->atol, c->h0, c->t_max, c->radius, c->fac_min, c->fac_max, c->safety,
@@ -596,14 +665,14 @@ static gf_status run_dopri5(gf_batch b, const gf_rays *rays, int32_t *rejects, d
     const Ctl c = ctl_of(ctl, omega);
     LaunchPlan p;
     if ((s = cuda_status(plan_any(b, sched, t, p), "gf_trace_dopri5 launch plan")) != GF_OK) return s;
-    if (!view_complete(b, p.pre, sched)) {
+    if (!view_complete(b, p.pre, p.df, sched)) {
         set_error("gf_trace_dopri5: batch tables missing");
         return GF_ERR_INVALID_ARG;
     }
     if (!use_graph)
         return cuda_status(enqueue(b, sched, t, p, r, rejects, omega, c, stream), "gf_trace_dopri5 launch");
     GraphCache &g = b->graphs[sched];
-    const std::string key = graph_key(sched, t, rays, rejects, omega, ctl);
+    const std::string key = graph_key(b->prec, sched, t, rays, rejects, omega, ctl);
     if (g.exec == nullptr || g.key != key) {
         if (g.exec) {
             cudaGraphExecDestroy(g.exec);
@@ -657,8 +726,8 @@ static std::string tune_key(gf_batch b, const gf_step_ctl *c)
     cudaDeviceProp p;
     cudaGetDeviceProperties(&p, b->device);
     char buf[400];
-    snprintf(buf, sizeof buf, "%s|sm%d|kind%d|nb%d|f64|rtol%.3g|atol%.3g", p.name, p.multiProcessorCount,
-             b->kind, b->nb_max, c->rtol, c->atol);
+    snprintf(buf, sizeof buf, "%s|sm%d|kind%d|nb%d|%s|rtol%.3g|atol%.3g", p.name, p.multiProcessorCount,
+             b->kind, b->nb_max, b->prec == GF_F64X ? "f64x" : "f64", c->rtol, c->atol);
     return buf;
 }
 
@@ -737,8 +806,10 @@ gf_status gf_batch_create(const gf_medium *media, int32_t n_media, const int64_t
     std::vector<float> pre_lim(n_media);
     std::vector<int32_t> nb(n_media);
     gf_status s = GF_OK;
-    const size_t row = (size_t)b->nb_max * kBlobStride, prow = (size_t)b->nb_max * 4;
+    const size_t row = (size_t)b->nb_max * kBlobStride, prow = (size_t)b->nb_max * 4,
+                 drow = (size_t)b->nb_max * kDfBlobStride;
     if ((s = cuda_status(cudaMalloc(&b->d_blobs, row * n_media * sizeof(double)), "cudaMalloc(batch)")) != GF_OK ||
+        (s = cuda_status(cudaMalloc(&b->d_df, drow * n_media * sizeof(float)), "cudaMalloc(batch)")) != GF_OK ||
         (s = cuda_status(cudaMalloc(&b->d_pre, prow * n_media * sizeof(float)), "cudaMalloc(batch)")) != GF_OK ||
         (s = cuda_status(cudaMalloc(&b->d_pre_lim, pre_lim.size() * sizeof(float)), "cudaMalloc(batch)")) != GF_OK ||
         (s = cuda_status(cudaMalloc(&b->d_base, base.size() * sizeof(double)), "cudaMalloc(batch)")) != GF_OK ||
@@ -759,6 +830,8 @@ gf_status gf_batch_create(const gf_medium *media, int32_t n_media, const int64_t
                                          p.n_blobs * kBlobStride * sizeof(double), cudaMemcpyDeviceToDevice),
                               "cudaMemcpy(batch blobs)")) != GF_OK ||
              (s = cuda_status(cudaMemcpy(b->d_pre + prow * m, p.pre32, p.n_blobs * 4 * sizeof(float),
+                                         cudaMemcpyDeviceToDevice), "cudaMemcpy(batch blobs)")) != GF_OK ||
+             (s = cuda_status(cudaMemcpy(b->d_df + drow * m, p.dfrows, p.n_blobs * kDfBlobStride * sizeof(float),
                                          cudaMemcpyDeviceToDevice), "cudaMemcpy(batch blobs)")) != GF_OK)) {
             batch_free(b);
             return s;
@@ -774,6 +847,23 @@ gf_status gf_batch_create(const gf_medium *media, int32_t n_media, const int64_t
         return s;
     }
     *out = b;
+    return GF_OK;
+}
+
+gf_status gf_batch_set_precision(gf_batch b, gf_precision prec)
+{
+    if (b == nullptr) {
+        set_error("gf_batch_set_precision: batch is NULL");
+        return GF_ERR_INVALID_ARG;
+    }
+    if (prec != GF_F64 && prec != GF_F64X) {
+        set_error("gf_batch_set_precision: DOPRI5 runs in GF_F64 or GF_F64X");
+        return GF_ERR_UNSUPPORTED;
+    }
+    if (prec != b->prec) {
+        b->prec = prec;
+        b->tuned = false;   // a launch shape tuned for the other mode
+    }
     return GF_OK;
 }
 
@@ -858,6 +948,8 @@ gf_status gf_dopri5_autotune(gf_batch b, const gf_rays *rays, double omega, cons
     sub.d_blobs = b->d_blobs;
     sub.d_pre = b->d_pre;
     sub.d_pre_lim = b->d_pre_lim;
+    sub.d_df = b->d_df;
+    sub.prec = b->prec;
     sub.d_base = b->d_base;
     sub.d_nb = b->d_nb;
     if ((s = cuda_status(cudaMalloc(&sub.d_head, sizeof(int)), "cudaMalloc(tune)")) != GF_OK) {
@@ -888,7 +980,7 @@ gf_status gf_dopri5_autotune(gf_batch b, const gf_rays *rays, double omega, cons
             for (int cp : comps)
                 for (int ch : chunks) {
                     gf_tune cand{bl, rp, cp, ch};
-                    if (lane_slot_bytes(b->nb_max, false) * bl * rp > kMaxLaneSmem) continue;
+                    if (lane_slot_bytes(b->nb_max, false, b->prec == GF_F64X) * bl * rp > kMaxLaneSmem) continue;
                     reset();
                     cudaEventRecord(e0);
                     gf_status rs = run_dopri5(&sub, &scratch, nullptr, omega, ctl, GF_SCHED_PERSISTENT,
@@ -913,7 +1005,7 @@ gf_status gf_dopri5_autotune(gf_batch b, const gf_rays *rays, double omega, cons
     cudaFree(sub.d_item_begin);
     cudaFree(sub.d_item_end);
     sub.d_blobs = nullptr;
-    sub.d_pre = sub.d_pre_lim = nullptr;
+    sub.d_pre = sub.d_pre_lim = sub.d_df = nullptr;
     sub.d_base = nullptr;
     sub.d_nb = nullptr;
     sub.d_head = nullptr;

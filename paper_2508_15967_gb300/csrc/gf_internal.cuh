@@ -21,6 +21,7 @@ enum : int { K_HOMOG = GF_MED_HOMOG, K_LUNEBURG = GF_MED_LUNEBURG, K_GRIN = GF_M
 //          sigma, -sigma cx, -sigma cy, -sigma cz, A, -2 sigma A
 // with sigma = sqrt(-s), so that A exp(s |x - c|^2) = A exp(-|u|^2), u = sigma x - sigma c.
 constexpr int kBlobStride = 6;
+constexpr int kDfRowFloats = 10;   // double-float blob row (GF_F64X), see gf_dfloat.cuh
 
 // Medium as the kernels see it (passed by value as a kernel argument).
 struct MediumParams {
@@ -32,6 +33,7 @@ struct MediumParams {
     const float *blobs32;        // float copy of the scaled rows
     const double *blobs64s;      // n_blobs scaled rows
     const float *pre32;          // n_blobs x 4 floats: sigma, -sigma cx, -sigma cy, -sigma cz
+    const float *dfrows;         // n_blobs double-float rows (GF_F64X; layout in gf_dfloat.cuh)
     const float4 *grid;          // grid_n^3 nodes x 2 float4
     int32_t n_species, pad2;     // cold plasma
     double species[2 * GF_MAX_SPECIES];
@@ -56,7 +58,7 @@ struct gf_medium_s {
     gf::MediumParams p{};
     int device = -1;
     double *d_blobs64 = nullptr;     // plain rows, then scaled rows (2 x n_blobs rows)
-    float *d_blobs32 = nullptr;      // float scaled rows, then pre-test rows
+    float *d_blobs32 = nullptr;      // float scaled rows, pre-test rows, double-float rows
     float4 *d_grid = nullptr;
     cudaLibrary_t jit_lib = nullptr;
     cudaKernel_t jit_kernel = nullptr;

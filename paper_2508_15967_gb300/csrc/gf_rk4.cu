@@ -21,21 +21,7 @@ struct RhsDF {
     template <bool WANT_D = true>
     __device__ __forceinline__ bool eval(const double *y, double *f, double &D, EvalCtx<double> &cx) const
     {
-        double n2, g[3];
-        EvalCtx<double> base;
-        iso_index<double, KIND>(m, nullptr, 0, y, n2, g, base);
-        blobs_df(cx.dfb, nb, y, n2, g, cx.dfT, cx.live);
-        if constexpr (WANT_D) D = y[3] * y[3] + y[4] * y[4] + y[5] * y[5] - om.w * om.w * n2;
-        if (!(n2 > 0.0)) return false;
-        const double inv = 1.0 / n2;
-        const double a = inv * om.inv_w, b = om.half_w * inv;
-        f[0] = a * y[3];
-        f[1] = a * y[4];
-        f[2] = a * y[5];
-        f[3] = b * g[0];
-        f[4] = b * g[1];
-        f[5] = b * g[2];
-        return true;
+        return rhs_df<KIND, WANT_D>(m, cx.dfb, nb, 1, om, y, f, D, cx.dfT, cx.live);
     }
 };
 

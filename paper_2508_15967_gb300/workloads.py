@@ -30,7 +30,7 @@ import numpy as np
 
 SEED_BASE = 250815967
 
-LUNEBURG, GRIN, ANISO, BATCHED, ADJOINT = 1, 2, 3, 4, 5
+LUNEBURG, GRIN, ANISO, BATCHED, ADJOINT, COLD = 1, 2, 3, 4, 5, 6
 
 
 def rng_for(index: int, offset: int = 0) -> np.random.Generator:
@@ -261,4 +261,22 @@ def adjoint(n: int = 65536, n_steps: int = 4000, dt: float = 1e-3, n_blobs: int 
     wl = Workload("adjoint", dict(kind="luneburg", blobs=blobs), x0, d, 1.0, dt, n_steps)
     wl.extra = dict(theta=blobs[:, 0].copy(), theta_star=theta_star,
                     checkpoint_every=checkpoint_every)
+    return wl
+
+
+def cold(n: int = 1 << 20, n_steps: int = 1500, dt: float = 1e-2) -> Workload:
+    """Cold magnetised plasma slab (Sec. 4.1): electrons and ions with squared
+    plasma frequencies 0.7 and 0.02 times the density f(x) = 1 + 0.1 x (the
+    linear gradient of Eq. 4) and cyclotron frequencies -0.5 and 0.05 times
+    g(x) = 1 + 0.05 x, w = 1.  Rays start at (x, y, 0) with x, y uniform in
+    [-1, 1), k_y uniform in +-0.25, k_z in +-0.2; k_x is the O-branch root
+    found by Newton from k_x = 1.2 (extra["k_start"] holds the start).  By
+    t = 15 most rays have reflected at the O-mode cut-off (x ~ 4.3) and the
+    density stays positive along every ray."""
+    rr = rng_for(COLD, 7)
+    x0 = np.column_stack([rr.uniform(-1.0, 1.0, n), rr.uniform(-1.0, 1.0, n), np.zeros(n)])
+    k_start = np.column_stack([np.full(n, 1.2), rr.uniform(-0.25, 0.25, n), rr.uniform(-0.2, 0.2, n)])
+    med = dict(kind="cold", species=((0.7, -0.5), (0.02, 0.05)), profile=(1.0, 0.1, 1.0, 0.05))
+    wl = Workload("cold", med, x0, np.zeros_like(x0), 1.0, dt, n_steps)
+    wl.extra = dict(k_start=k_start)
     return wl

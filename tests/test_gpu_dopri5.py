@@ -222,6 +222,34 @@ def test_autotune_returns_a_valid_shape_and_caches_it(tmp_path):
         assert np.array_equal(g[k], ref[k])
 
 
+def test_f64x_mode_parity_and_schedule_independence():
+    """GF_F64X (double-float blob sums): as accurate as the oracle at a fixed
+    end time and at the exits, bit-identical across both schedules and several
+    launch shapes; switching back to GF_F64 gives a never-switched batch's
+    results; GF_F32 is refused."""
+    wl, om, media, batch, k0 = _setup()
+    off = wl.extra["offsets"]
+    gf.gf_batch_set_precision(batch, gf.GF_F64X)
+    ctl = _ctl(wl, t_max=2.5, radius=0.0)
+    g = _host(*_gpu(batch, wl.x0, k0, ctl))
+    o = _oracle(om, off, wl.x0, k0, ctl)
+    _compare_fixed_time(g, o, om, off, wl.x0, k0, ctl, 2.5)
+    ctl = _ctl(wl)
+    ref = _host(*_gpu(batch, wl.x0, k0, ctl, gf.GF_SCHED_PER_MEDIUM))
+    for tune in [None, (64, 1, 1, 1), (256, 2, 16, 7)]:
+        g = _host(*_gpu(batch, wl.x0, k0, ctl, gf.GF_SCHED_PERSISTENT, tune))
+        for k in ref:
+            assert np.array_equal(g[k], ref[k]), (tune, k)
+    _compare_exit(ref, om, off, wl.x0, k0, ctl, _oracle(om, off, wl.x0, k0, ctl))
+    gf.gf_batch_set_precision(batch, gf.GF_F64)
+    fresh = gf.gf_batch_create(media, off)
+    a, b = _host(*_gpu(batch, wl.x0, k0, ctl)), _host(*_gpu(fresh, wl.x0, k0, ctl))
+    for k in a:
+        assert np.array_equal(a[k], b[k])
+    with pytest.raises(gf.GfError, match="GF_F64"):
+        gf.gf_batch_set_precision(batch, gf.GF_F32)
+
+
 def test_full_batched_workload_sampled():
     """All 4096 media (~12.2M rays, log-uniform counts) in one persistent graph
     launch; 48 seeded sampled rays re-traced by the oracle."""
