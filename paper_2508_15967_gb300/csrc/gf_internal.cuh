@@ -161,6 +161,22 @@ __device__ __forceinline__ double recip_pos(double v)
     return fma(r, fma(e, e, e), r);
 }
 
+// 1/v of either sign in precision R: recip_pos on |v| for double (an FP64
+// division is ~10 FP64-pipe operations), the correctly rounded float reciprocal
+// for float.  v = 0 gives inf of v's sign; v NaN gives NaN.
+template <typename R>
+__device__ __forceinline__ R recip(R v);
+template <>
+__device__ __forceinline__ double recip<double>(double v)
+{
+    return copysign(recip_pos(fabs(v)), v);
+}
+template <>
+__device__ __forceinline__ float recip<float>(float v)
+{
+    return __frcp_rn(v);
+}
+
 // a < -40.5 for a double, decided on the bit pattern with integer compares
 // (for negative a, larger magnitude means a larger unsigned pattern; NaN with
 // the sign bit set also counts as negligible).  Same decision as the FP64
@@ -345,7 +361,7 @@ __device__ __forceinline__ void iso_index(const MediumParams &m, const R *__rest
 // Returns false (cut-off) where n^2 <= 0.  D is computed when WANT_D.
 template <typename R>
 struct Omega {
-    R w, inv_w, half_w;   // w, 1/w, w/2
+    R w, inv_w, half_w, inv_w2;   // w, 1/w, w/2, 1/w^2
 };
 
 template <typename R, int KIND, bool WANT_D>
@@ -513,7 +529,7 @@ __device__ __forceinline__ bool rhs_spline(const MediumParams &m, const Omega<R>
 template <typename R>
 __device__ __forceinline__ bool rhs_cold(const MediumParams &m, const Omega<R> &om, const R *y, R *f, R &D)
 {
-    const R w = om.w, w2 = w * w;
+    const R w = om.w, w2 = w * w, iw2 = om.inv_w2;
     const R fx = (R)m.prof[1], gx = (R)m.prof[3];
     const R fv = (R)m.prof[0] + fx * y[0], gv = (R)m.prof[2] + gx * y[0];
     R S = 1, Dst = 0, P = 1, Sx = 0, Dx = 0, Px = 0, Sw = 0, Dw = 0, Pw = 0;
@@ -522,19 +538,19 @@ __device__ __forceinline__ bool rhs_cold(const MediumParams &m, const Omega<R> &
         const R wp2 = wp * fv, wp2x = wp * fx;
         const R W = Om * gv, Wx = Om * gx;
         const R den = w2 - W * W;
-        const R iden = (R)1 / den;
+        const R iden = recip<R>(den);   // either sign: below or above the cyclotron resonance
         const R t = wp2 * iden;
         S -= t;
         Dst += W * t * om.inv_w;
-        P -= wp2 / w2;
+        P -= wp2 * iw2;
         Sx -= (wp2x + (R)2 * t * W * Wx) * iden;
         Dx += ((Wx * wp2 + W * wp2x) + (R)2 * W * W * t * Wx) * iden * om.inv_w;
-        Px -= wp2x / w2;
+        Px -= wp2x * iw2;
         Sw += (R)2 * w * t * iden;
         Dw -= W * t * ((R)3 * w2 - W * W) * iden * om.inv_w * om.inv_w;
-        Pw += (R)2 * wp2 / (w2 * w);
+        Pw += (R)2 * wp2 * iw2 * om.inv_w;
     }
-    const R a = (y[3] * y[3] + y[4] * y[4]) / w2, b = y[5] * y[5] / w2;
+    const R a = (y[3] * y[3] + y[4] * y[4]) * iw2, b = y[5] * y[5] * iw2;
     const R RL = S * S - Dst * Dst;
     D = S * a * (a + b) + P * b * (a + b) - RL * a - P * S * (a + (R)2 * b) + P * RL;
     const R DS = a * (a + b) - (R)2 * S * a - P * (a + (R)2 * b) + (R)2 * P * S;
@@ -544,8 +560,8 @@ __device__ __forceinline__ bool rhs_cold(const MediumParams &m, const Omega<R> &
     const R Db = S * a + P * (a + (R)2 * b) - (R)2 * P * S;
     const R Dom = -(R)2 * (Da * a + Db * b) * om.inv_w + DS * Sw + DD * Dw + DP * Pw;
     if (!(Dom != (R)0) || !isfinite(Dom)) return false;
-    const R inv = (R)1 / Dom;
-    const R ka = (R)2 * Da / w2, kb = (R)2 * Db / w2;
+    const R inv = recip<R>(Dom);
+    const R ka = (R)2 * Da * iw2, kb = (R)2 * Db * iw2;
     f[0] = -ka * y[3] * inv;
     f[1] = -ka * y[4] * inv;
     f[2] = -kb * y[5] * inv;
@@ -597,7 +613,7 @@ struct Rhs {
 template <typename R>
 __host__ __device__ inline Omega<R> make_omega(double w)
 {
-    return Omega<R>{(R)w, (R)(1.0 / w), (R)(0.5 * w)};
+    return Omega<R>{(R)w, (R)(1.0 / w), (R)(0.5 * w), (R)(1.0 / (w * w))};
 }
 
 }  // namespace gf
