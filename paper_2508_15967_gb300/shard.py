@@ -2,7 +2,8 @@
 
 Rays are independent (the paper's ensemble of independent problems, Sec. 5),
 so forward tracing needs no communication: each rank traces a contiguous
-sub-range, addressed in the C ABI by offset pointers with the full row stride.
+sub-range, addressed in the C ABI by offset pointers with the full row stride
+(a batch of media: contiguous media balanced on their ray counts).
 The adjoint's parameter gradient is a sum over rays, so the one exchange of
 the data-parallel backward is a sum of the per-rank gradients.
 """
@@ -19,6 +20,31 @@ def shard_bounds(n: int, rank: int, world: int) -> tuple[int, int]:
     q, r = divmod(n, world)
     lo = rank * q + min(rank, r)
     return lo, lo + q + (1 if rank < r else 0)
+
+
+def shard_media(offsets, rank: int, world: int) -> tuple[int, int]:
+    """Contiguous media [m_lo, m_hi) of a batch for `rank` of `world`, balanced
+    on ray counts: the cuts are the media at which the prefix sum of rays
+    (offsets, n_media + 1 non-decreasing entries) first reaches k total /
+    world, so every rank's ray count is within one medium's count of the
+    ideal.  Rank r traces rays [offsets[m_lo], offsets[m_hi])."""
+    import numpy as np
+    off = np.asarray(offsets, dtype=np.int64)
+    if off.ndim != 1 or off.size < 1 or off[0] != 0 or (np.diff(off) < 0).any():
+        raise ValueError("offsets must start at 0 and be non-decreasing")
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("need world >= 1 and 0 <= rank < world")
+    n_media, total = off.size - 1, int(off[-1])
+
+    def cut(k: int) -> int:
+        if k <= 0:
+            return 0
+        if k >= world:
+            return n_media
+        # first medium boundary whose prefix count reaches k total / world (exact integer test)
+        return int(np.searchsorted(off * world, k * total, side="left"))
+
+    return cut(rank), cut(rank + 1)
 
 
 def allreduce_gradient(grad: torch.Tensor, group=None) -> torch.Tensor:

@@ -1,7 +1,8 @@
 """Multi-process (world_size 2, gloo, CPU) checks of the data-parallel path:
 shards cover every ray once; the sum of per-shard adjoint gradients equals the
 single-process gradient (oracle tangent-linear sensitivities on each shard);
-the job time is the slowest rank's."""
+a batch of media sharded by ray counts traces, rank by rank, exactly what one
+process traces; the job time is the slowest rank's."""
 from __future__ import annotations
 
 import os
@@ -12,7 +13,7 @@ import pytest
 import torch
 import torch.multiprocessing as mp
 
-from paper_2508_15967_gb300.shard import allreduce_gradient, max_over_ranks, shard_bounds
+from paper_2508_15967_gb300.shard import allreduce_gradient, max_over_ranks, shard_bounds, shard_media
 
 
 def test_shard_bounds_partition():
@@ -67,3 +68,64 @@ def test_data_parallel_adjoint_gradient_gloo_world2():
         g, t = res[rank]
         np.testing.assert_allclose(g, full, rtol=1e-12, atol=1e-15)
         assert t == 1.5
+
+
+def test_shard_media_partition_and_balance():
+    from paper_2508_15967_gb300 import workloads as W
+    off = W.batched(n_media=4096).extra["offsets"]
+    counts = np.diff(off)
+    for world in (1, 2, 3, 4, 8):
+        spans = [shard_media(off, r, world) for r in range(world)]
+        assert spans[0][0] == 0 and spans[-1][1] == len(counts)
+        assert all(spans[i][1] == spans[i + 1][0] for i in range(world - 1))
+        rays = np.array([off[hi] - off[lo] for lo, hi in spans])
+        assert rays.sum() == off[-1]
+        assert np.abs(rays - off[-1] / world).max() <= counts.max()
+    assert [shard_media([0, 0, 0], r, 2) for r in range(2)] == [(0, 0), (0, 2)]   # no rays: still a partition
+    with pytest.raises(ValueError):
+        shard_media([0, 5, 3], 0, 2)
+
+
+def _batch_case():
+    from paper_2508_15967_gb300 import workloads as W
+    import oracle as O
+    wl = W.batched(n_media=10, scale_counts=1.0 / 512)
+    blobs, off = wl.extra["blobs"], wl.extra["offsets"]
+    om = [O.medium(kind="luneburg", blobs=blobs[j]) for j in range(len(off) - 1)]
+    k0 = np.empty_like(wl.x0)
+    for j in range(len(om)):
+        if off[j + 1] > off[j]:
+            k0[off[j]:off[j + 1]], _ = O.onshell(om[j], wl.x0[off[j]:off[j + 1]], wl.d[off[j]:off[j + 1]])
+    ctl = dict(rtol=1e-9, atol=1e-9, h0=1e-3, t_max=10.0, radius=1.5, max_steps=100000)
+    return wl, om, off, k0, ctl
+
+
+def _media_worker(rank, world, port, out):
+    import oracle as O
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    torch.distributed.init_process_group("gloo", rank=rank, world_size=world)
+    wl, om, off, k0, ctl = _batch_case()
+    m_lo, m_hi = shard_media(off, rank, world)
+    lo, hi = int(off[m_lo]), int(off[m_hi])
+    r = O.make_rays(wl.x0[lo:hi], k0[lo:hi])
+    O.trace_dopri5(om[m_lo:m_hi], np.asarray(off[m_lo:m_hi + 1]) - lo, r, 1.0, **ctl)
+    out[rank] = (lo, hi, r.y.copy(), r.steps.copy(), r.status.copy())
+    torch.distributed.destroy_process_group()
+
+
+def test_batched_media_shards_gloo_world2():
+    import oracle as O
+    world = 2
+    with mp.Manager() as mgr:
+        out = mgr.dict()
+        mp.spawn(_media_worker, args=(world, _free_port(), out), nprocs=world, join=True)
+        res = dict(out)
+    wl, om, off, k0, ctl = _batch_case()
+    r = O.make_rays(wl.x0, k0)
+    O.trace_dopri5(om, off, r, 1.0, **ctl)
+    spans = sorted(res[k][:2] for k in range(world))
+    assert spans[0][0] == 0 and spans[-1][1] == wl.n and spans[0][1] == spans[1][0]
+    for k in range(world):
+        lo, hi, y, steps, status = res[k]
+        assert np.array_equal(y, r.y[lo:hi]) and np.array_equal(steps, r.steps[lo:hi])
+        assert np.array_equal(status, r.status[lo:hi])
