@@ -32,7 +32,7 @@ constexpr double e1 = 35.0 / 384.0 - 5179.0 / 57600.0, e3 = 500.0 / 1113.0 - 757
 
 struct Ctl {
     double rtol, atol, h0, t_max, r2, fac_min, fac_max, safety;
-    float safety_f;
+    float safety_f, rtol_f, atol_f;
     int64_t max_steps, max_attempts;
     Omega<double> om;
 };
@@ -205,12 +205,14 @@ __device__ __forceinline__ void lane_attempt(Lane &L, const Slot &S, int stride,
     // is scaled and normed in FP32, as is the step factor: the controller is
     // a heuristic, and the FP32 norm differs from an FP64 one by ~1e-7
     // relative, which can only flip an accept decision for err within that of 1.
+    // Its float inputs are the bit-pattern truncations of e, y and Y (the
+    // hardware conversions run on the FP64 pipe).
     float err2 = 0.0f;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
         const double e = hs * (e1 * K1[i] + e3 * K3[i] + e4 * K4[i] + e5 * K5[i] + e6 * K6[i] + e7 * K7[i]);
-        const double sc = c.atol + c.rtol * fmax(fabs(y[i]), fabs(Y[i]));
-        const float q = (float)e / (float)sc;
+        const float sc = fmaf(c.rtol_f, fmaxf(fabsf(narrow_trunc(y[i])), fabsf(narrow_trunc(Y[i]))), c.atol_f);
+        const float q = narrow_trunc(e) / sc;
         err2 = fmaf(q, q, err2);
     }
     const float errf = sqrtf(err2 * (1.0f / 6.0f));
@@ -488,6 +490,8 @@ static Ctl ctl_of(const gf_step_ctl *c, double omega)
     k.fac_max = c->fac_max;
     k.safety = c->safety;
     k.safety_f = (float)c->safety;
+    k.rtol_f = (float)c->rtol;
+    k.atol_f = (float)c->atol;
     k.max_steps = c->max_steps;
     // rejections shrink h geometrically to h_min, so attempts are bounded; this
     // cap only guards against a controller that never converges
