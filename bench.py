@@ -476,8 +476,8 @@ def run_gpu(a):
             k_ev[1].record(stream)
 
     # measured FMA peaks (informational; the roofline peak is derived below)
-    peak64, _ = gf.gf_bench_fma_peak(gf.GF_F64, 1 << 15, 4)
-    peak32, _ = gf.gf_bench_fma_peak(gf.GF_F32, 1 << 18, 8)
+    fma64, _ = gf.gf_bench_fma_peak(gf.GF_F64, 1 << 15, 4)
+    fma32, _ = gf.gf_bench_fma_peak(gf.GF_F32, 1 << 18, 8)
 
     for _ in range(a.warmup):
         step()
@@ -576,7 +576,7 @@ def run_gpu(a):
                      "flops_per_launch": flops, "evaluations": evals, "blob_terms_live": live,
                      "blob_terms_total": evals * n_blobs,
                      "peak_basis": basis,
-                     "fma_peak_measured_tflops": {"f64": peak64, "f32": peak32}},
+                     "fma_peak_measured_tflops": {"f64": fma64, "f32": fma32}},
         "clocks": clk, "gpu_launches": 2 * a.steps, "e2e": e2e, "wall_s": wall,
     }
     if world == 1 and not a.no_extras:

@@ -50,7 +50,7 @@ typedef enum {
     GF_ERR_INVALID_ARG = 1,   /* a NULL required pointer, a bad size or value       */
     GF_ERR_CUDA = 2,          /* a CUDA runtime call failed (text in gf_last_error) */
     GF_ERR_OOM = 3,           /* device memory allocation failed                    */
-    GF_ERR_UNSUPPORTED = 4,   /* valid request this build does not provide          */
+    GF_ERR_UNSUPPORTED = 4,   /* valid request the library does not provide         */
     GF_ERR_TIMEOUT = 5        /* a bounded device-side wait gave up                 */
 } gf_status;
 
