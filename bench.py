@@ -156,21 +156,22 @@ def run_reference(a):
 
 # Algorithmic FP64 flops (add/mul 1, fma 2) of the fused RK4 kernel, per unit
 # of work; units are counted exactly by an untimed pass with work counters.
-#   live blob term  36: x - c (3), |x - c|^2 (5), exponent (1), table exp (18:
-#                       reduction 7, degree-5 polynomial 9, table fma 2),
-#                       A e, n^2 +=, 2 s A e (3), grad += (6)
+#   live blob term  26: x - c (3), |x - c|^2 (5), exponent (1), table exp (8: a
+#                       base-2 table exp at FP64 accuracy -- exact reduction 1,
+#                       degree-3 polynomial 5, table fma 2), A e, n^2 +=,
+#                       2 s A e (3), grad += (6)
 #   culled term      9: x - c, |x - c|^2 and the exponent, then skipped
 #   evaluation      51: GRIN base n^2 and gradient (8), 1/n^2 as 8, the two
 #                       prefactors (2), f (6), stage update and RK4 accumulate (24),
 #                       D at one evaluation in four (5/4 rounded up to 3)
 #   ray-step        18: final y + dt/6 (...) update
-FLOPS_LIVE_TERM, FLOPS_CULLED_TERM, FLOPS_EVAL, FLOPS_STEP = 36, 9, 51, 18
+FLOPS_LIVE_TERM, FLOPS_CULLED_TERM, FLOPS_EVAL, FLOPS_STEP = 26, 9, 51, 18
 
 # DRAM bytes (read + write) of one rk4_kernel<double, GRIN> launch over
 # 1,048,576 rays, from an ncu capture of the same launch shape (the kernel
 # loads and stores the ray state once, so the count does not depend on the
 # number of steps).  Valid only for the FP64 GRIN kernel as captured.
-TRAFFIC_BYTES_1M = 75_756_800 + 23_393_792
+TRAFFIC_BYTES_1M = 75_686_144 + 23_254_016
 
 
 def algorithmic_flops(evals: int, live: int, n_blobs: int, ray_steps: int) -> int:

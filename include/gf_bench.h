@@ -38,19 +38,20 @@ gf_status gf_bench_fma_peak(gf_precision prec, int64_t iters, int32_t blocks_per
 gf_status gf_bench_set_counters(unsigned long long *counters);
 
 /*
- * gf_bench_exp -- evaluate the library's table-driven exponential (used for
- * every Gaussian-blob term; defined for a <= 0, returning 0 for a <= -708)
- * and CUDA's exp on n device doubles `in`, writing out_lib and out_cuda (device,
- * n each), so that tests can bound its error.  Stream-ordered on `stream`.
- * Errors: GF_ERR_INVALID_ARG (n < 0, non-device pointers), GF_ERR_CUDA.
+ * gf_bench_exp -- evaluate the library's table-driven base-2 exponential 2^a
+ * (used for every Gaussian-blob term of the FP64 evaluator, whose rows carry
+ * the exponent in base 2; defined for a <= 0, returning 0 for a <= -1021)
+ * and CUDA's exp2 on n device doubles `in`, writing out_lib and out_cuda
+ * (device, n each), so that tests can bound its error.  Stream-ordered on
+ * `stream`.  Errors: GF_ERR_INVALID_ARG (n < 0, non-device pointers), GF_ERR_CUDA.
  */
 gf_status gf_bench_exp(const double *in, double *out_lib, double *out_cuda, int64_t n, void *stream);
 
 /*
- * gf_bench_exp_df -- evaluate the double-float exponential of the GF_F64X
- * blob evaluator (defined for -44 < a <= 0) on n device doubles (each first
- * split into a float pair), writing hi + lo as doubles to `out` (device).
- * Errors: GF_ERR_INVALID_ARG, GF_ERR_CUDA.
+ * gf_bench_exp_df -- evaluate the double-float base-2 exponential 2^a of the
+ * GF_F64X blob evaluator (defined for -63 < a <= 0) on n device doubles
+ * (each first split into a float pair), writing hi + lo as doubles to `out`
+ * (device).  Errors: GF_ERR_INVALID_ARG, GF_ERR_CUDA.
  */
 gf_status gf_bench_exp_df(const double *in, double *out, int64_t n, void *stream);
 

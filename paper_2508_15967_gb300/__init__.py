@@ -463,7 +463,7 @@ def gf_bench_set_counters(counters: torch.Tensor | None) -> None:
 
 
 def gf_bench_exp(a: torch.Tensor):
-    """(library exp, CUDA exp) of a float64 device tensor."""
+    """(library 2^a, CUDA exp2) of a float64 device tensor."""
     a = a.contiguous()
     o1, o2 = torch.empty_like(a), torch.empty_like(a)
     _check("gf_bench_exp", lib().gf_bench_exp(_ptr(a), _ptr(o1), _ptr(o2), a.numel(), _stream(None)))
@@ -471,7 +471,7 @@ def gf_bench_exp(a: torch.Tensor):
 
 
 def gf_bench_exp_df(a: torch.Tensor) -> torch.Tensor:
-    """Double-float exp of a float64 device tensor (hi + lo returned as float64)."""
+    """Double-float 2^a of a float64 device tensor (hi + lo returned as float64)."""
     a = a.contiguous()
     o = torch.empty_like(a)
     _check("gf_bench_exp_df", lib().gf_bench_exp_df(_ptr(a), _ptr(o), a.numel(), _stream(None)))

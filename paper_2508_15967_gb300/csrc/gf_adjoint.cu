@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kAdjBlock, 7) adjoint_kernel(
                     double n2, g[3];
                     base_index<KIND>(m, Y, n2, g);
                     // blob terms with the forward evaluator's arithmetic (scaled rows,
-                    // FP32 pre-test); negligible terms (see kBlobCull) are stored as G = 0
+                    // FP32 pre-test); negligible terms (see kBlobCull2) are stored as G = 0
                     double *Gs = S.G + ((int64_t)(s * 4 + st) * nb) * n + i;
                     const PreX px = pretest_point(m, Y);
                     int live = 0;

@@ -110,8 +110,9 @@ static void free_medium(gf_medium m)
     delete m;
 }
 
-// A_j in the plain rows and A_j, -2 sigma_j A_j in the scaled rows (double
-// and float).
+// A_j in the plain rows, A_j and -2 ln2 sigma_j A_j in the scaled rows
+// (double and float), and the (hi, lo) pairs of A_j and 2 s_j A_j in the
+// double-float rows.
 __global__ void set_amplitudes_kernel(double *b64, float *b32, const double *A, int nb)
 {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -120,13 +121,17 @@ __global__ void set_amplitudes_kernel(double *b64, float *b32, const double *A, 
         b64[kBlobStride * j] = a;
         double *sc = b64 + kBlobStride * (nb + j);
         sc[4] = a;
-        sc[5] = (-2.0 * sc[0]) * a;
+        sc[5] = (kNeg2Ln2 * sc[0]) * a;
         b32[kBlobStride * j + 4] = (float)sc[4];
         b32[kBlobStride * j + 5] = (float)sc[5];
-        float *dfr = b32 + (kBlobStride + 4) * nb + kDfRowFloats * j;   // A_hi, A_lo
+        float *dfr = b32 + (kBlobStride + 4) * nb + kDfRowFloats * j;   // A and 2 s A pairs
+        const double two_sa = (2.0 * b64[kBlobStride * j + 4]) * a;
         const float hi = __double2float_rn(a);
         dfr[8] = hi;
         dfr[9] = __double2float_rn(a - (double)hi);
+        const float hi2 = __double2float_rn(two_sa);
+        dfr[10] = hi2;
+        dfr[11] = __double2float_rn(two_sa - (double)hi2);
     }
 }
 
@@ -206,25 +211,26 @@ gf_status gf_medium_create(const gf_medium_desc *d, gf_medium *out)
             return GF_ERR_INVALID_ARG;
         }
         const double sj = -1.0 / (2.0 * w * w);
-        const double sig = std::sqrt(-sj);
-        if (!(sj < 0) || !std::isfinite(sj) || !(sig > 0) || !std::isfinite(-2.0 * sig * b[0])) {
+        // base-2 scale: A exp(s |x - c|^2) = A 2^(-|u|^2) with u = sig (x - c)
+        const double sig = std::sqrt(-sj * kInvLn2);
+        if (!(sj < 0) || !std::isfinite(sj) || !(sig > 0) || !std::isfinite(kNeg2Ln2 * sig * b[0])) {
             set_error("gf_medium_create: blob %d: width %g out of range", j, w);
             return GF_ERR_INVALID_ARG;
         }
         const double row[kBlobStride] = {b[0], b[1], b[2], b[3], sj, 2.0 * sj};
         const double srow[kBlobStride] = {sig, -(sig * b[1]), -(sig * b[2]), -(sig * b[3]), b[0],
-                                          (-2.0 * sig) * b[0]};
+                                          (kNeg2Ln2 * sig) * b[0]};
         for (int c = 0; c < kBlobStride; ++c) {
             t64[kBlobStride * j + c] = row[c];
             t64[kBlobStride * (nbl + j) + c] = srow[c];
             t32[kBlobStride * j + c] = (float)srow[c];
         }
         for (int c = 0; c < 4; ++c) t32[kBlobStride * nbl + 4 * j + c] = (float)srow[c];
-        // double-float row: c_hi[3], c_lo[3], s_hi, s_lo, A_hi, A_lo with hi = RN_float(v)
-        // and lo = RN_float(v - hi) (v - hi is exact in double)
+        // double-float row: c_hi[3], c_lo[3], then (hi, lo) of s/ln2, A and 2 s A, with
+        // hi = RN_float(v) and lo = RN_float(v - hi) (v - hi is exact in double)
         float *dfr = t32.data() + (kBlobStride + 4) * nbl + kDfRowFloats * j;
-        const double vals[5] = {b[1], b[2], b[3], sj, b[0]};
-        for (int c = 0; c < 5; ++c) {
+        const double vals[6] = {b[1], b[2], b[3], sj * kInvLn2, b[0], (2.0 * sj) * b[0]};
+        for (int c = 0; c < 6; ++c) {
             const float hi = (float)vals[c];
             const float lo = (float)(vals[c] - (double)hi);
             const int at = c < 3 ? c : 6 + 2 * (c - 3);

@@ -53,12 +53,12 @@ static gf_status run_peak(int64_t iters, int bps, double *tflops, double *ms)
 
 __global__ void dfexp_check_kernel(const double *in, double *out, int64_t n)
 {
-    __shared__ float sT[128];
+    __shared__ float sT[2 * kDfExpN];
     stage_dfexp_table(sT);
     __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    out[i] = df_to_double(df_exp(df_from_double(in[i]), sT));
+    out[i] = df_to_double(df_exp2(df_from_double(in[i]), sT));
 }
 
 __global__ void exp_check_kernel(const double *in, double *out_lib, double *out_cuda, int64_t n)
@@ -68,8 +68,8 @@ __global__ void exp_check_kernel(const double *in, double *out_lib, double *out_
     __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    out_lib[i] = exp_tang(in[i], sT);
-    out_cuda[i] = exp(in[i]);
+    out_lib[i] = exp2_tab(in[i], sT);
+    out_cuda[i] = exp2(in[i]);
 }
 
 __global__ void recip_check_kernel(const double *in, double *out_recip, float *out_narrow, int64_t n)

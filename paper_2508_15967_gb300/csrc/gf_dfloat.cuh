@@ -106,52 +106,49 @@ __device__ __forceinline__ dfl df_from_double(double x)
 
 __device__ __forceinline__ double df_to_double(dfl x) { return (double)x.hi + (double)x.lo; }
 
-// exp(a) for -44 < a <= 0 in double-float: Tang's table-driven method with
-// k = round(64 a / ln2), r = a - k ln2/64 (ln2/64 = L1 + L2 + L3 + L4 with
-// k Li exact for i <= 3), expm1(r) = r + r^2/2 + r^3/6 + r^4 (1/24 + r/120)
-// (the last group in float is enough: r^4/24 < 4e-11), result
-// 2^(k >> 6) (T_j + T_j expm1(r)) with T_j = 2^(j/64) as a float pair.
-// sT: the 128-float (hi, lo) table in shared memory.
-__device__ __forceinline__ dfl df_exp(dfl a, const float *__restrict__ sT)
+// 2^a for -63 < a <= 0 in double-float: Tang's table-driven method in base
+// 2 with a 2048-entry table, so that the reduction is exact.  k =
+// round(2048 a.hi) (adding 1.5 * 2^23 rounds 2048 a.hi to an integer), rh =
+// a.hi - k/2048 exact with |rh| <= 2^-12, r = rh + a.lo; then
+// 2^r - 1 = c1 r + c2 r^2 + c3 r^3 (truncation below (r ln2)^4/24 < 4e-17):
+// c1 rh in double-float, the small rest c1 a.lo + c2 r^2 + c3 r^3 (below
+// 3.5e-8 for |a| <= 1) in float; the result T (1 + p) with T = 2^(j/2048) a
+// float pair, summed with error-free transformations and renormalised, times
+// 2^(k >> 11).  Relative error about 2^-47 max(1, |a|) (a.lo enters through
+// one float product), median ~2^-50.  sT: the (hi, lo) table in shared memory.
+__device__ __forceinline__ dfl df_exp2(dfl a, const float *__restrict__ sT)
 {
-    const float kf = rintf(__fmul_rn(a.hi, kDfInvL));
-    const float t1 = __fmaf_rn(-kf, kDfL1, a.hi);                 // exact
-    dfl r = two_sum(t1, __fmul_rn(-kf, kDfL2));                   // exact product
-    r = df_add_f(r, a.lo);
-    r = df_add_f(r, __fmul_rn(-kf, kDfL3));                       // exact product
-    r = fast_two_sum(r.hi, __fmaf_rn(-kf, kDfL4, r.lo));
-    const dfl r2 = df_sqr(r);
-    const dfl r3 = df_mul(r2, r);
-    // no cancellation in the polynomial (|r^2/2| < 3e-3 |r|) or in T + T p
-    // (|p| < 6e-3): the sloppy double-word sum keeps its 2 u^2 error there
-    dfl p = df_add_sloppy(r, dfl{__fmul_rn(0.5f, r2.hi), __fmul_rn(0.5f, r2.lo)});
-    p = df_add_sloppy(p, df_mul(r3, dfl{kDfSixthHi, kDfSixthLo}));
-    const float r4 = __fmul_rn(r2.hi, r2.hi);
-    p = df_add_f(p, __fmul_rn(r4, __fmaf_rn(r.hi, 1.0f / 120.0f, 1.0f / 24.0f)));
-    const int k = (int)kf;
-    const int j = k & 63;
+    const float tf = __fmaf_rn(a.hi, 2048.0f, 12582912.0f);           // 1.5 * 2^23 + k
+    const int k = __float_as_int(tf) - 0x4B400000;                      // bits of 1.5 * 2^23
+    const float kf = __fsub_rn(tf, 12582912.0f);                        // exact
+    const float rh = __fmaf_rn(kf, -0x1p-11f, a.hi);                    // exact
+    const float rs = __fadd_rn(rh, a.lo);
+    const dfl P1 = df_mul_f(dfl{kDfC1Hi, kDfC1Lo}, rh);
+    const float small = __fmaf_rn(__fmul_rn(rs, rs), __fmaf_rn(rs, kDfC3, kDfC2), __fmul_rn(kDfC1Hi, a.lo));
+    const float plo = __fadd_rn(P1.lo, small);                          // p = P1.hi + plo
+    const int j = k & (kDfExpN - 1);
     const dfl T = {sT[2 * j], sT[2 * j + 1]};
-    const dfl G = df_add_sloppy(T, df_mul(T, p));
-    const float sc = __int_as_float((127 + (k >> 6)) << 23);      // 2^(k >> 6), k >> 6 >= -64
+    // T (1 + p) = T.hi + T.hi P1.hi + [T.lo + (T.lo P1.hi + T.hi plo + error of T.hi P1.hi)]
+    const dfl ph = two_prod(T.hi, P1.hi);
+    const float tl = __fmaf_rn(T.lo, P1.hi, __fmaf_rn(T.hi, plo, ph.lo));
+    const dfl s = fast_two_sum(T.hi, ph.hi);
+    const dfl u = two_sum(s.lo, T.lo);
+    const dfl v = fast_two_sum(s.hi, u.hi);
+    const dfl G = fast_two_sum(v.hi, __fadd_rn(v.lo, __fadd_rn(tl, u.lo)));
+    const float sc = __int_as_float((127 + (k >> 11)) << 23);           // 2^(k >> 11), k >> 11 >= -64
     return {__fmul_rn(G.hi, sc), __fmul_rn(G.lo, sc)};
 }
 
-static __constant__ float c_dfexp2_tab[128] = {
-#define GF_T8(i) kDfExp2Tab[i], kDfExp2Tab[i + 1], kDfExp2Tab[i + 2], kDfExp2Tab[i + 3], \
-                 kDfExp2Tab[i + 4], kDfExp2Tab[i + 5], kDfExp2Tab[i + 6], kDfExp2Tab[i + 7]
-    GF_T8(0),  GF_T8(8),  GF_T8(16), GF_T8(24), GF_T8(32), GF_T8(40), GF_T8(48), GF_T8(56),
-    GF_T8(64), GF_T8(72), GF_T8(80), GF_T8(88), GF_T8(96), GF_T8(104), GF_T8(112), GF_T8(120)
-#undef GF_T8
-};
+static __constant__ float c_dfexp2_tab[2 * kDfExpN] = {GF_DFEXP2_TAB_VALUES};
 
 __device__ __forceinline__ void stage_dfexp_table(float *sT)
 {
-    for (int j = threadIdx.x; j < 128; j += blockDim.x) sT[j] = c_dfexp2_tab[j];
+    for (int j = threadIdx.x; j < 2 * kDfExpN; j += blockDim.x) sT[j] = c_dfexp2_tab[j];
 }
 
-// Double-float blob row: c_hi[3], c_lo[3], s_hi, s_lo, A_hi, A_lo, each
-// value split exactly as hi = RN_float(v), lo = RN_float(v - hi) (2 s is
-// formed exactly by doubling s).  Built on the host with the medium.
+// Double-float blob row: c_hi[3], c_lo[3], then the pairs of s2 = s/ln2 (the
+// exponent in base 2), A and B = 2 s A, each value split exactly as
+// hi = RN_float(v), lo = RN_float(v - hi).  Built on the host with the medium.
 constexpr int kDfBlobStride = kDfRowFloats;
 
 __device__ __forceinline__ void stage_df_blobs(const MediumParams &m, float *sd)
@@ -162,9 +159,11 @@ __device__ __forceinline__ void stage_df_blobs(const MediumParams &m, float *sd)
 // Sum over blobs of A_j exp(s_j |x - c_j|^2) and of its gradient, in
 // double-float, added to n2 and g in double.  Field f of blob j is read from
 // sd[(kDfBlobStride j + f) * stride] (stride 1: a block-shared table; stride
-// = lanes: one table per lane).  Terms whose exponent is below -40.5 are
-// skipped (as in the FP64 evaluator); a float pre-test with margin removes
-// most of them before any double-float work.
+// = lanes: one table per lane).  Terms whose base-2 exponent s2 |x - c|^2 is
+// below -58.5 are skipped (as in the FP64 evaluator); a float pre-test with
+// a margin of 1 (kDfPreCull2) removes most of them before any double-float work.
+constexpr float kDfPreCull2 = 59.5f;
+
 __device__ __forceinline__ void blobs_df(const float *__restrict__ sd, int nb, const double *x, double &n2,
                                          double *g, const float *__restrict__ sT, int &live, int stride = 1)
 {
@@ -174,17 +173,17 @@ __device__ __forceinline__ void blobs_df(const float *__restrict__ sd, int nb, c
         const float *bp = sd + kDfBlobStride * j * stride;
         const auto b = [&](int f) { return bp[f * stride]; };   // read where used
         const float ex = X0.hi - b(0), ey = X1.hi - b(1), ez = X2.hi - b(2);
-        if ((ex * ex + ey * ey + ez * ez) * b(6) < -kBlobCullQF) continue;
+        if ((ex * ex + ey * ey + ez * ez) * b(6) < -kDfPreCull2) continue;
         const dfl d0 = df_add(X0, dfl{-b(0), -b(3)});
         const dfl d1 = df_add(X1, dfl{-b(1), -b(4)});
         const dfl d2 = df_add(X2, dfl{-b(2), -b(5)});
         const dfl q = df_add_sloppy(df_add_sloppy(df_sqr(d0), df_sqr(d1)), df_sqr(d2));   // no cancellation
-        const dfl s = {b(6), b(7)};
-        const dfl a = df_mul(s, q);
-        if (a.hi < (float)kBlobCull) continue;
-        const dfl AG = df_mul(dfl{b(8), b(9)}, df_exp(a, sT));
+        const dfl a = df_mul(dfl{b(6), b(7)}, q);
+        if (a.hi < (float)kBlobCull2) continue;
+        const dfl E = df_exp2(a, sT);
+        const dfl AG = df_mul(dfl{b(8), b(9)}, E);
         N = df_add_sloppy(N, AG);                                    // absolute error ~u^2 |N|, |AG|
-        const dfl c = df_mul(dfl{2.f * s.hi, 2.f * s.lo}, AG);      // 2 s A G
+        const dfl c = df_mul(dfl{b(10), b(11)}, E);                 // 2 s A G
         G0 = df_add_sloppy(G0, df_mul(c, d0));
         G1 = df_add_sloppy(G1, df_mul(c, d1));
         G2 = df_add_sloppy(G2, df_mul(c, d2));

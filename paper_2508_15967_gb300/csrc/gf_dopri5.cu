@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(128) dopri5_medium_kernel(const BatchView B, c
 {
     extern __shared__ double sm_dyn[];
     __shared__ double sT[DF ? 1 : kExpTabN];
-    __shared__ float sdT[DF ? 128 : 1];
+    __shared__ float sdT[DF ? 2 * kDfExpN : 1];
     const Tabs tb = stage_tables<DF>(sT, sdT);
     __syncthreads();
     const int stride = blockDim.x;
@@ -296,7 +296,7 @@ __global__ void dopri5_persistent_kernel(const BatchView B, const RaysView<doubl
 {
     extern __shared__ double sm_dyn[];
     __shared__ double sT[DF ? 1 : kExpTabN];
-    __shared__ float sdT[DF ? 128 : 1];
+    __shared__ float sdT[DF ? 2 * kDfExpN : 1];
     const Tabs tb = stage_tables<DF>(sT, sdT);
     __syncthreads();
     const int stride = blockDim.x * RPT;

@@ -18,10 +18,13 @@ enum : int { K_HOMOG = GF_MED_HOMOG, K_LUNEBURG = GF_MED_LUNEBURG, K_GRIN = GF_M
 // Device blob rows, 6 values each:
 //   plain  (adjoint sweep, double-float path): A, cx, cy, cz, s = -1 / (2 w^2), 2 s
 //   scaled (FP64 evaluator; a float copy for the FP32 evaluator):
-//          sigma, -sigma cx, -sigma cy, -sigma cz, A, -2 sigma A
-// with sigma = sqrt(-s), so that A exp(s |x - c|^2) = A exp(-|u|^2), u = sigma x - sigma c.
+//          sigma, -sigma cx, -sigma cy, -sigma cz, A, -2 ln2 sigma A
+// with sigma = sqrt(-s / ln2), so that A exp(s |x - c|^2) = A 2^(-|u|^2),
+// u = sigma x - sigma c, and grad (A 2^(-|u|^2)) = (-2 ln2 sigma A) 2^(-|u|^2) u.
 constexpr int kBlobStride = 6;
-constexpr int kDfRowFloats = 10;   // double-float blob row (GF_F64X), see gf_dfloat.cuh
+constexpr double kInvLn2 = 0x1.71547652b82fep+0;    // 1/ln2, rounded
+constexpr double kNeg2Ln2 = -0x1.62e42fefa39efp+0;  // -2 ln2, rounded
+constexpr int kDfRowFloats = 12;   // double-float blob row (GF_F64X), see gf_dfloat.cuh
 
 // Medium as the kernels see it (passed by value as a kernel argument).
 struct MediumParams {
@@ -106,32 +109,6 @@ __device__ __forceinline__ void stage_exp_table(double *sT)
     for (int j = threadIdx.x; j < kExpTabN; j += blockDim.x) sT[j] = g_exp2_tab[j];
 }
 
-// exp(a) for a <= 0 (finite or -inf; a <= -708 returns 0, below the smallest
-// normal double), table-driven after Tang (ACM TOMS 1989): with
-// k = round(2048 a / ln2), r = a - k ln2/2048 (Cody-Waite two-part ln2/2048),
-// |r| <= ln2/4096, exp(a) = 2^(k >> 11) * 2^((k & 2047)/2048) * (1 + expm1(r))
-// and expm1(r) = r + r^2 (1/2 + r/6) (truncation < r^4/24 < 3.5e-17).
-// Eight FP64 operations; the rounding to the integer k, the table index and
-// the power-of-two scaling are integer operations on the bit patterns.
-// Error against exp(a): < 0.5 ulp (table) + 0.5 ulp (last fma) + 0.16 ulp.
-__device__ __forceinline__ double exp_tang(double a, const double *__restrict__ T)
-{
-    const double shifter = 6755399441055744.0;   // 1.5 * 2^52: fma(a, c, shifter) rounds to integer
-    const double t = fma(a, kInvLn2xN, shifter);
-    const int k = __double2loint(t);
-    const double kd = t - shifter;
-    double r = fma(kd, -kLn2ByNHi, a);           // exact
-    r = fma(kd, -kLn2ByNLo, r);
-    const double c = fma(r, 1.0 / 6.0, 0.5);
-    const double p = fma(r * r, c, r);           // expm1(r)
-    const double Tj = T[k & (kExpTabN - 1)];
-    const double v = fma(Tj, p, Tj);
-    const int hi = __double2hiint(v) + ((k >> 11) << 20);
-    const unsigned ahi = (unsigned)__double2hiint(a);
-    // a <= -708 (sign set, |a| >= 708: hi word >= that of -708.0) flushes to 0
-    return ahi >= 0xC0862000u ? 0.0 : __hiloint2double(hi, __double2loint(v));
-}
-
 // x rounded toward zero to float, on the bit pattern with integer operations
 // (the FP64 pipe also executes the hardware conversion): exact sign, exponent
 // and leading 23 fraction bits for 2^-126 <= |x| < 2^128 (relative error
@@ -161,6 +138,68 @@ __device__ __forceinline__ double recip_pos(double v)
     return fma(r, fma(e, e, e), r);
 }
 
+// 2^a for a <= 0 (finite or -inf; a <= -1021 returns 0, below four times the
+// smallest normal double), table-driven after Tang (ACM TOMS 1989) in base 2,
+// where the argument reduction is exact: with k = round(2048 a) and
+// r = a - k/2048, 2^a = 2^(k >> 11) * 2^((k & 2047)/2048) * 2^r and
+// 2^r - 1 = r (c1 + r (c2 + r c3)), c_n = ln2^n / n! (truncation below
+// (r ln2)^4 / 24).  k is found in FP32 from a truncated to float (2048 |a| <
+// 2^22, so adding 1.5 * 2^23 rounds it to an integer); it may then be one off
+// the nearest integer, which leaves |r| <= 2^-12 + 2^-23 |a| (2.52e-4 for
+// |a| <= 64, 3.7e-4 up to 1021).  -k/2048 is exact in float and widened
+// to double on its bit pattern (zero widens to 2^-127, which moves r by far
+// less than an ulp of 2^a), and r = a + (-k/2048) is exact.  Five FP64
+// operations (r, the polynomial's three, the table product); the rest runs
+// on the FP32 and integer pipes, which the FP64-bound evaluator leaves idle.
+// Error against 2^a: table and final rounding 0.5 ulp each, truncation
+// below 3.9e-17 relative for |a| <= 64 (1.8e-16 up to 1021), i.e. under
+// 1.35 ulp (2.6 ulp); the blob terms only use -58.5 <= a <= 0.
+__device__ __forceinline__ double exp2_tab(double a, const double *__restrict__ T)
+{
+    const float af = narrow_trunc(a);
+    const float tf = fmaf(af, 2048.0f, 12582912.0f);            // 1.5 * 2^23 + k
+    const int k = __float_as_int(tf) - 0x4B400000;               // bits of 1.5 * 2^23
+    const unsigned wb = __float_as_uint(fmaf(tf, -0x1p-11f, 6144.0f));   // -k/2048 >= 0, exact
+    const double w = __hiloint2double((int)((wb >> 3) + ((1023u - 127u) << 20)), (int)(wb << 29));
+    const double r = a + w;
+    const double p = r * fma(r, fma(r, kExp2C3, kExp2C2), kExp2C1);     // 2^r - 1
+    const double Tj = T[k & (kExpTabN - 1)];
+    const double v = fma(Tj, p, Tj);
+    const int hi = __double2hiint(v) + ((k >> 11) << 20);
+    const unsigned ahi = (unsigned)__double2hiint(a);
+    // a <= -1021 (sign set, |a| >= 1021: hi word >= that of -1021.0), -inf and
+    // NaN with the sign bit set flush to 0
+    return ahi >= 0xC08FE800u ? 0.0 : __hiloint2double(hi, __double2loint(v));
+}
+
+// 2^a in FP32 with the hardware base-2 exponential (ex2.approx.ftz.f32:
+// relative error ~2^-22, subnormal results flushed to zero).
+__device__ __forceinline__ float exp2_fast(float a)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+
+// v > 0 (+inf included; NaN, zeros and negatives excluded).  For a double
+// the decision is an unsigned compare of the bit pattern, off the FP64 pipe.
+__device__ __forceinline__ bool positive(double v)
+{
+    return (unsigned long long)__double_as_longlong(v) - 1ull < 0x7FF0000000000000ull;
+}
+__device__ __forceinline__ bool positive(float v) { return v > 0.0f; }
+
+// fmax(m, |d|) for m >= 0 (NaN operands ignored as fmax ignores them); for a
+// double on the bit patterns (non-negative doubles order as their patterns).
+__device__ __forceinline__ double max_abs(double m, double d)
+{
+    const unsigned long long a = (unsigned long long)__double_as_longlong(d) & 0x7FFFFFFFFFFFFFFFull;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(m);
+    constexpr unsigned long long kInf = 0x7FF0000000000000ull;
+    return (a > b || b > kInf) && a <= kInf ? __longlong_as_double((long long)a) : m;
+}
+__device__ __forceinline__ float max_abs(float m, float d) { return fmaxf(m, fabsf(d)); }
+
 // 1/v of either sign in precision R: recip_pos on |v| for double (an FP64
 // division is ~10 FP64-pipe operations), the correctly rounded float reciprocal
 // for float.  v = 0 gives inf of v's sign; v NaN gives NaN.
@@ -177,13 +216,13 @@ __device__ __forceinline__ float recip<float>(float v)
     return __frcp_rn(v);
 }
 
-// a < -40.5 for a double, decided on the bit pattern with integer compares
-// (for negative a, larger magnitude means a larger unsigned pattern; NaN with
-// the sign bit set also counts as negligible).  Same decision as the FP64
-// comparison, without an FP64 instruction.
+// a < -58.5 (kBlobCull2) for a double, decided on the bit pattern with
+// integer compares (for negative a, larger magnitude means a larger unsigned
+// pattern; NaN with the sign bit set also counts as negligible).  Same
+// decision as the FP64 comparison, without an FP64 instruction.
 __device__ __forceinline__ bool below_cull(double a)
 {
-    return (unsigned long long)__double_as_longlong(a) > 0xC044400000000000ull;   // bits of -40.5
+    return (unsigned long long)__double_as_longlong(a) > 0xC04D400000000000ull;   // bits of -58.5
 }
 
 template <typename R>
@@ -202,20 +241,23 @@ __device__ __forceinline__ void stage_blobs(const MediumParams &m, R *sb)
     for (int j = threadIdx.x; j < m.n_blobs * kBlobStride; j += blockDim.x) sb[j] = src[j];
 }
 
-// Blob terms whose exponent s |x - c|^2 is below this are skipped: their
-// contribution A e^{-40.5} < 2.6e-18 |A| to n^2 (and < 3e-17 |A| / w to
-// grad n^2 for the widths in use) is far below the rounding of the sums.
-constexpr double kBlobCull = -40.5;
+// Blob terms whose exponent is below this are skipped.  The FP64, FP32 and
+// double-float evaluators' rows carry the exponent in base 2 (sigma =
+// 1/sqrt(2 w^2 ln2), s2 = s/ln2), so that a term is A 2^(-|u|^2): the
+// threshold 2^-58.5 = e^-40.55 leaves a contribution below 2.6e-18 |A| to
+// n^2 (and below 3e-17 |A| / w to grad n^2 for the widths in use), far below
+// the rounding of the sums.
+constexpr double kBlobCull2 = -58.5;
 // FP32 pre-test of the FP64 evaluator: a term whose |u|^2, computed in FP32
 // from x (truncated, relative error 2^-23) and rounded sigma, sigma c
-// (2^-24), exceeds 41 has an exact exponent below -40.5.  The error of each
+// (2^-24), exceeds 59 has an exact exponent below -58.5.  The error of each
 // u_i is below 6e-8 (3 sigma |x_i| + sigma |c_i| + |u_i|), that of |u|^2
-// (|u| < 6.5 near the threshold) below 22 times that; the host sets pre_lim so
-// that sigma (2 max|x_i| + max|c_i|) <= 1e5 for every blob, which keeps the
-// error below 0.2, under the 0.5 margin.  The FP64 test then
-// decides the remaining terms exactly as without the pre-test; rays beyond
-// pre_lim skip the pre-test.
-constexpr float kBlobCullQF = 41.0f;
+// (|u| < 7.7 near the threshold) below 27 times that; the host sets pre_lim
+// so that sigma (2 max|x_i| + max|c_i|) <= 1e5 for every blob, which keeps
+// the error below 0.2, under the 0.5 margin.  The FP64 test then decides the
+// remaining terms exactly as without the pre-test; rays beyond pre_lim skip
+// the pre-test.
+constexpr float kBlobCullQF2 = 59.0f;
 
 // Evaluation context: the shared exp table, the FP32 pre-test rows (FP64
 // path with a block-shared table only), the double-float tables (GF_F64X) and
@@ -254,17 +296,18 @@ __device__ __forceinline__ PreX pretest_point(const MediumParams &m, const doubl
 }
 
 // True if the blob whose pre-test row is bp (field f at bp[f * ps]) is
-// certainly negligible at p (see kBlobCullQF); p.on must hold.
+// certainly negligible at p (see kBlobCullQF2); p.on must hold.
 __device__ __forceinline__ bool pretest_negligible(const float *__restrict__ bp, int ps, const PreX &p)
 {
     const float v0 = fmaf(bp[0], p.x0, bp[ps]), v1 = fmaf(bp[0], p.x1, bp[2 * ps]), v2 = fmaf(bp[0], p.x2, bp[3 * ps]);
-    return v0 * v0 + v1 * v1 + v2 * v2 > kBlobCullQF;
+    return v0 * v0 + v1 * v1 + v2 * v2 > kBlobCullQF2;
 }
 
 // One Gaussian-blob term on a scaled row b (field f at b[f * stride]):
-// u = sigma x - sigma c, G = exp(-|u|^2) = exp(s |x - c|^2); for a term that is
-// not negligible (exponent >= -40.5) adds A G to n2 and (-2 sigma A) G u to g
-// and counts it in live.  Returns G, or 0 for a negligible term.
+// u = sigma x - sigma c with sigma = 1/sqrt(2 w^2 ln2), G = 2^(-|u|^2) =
+// exp(s |x - c|^2); for a term that is not negligible (exponent >= -58.5)
+// adds A G to n2 and (-2 ln2 sigma A) G u (= 2 s A G (x - c)) to g and counts
+// it in live.  Returns G, or 0 for a negligible term.
 __device__ __forceinline__ double blob_term_scaled(const double *__restrict__ b, int stride, const double *x,
                                                    double &n2, double *g, const double *__restrict__ T, int &live)
 {
@@ -273,7 +316,7 @@ __device__ __forceinline__ double blob_term_scaled(const double *__restrict__ b,
                  u2 = fma(sg, x[2], b[3 * stride]);
     const double a = fma(-u2, u2, fma(-u1, u1, -(u0 * u0)));
     if (below_cull(a)) return 0.0;
-    const double G = exp_tang(a, T);
+    const double G = exp2_tab(a, T);
     n2 = fma(b[4 * stride], G, n2);
     const double c = b[5 * stride] * G;
     g[0] = fma(c, u0, g[0]);
@@ -321,8 +364,8 @@ __device__ __forceinline__ void iso_index(const MediumParams &m, const R *__rest
         g[2] = (R)-2 * c * x[2];
     }
     if constexpr (sizeof(R) == 8) {
-        // scaled rows: u = sigma x - sigma c, G = exp(-|u|^2),
-        // n^2 += A G, grad n^2 += (-2 sigma A) G u   (19 FP64 operations per live term)
+        // scaled rows: u = sigma x - sigma c, G = 2^(-|u|^2),
+        // n^2 += A G, grad n^2 += (-2 ln2 sigma A) G u   (16 FP64 operations per live term)
         PreX px = {0.f, 0.f, 0.f, false};
         if (cx.pre != nullptr) px = pretest_point(m, x);
 #pragma unroll 2
@@ -331,8 +374,9 @@ __device__ __forceinline__ void iso_index(const MediumParams &m, const R *__rest
             blob_term_scaled(sb + kBlobStride * j * stride, stride, x, n2, g, cx.T, cx.live);
         }
     } else {
-        // the same scaled form in FP32 with the fast exponential (__expf,
-        // relative error below 1e-5 down to the culling threshold).  Near a
+        // the same scaled form in FP32 with the hardware base-2 exponential
+        // (relative error ~2^-22; the FP32 rounding of |u|^2 adds up to
+        // 58.5 ln2 2^-24 ~ 2.4e-6 near the culling threshold).  Near a
         // blob centre u = sigma x - sigma c loses ~ulp(sigma x) to cancellation,
         // a relative error of ~4e-6 in G there: below one float ulp of n^2 for
         // the amplitudes in use, far inside the FP32 gate.
@@ -343,8 +387,8 @@ __device__ __forceinline__ void iso_index(const MediumParams &m, const R *__rest
             const float u0 = fmaf(sg, x[0], b[stride]), u1 = fmaf(sg, x[1], b[2 * stride]),
                         u2 = fmaf(sg, x[2], b[3 * stride]);
             const float a = fmaf(-u2, u2, fmaf(-u1, u1, -(u0 * u0)));
-            if (a >= (float)kBlobCull) {
-                const float G = __expf(a);
+            if (a >= (float)kBlobCull2) {
+                const float G = exp2_fast(a);
                 n2 = fmaf(b[4 * stride], G, n2);
                 const float c = b[5 * stride] * G;
                 g[0] = fmaf(c, u0, g[0]);
@@ -372,7 +416,7 @@ __device__ __forceinline__ bool rhs_iso(const MediumParams &m, const R *__restri
     R n2, g[3];
     iso_index<R, KIND>(m, sb, nb, y, n2, g, cx, stride);
     if constexpr (WANT_D) D = y[3] * y[3] + y[4] * y[4] + y[5] * y[5] - om.w * om.w * n2;
-    if (!(n2 > (R)0)) return false;
+    if (!positive(n2)) return false;
     R inv;
     if constexpr (sizeof(R) == 8)
         inv = recip_pos(n2);

@@ -52,6 +52,15 @@ __device__ __forceinline__ bool finite6(const R *y)
     for (int c = 0; c < 6; ++c) ok = ok && isfinite(y[c]);
     return ok;
 }
+// Doubles: exponent field not all ones, tested on the high words (integer pipe).
+template <>
+__device__ __forceinline__ bool finite6<double>(const double *y)
+{
+    unsigned bad = 0u;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) bad |= (~(unsigned)__double2hiint(y[c]) & 0x7ff00000u) ? 0u : 1u;
+    return bad == 0u;
+}
 
 // State update y <- y + inc.  FP64: plain add.  FP32: Kahan-compensated
 // (Kahan 1965) so that 10^4 small increments to |x| ~ 1 do not drift.
@@ -119,7 +128,7 @@ rk4_kernel(const MediumParams m, const RaysView<R> r, const Omega<R> om, const R
     __shared__ double sT[kBlobs64 ? kExpTabN : 1];
     __shared__ float sp[kBlobs64 ? 4 * GF_MAX_BLOBS : 1];
     __shared__ float sdf[DF ? kDfBlobStride * GF_MAX_BLOBS : 1];
-    __shared__ float sdT[DF ? 128 : 1];
+    __shared__ float sdT[DF ? 2 * kDfExpN : 1];
     if constexpr (KIND != K_SPLINE && !DF) stage_blobs<R>(m, sb);
     if constexpr (kBlobs64) {
         stage_pretest(m, sp);
@@ -162,7 +171,7 @@ rk4_kernel(const MediumParams m, const RaysView<R> r, const Omega<R> om, const R
             R K[6], acc[6], Y[6], D;
             evals += 4;
             bool ok = f.template eval<true>(y, K, D, cx);
-            dm = fmax(dm, fabs(D));
+            dm = max_abs(dm, D);
             if (!ok) { st = GF_RAY_CUTOFF; break; }
 #pragma unroll
             for (int c = 0; c < 6; ++c) { acc[c] = K[c]; Y[c] = y[c] + h2 * K[c]; }
@@ -189,7 +198,7 @@ rk4_kernel(const MediumParams m, const RaysView<R> r, const Omega<R> om, const R
         R K[6], D;
         f.template eval<true>(y, K, D, cx);
         ++evals;
-        dm = fmax(dm, fabs(D));
+        dm = max_abs(dm, D);
         if (r.d_res) r.d_res[i] = (double)fabs(D);
         if (r.d_max) r.d_max[i] = (double)dm;
 #pragma unroll
