@@ -168,7 +168,9 @@ __global__ void __launch_bounds__(kAdjBlock, 7) adjoint_kernel(
                     const double *Gs = S.G + ((int64_t)(s * 4 + st) * nb) * n + i;
                     for (int j = 0; j < nb; ++j) {
                         const double G = Gs[(int64_t)j * n];
-                        if (G == 0.0) continue;   // negligible term: no contribution
+                        // negligible term (stored as +0): no contribution; tested on the
+                        // bit pattern, since an FP64 compare would occupy the FP64 pipe
+                        if (__double_as_longlong(G) == 0ll) continue;
                         const double *b = sb + kBlobStride * j;
                         const double dx = Y[0] - b[1], dy = Y[1] - b[2], dz = Y[2] - b[3];
                         const double dK = dx * Kb[3] + dy * Kb[4] + dz * Kb[5];

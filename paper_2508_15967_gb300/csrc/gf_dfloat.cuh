@@ -97,14 +97,34 @@ __device__ __forceinline__ dfl df_sqr(dfl x)
     return fast_two_sum(p, e);
 }
 
-// exact double -> (hi, lo) split; the remainder x - hi is exact in double
-__device__ __forceinline__ dfl df_from_double(double x)
+// The conversions between double and float run on the FP64 pipe, which the
+// rest of the ray step keeps busy; these do them on the bit patterns with
+// integer operations instead.
+
+// x rounded to the nearest float (ties to even, as the hardware conversion)
+// for 2^-126 <= |x| < 2^128 - 2^103; smaller |x| gives a zero of x's sign,
+// larger |x|, inf and NaN give inf.
+__device__ __forceinline__ float narrow_rn(double x)
 {
-    const float hi = __double2float_rn(x);
-    return {hi, __double2float_rn(x - (double)hi)};
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned mag = hi & 0x7fffffffu;
+    unsigned f = ((mag - ((1023u - 127u) << 20)) << 3) | (lo >> 29);
+    const unsigned drop = lo & 0x1fffffffu;   // the 29 bits below the float's last place
+    f += (drop > 0x10000000u || (drop == 0x10000000u && (f & 1u))) ? 1u : 0u;   // carries into the exponent
+    f = mag < ((1023u - 126u) << 20) ? 0u : (mag >= ((1023u + 128u) << 20) ? 0x7f800000u : f);
+    return __uint_as_float((hi & 0x80000000u) | f);
 }
 
-__device__ __forceinline__ double df_to_double(dfl x) { return (double)x.hi + (double)x.lo; }
+// double -> (hi, lo): hi = x rounded to float, lo = the exact remainder
+// x - hi rounded to float (one FP64 subtraction); ~2^-48 relative for
+// 2^-126 <= |x| < 2^128 (positions and directions of rays).
+__device__ __forceinline__ dfl df_from_double(double x)
+{
+    const float hi = narrow_rn(x);
+    return {hi, narrow_rn(x - widen(hi))};
+}
+
+__device__ __forceinline__ double df_to_double(dfl x) { return widen(x.hi) + widen(x.lo); }
 
 // 2^a for -63 < a <= 0 in double-float: Tang's table-driven method in base
 // 2 with a 2048-entry table, so that the reduction is exact.  k =
@@ -208,8 +228,8 @@ __device__ __forceinline__ bool rhs_df(const MediumParams &m, const float *__res
     iso_index<double, KIND>(m, nullptr, 0, y, n2, g, base);
     blobs_df(sd, nb, y, n2, g, dT, live, stride);
     if constexpr (WANT_D) D = y[3] * y[3] + y[4] * y[4] + y[5] * y[5] - om.w * om.w * n2;
-    if (!(n2 > 0.0)) return false;
-    const double inv = 1.0 / n2;
+    if (!positive(n2)) return false;
+    const double inv = recip_pos(n2);
     const double a = inv * om.inv_w, b = om.half_w * inv;
     f[0] = a * y[3];
     f[1] = a * y[4];

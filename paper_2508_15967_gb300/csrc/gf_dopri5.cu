@@ -199,7 +199,7 @@ __device__ __forceinline__ void lane_attempt(Lane &L, const Slot &S, int stride,
     if (!f.template eval<true>(Y, K7, D)) { L.status = GF_RAY_CUTOFF; return; }
     bool fin = true;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) fin = fin && isfinite(Y[i]) && isfinite(K7[i]);
+    for (int i = 0; i < 6; ++i) fin = fin && finite_bits(Y[i]) && finite_bits(K7[i]);
     if (!fin) { L.status = GF_RAY_NONFINITE; return; }
     // The embedded error estimate e (FP64: a small difference of O(1) terms)
     // is scaled and normed in FP32, as is the step factor: the controller is
@@ -216,9 +216,8 @@ __device__ __forceinline__ void lane_attempt(Lane &L, const Slot &S, int stride,
         err2 = fmaf(q, q, err2);
     }
     const float errf = sqrtf(err2 * (1.0f / 6.0f));
-    const double err = errf;
-    const double fac = errf > 0.0f ? (double)(c.safety_f * powf(errf, -0.2f)) : L.fmax;
-    if (err <= 1.0) {
+    const double fac = errf > 0.0f ? widen(c.safety_f * powf(errf, -0.2f)) : L.fmax;
+    if (errf <= 1.0f) {
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
             L.y[i] = Y[i];
@@ -226,7 +225,7 @@ __device__ __forceinline__ void lane_attempt(Lane &L, const Slot &S, int stride,
         }
         L.t = last ? c.t_max : L.t + hs;
         ++L.steps;
-        L.dm = fmax(L.dm, fabs(D));
+        L.dm = max_abs(L.dm, D);
         L.h = hs * fmin(L.fmax, fmax(c.fac_min, fac));
         L.fmax = c.fac_max;
         if (c.r2 > 0.0 && Y[0] * Y[0] + Y[1] * Y[1] + Y[2] * Y[2] > c.r2) L.status = GF_RAY_EXITED;

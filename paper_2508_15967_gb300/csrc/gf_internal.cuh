@@ -122,6 +122,18 @@ __device__ __forceinline__ float narrow_trunc(double x)
     return __uint_as_float((hi & 0x80000000u) | f);
 }
 
+// v as a double, on the bit pattern with integer operations (the hardware
+// conversion runs on the FP64 pipe): exact for zeros, normal floats, inf and NaN; subnormal
+// floats (below 1.2e-38) become a zero of their sign.
+__device__ __forceinline__ double widen(float v)
+{
+    const unsigned b = __float_as_uint(v);
+    const unsigned mag = b & 0x7fffffffu, sign = b & 0x80000000u;
+    const unsigned adj = mag >= 0x7f800000u ? (2047u - 255u) << 20 : (1023u - 127u) << 20;
+    const bool tiny = mag < 0x00800000u;
+    return __hiloint2double((int)(tiny ? sign : sign | ((mag >> 3) + adj)), tiny ? 0 : (int)(b << 29));
+}
+
 // 1/v for v > 0: the FP32 reciprocal of v's leading 24 bits, widened on the
 // bit pattern, is a seed r with relative error |d| < 2^-22; one Newton step
 // of cubic order, r (1 + e + e^2) with e = 1 - v r, leaves |d|^3 < 2^-66
@@ -179,6 +191,12 @@ __device__ __forceinline__ float exp2_fast(float a)
     float r;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
     return r;
+}
+
+// True if v is neither infinite nor NaN, tested on the high word (integer pipe).
+__device__ __forceinline__ bool finite_bits(double v)
+{
+    return (~(unsigned)__double2hiint(v) & 0x7ff00000u) != 0u;
 }
 
 // v > 0 (+inf included; NaN, zeros and negatives excluded).  For a double

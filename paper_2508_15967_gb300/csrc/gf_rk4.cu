@@ -58,7 +58,7 @@ __device__ __forceinline__ bool finite6<double>(const double *y)
 {
     unsigned bad = 0u;
 #pragma unroll
-    for (int c = 0; c < 6; ++c) bad |= (~(unsigned)__double2hiint(y[c]) & 0x7ff00000u) ? 0u : 1u;
+    for (int c = 0; c < 6; ++c) bad |= finite_bits(y[c]) ? 0u : 1u;
     return bad == 0u;
 }
 
