@@ -239,7 +239,7 @@ gf_status gf_trace_rk4(gf_medium m, gf_precision prec, const gf_rays *rays, doub
  * with y = (x0, x1, x2, k0, k1, k2) and out[0..7] = (D, D_x0, D_x1, D_x2,
  * D_k0, D_k1, D_k2, D_w) (the symbolic front end writes it).  The source may
  * call double gf_exp(double), the library's table-driven exponential (error
- * < 1.16 ulp for |a| < 708, CUDA's exp outside).  It is compiled
+ * < 1.35 ulp for |a| < 708, CUDA's exp outside).  It is compiled
  * with NVRTC (loaded on first use) for the current device (sm_103a on GB300)
  * together with the library's RK4 kernel; the right-hand side is the generic
  * f = (-D_k / D_w, D_x / D_w) and a ray stops with GF_RAY_CUTOFF where D_w = 0

@@ -20,11 +20,13 @@
 
 namespace gf {
 
-// Table-driven exponential available to generated code as gf_exp(a): the
-// library's method (Tang's 2^(j/2048) table, staged in shared memory by the
-// kernel below, Cody-Waite reduction, degree-3 polynomial, < 1.16 ulp) for
-// |a| < 708, CUDA's exp outside (overflow, underflow, inf, NaN).  The table
-// and constants are printed into the source as exact hex literals.
+// Table-driven exponential available to generated code as gf_exp(a) of a
+// natural-base argument of either sign: Tang's method with the library's
+// 2^(j/2048) table (staged in shared memory by the kernel below), a
+// Cody-Waite two-part reduction by ln2/2048 and a degree-3 polynomial,
+// < 1.35 ulp, for |a| < 708; CUDA's exp outside (overflow, underflow, inf,
+// NaN).  The table and constants are printed into the source as exact hex
+// literals.
 static const char *kJitExp = R"JIT(
 __shared__ double gf_T[2048];
 __device__ __forceinline__ double gf_exp(double a)
