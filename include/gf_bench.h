@@ -65,6 +65,27 @@ gf_status gf_bench_exp_df(const double *in, double *out, int64_t n, void *stream
  */
 gf_status gf_bench_recip(const double *in, double *out_recip, float *out_narrow, int64_t n, void *stream);
 
+/*
+ * gf_fault_inject -- failure testing without a device fault (the paper has no
+ * counterpart).  After gf_fault_inject(n) with n >= 1, the n-th CUDA call that
+ * the library checks from then on (allocations, copies, launches, graph
+ * capture and instantiation, pointer queries), counted across all entry
+ * points and threads, reports GF_ERR_CUDA with a message containing
+ * "injected fault", although the call itself ran and succeeded; its entry
+ * point then takes its ordinary error path, which must release what it took
+ * and leave every object and stream usable.  Fires once; n <= 0 disarms.
+ * Host only: nothing is enqueued and the device is not touched.  Always GF_OK.
+ */
+gf_status gf_fault_inject(int64_t n);
+
+/*
+ * gf_bench_live_allocations -- the number of device allocations the library
+ * holds now (media, batches and their caches, scratch of calls in progress);
+ * their total size in bytes is written to *bytes when bytes is not NULL.
+ * Host only.  Never fails.
+ */
+int64_t gf_bench_live_allocations(size_t *bytes);
+
 #ifdef __cplusplus
 }
 #endif

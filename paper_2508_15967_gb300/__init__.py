@@ -89,6 +89,8 @@ def lib() -> C.CDLL:
             "gf_bench_exp": ([P, P, P, I64, P], I32),
             "gf_bench_exp_df": ([P, P, I64, P], I32),
             "gf_bench_recip": ([P, P, P, I64, P], I32),
+            "gf_fault_inject": ([I64], I32),
+            "gf_bench_live_allocations": ([P], I64),
             "gf_adjoint_scratch_bytes": ([P, I64, I64], C.c_size_t),
             "gf_trace_adjoint": ([P, I64, D, D, I64, I64, P, P, P, I64, P, P, P, C.c_size_t, P], I32),
             "gf_trace_adjoint_static": ([P, I64, D, D, I64, I64, P, P, P, I64, P, P, P], I32),
@@ -485,6 +487,19 @@ def gf_bench_recip(a: torch.Tensor):
     o2 = torch.empty(a.shape, dtype=torch.float32, device=a.device)
     _check("gf_bench_recip", lib().gf_bench_recip(_ptr(a), _ptr(o1), _ptr(o2), a.numel(), _stream(None)))
     return o1, o2
+
+
+def gf_fault_inject(n: int) -> None:
+    """Make the n-th CUDA call the library checks from now on report an
+    injected failure (n <= 0 disarms); see gf_bench.h."""
+    _check("gf_fault_inject", lib().gf_fault_inject(int(n)))
+
+
+def gf_bench_live_allocations() -> tuple[int, int]:
+    """(number, total bytes) of the device allocations the library holds."""
+    nbytes = C.c_size_t(0)
+    n = lib().gf_bench_live_allocations(C.byref(nbytes))
+    return int(n), int(nbytes.value)
 
 
 def medium_from_workload(spec: dict) -> Medium:

@@ -2,10 +2,13 @@
 // reporting, argument validation, medium objects and the RK4 / on-shell
 // entry points.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
+#include <unordered_map>
 #include <vector>
 
 #include "gf_internal.cuh"
@@ -24,12 +27,57 @@ void set_error(const char *fmt, ...)
     g_err = buf;
 }
 
+// Fault injection (gf_fault_inject): the number of further successful checked
+// CUDA calls after which one reports a failure; 0 = disarmed.
+static std::atomic<long long> g_inject{0};
+
 gf_status cuda_status(cudaError_t e, const char *what)
 {
-    if (e == cudaSuccess) return GF_OK;
+    if (e == cudaSuccess) {
+        long long n = g_inject.load();
+        while (n > 0 && !g_inject.compare_exchange_weak(n, n - 1)) {
+        }
+        if (n == 1) {
+            set_error("%s: injected fault (gf_fault_inject)", what);
+            return GF_ERR_CUDA;
+        }
+        return GF_OK;
+    }
     set_error("%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
     if (e == cudaErrorMemoryAllocation) return GF_ERR_OOM;
     return GF_ERR_CUDA;
+}
+
+// Device allocations of the library, with their sizes: every allocation the
+// library makes goes through dev_alloc / dev_free, so that tests can check
+// that error paths release what they took (gf_bench_live_allocations).
+static std::mutex g_alloc_mutex;
+static std::unordered_map<void *, size_t> g_allocs;
+static size_t g_alloc_bytes = 0;
+
+cudaError_t dev_alloc(void **p, size_t bytes)
+{
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) {
+        std::lock_guard<std::mutex> lock(g_alloc_mutex);
+        g_allocs[*p] = bytes;
+        g_alloc_bytes += bytes;
+    }
+    return e;
+}
+
+void dev_free(void *p)
+{
+    if (p == nullptr) return;
+    {
+        std::lock_guard<std::mutex> lock(g_alloc_mutex);
+        auto it = g_allocs.find(p);
+        if (it != g_allocs.end()) {
+            g_alloc_bytes -= it->second;
+            g_allocs.erase(it);
+        }
+    }
+    cudaFree(p);
 }
 
 // A pointer the kernels may dereference: device or managed memory, on any
@@ -103,9 +151,9 @@ static gf_status check_medium(gf_medium m)
 
 static void free_medium(gf_medium m)
 {
-    if (m->d_blobs64) cudaFree(m->d_blobs64);
-    if (m->d_blobs32) cudaFree(m->d_blobs32);
-    if (m->d_grid) cudaFree(m->d_grid);
+    dev_free(m->d_blobs64);
+    dev_free(m->d_blobs32);
+    dev_free(m->d_grid);
     if (m->jit_lib) cudaLibraryUnload(m->jit_lib);
     delete m;
 }
@@ -144,6 +192,19 @@ extern "C" {
 const char *gf_last_error(void) { return g_err.c_str(); }
 
 int32_t gf_version(void) { return 100; }
+
+gf_status gf_fault_inject(int64_t n)
+{
+    g_inject.store(n > 0 ? (long long)n : 0);
+    return GF_OK;
+}
+
+int64_t gf_bench_live_allocations(size_t *bytes)
+{
+    std::lock_guard<std::mutex> lock(g_alloc_mutex);
+    if (bytes != nullptr) *bytes = g_alloc_bytes;
+    return (int64_t)g_allocs.size();
+}
 
 gf_status gf_medium_create(const gf_medium_desc *d, gf_medium *out)
 {
@@ -261,8 +322,8 @@ gf_status gf_medium_create(const gf_medium_desc *d, gf_medium *out)
     for (int i = 0; i < 4; ++i) p.prof[i] = d->kind == GF_MED_COLD ? d->profile[i] : 0.0;
     gf_status s = GF_OK;
     const size_t n64 = std::max<size_t>(t64.size(), 1), n32 = std::max<size_t>(t32.size(), 1);
-    if ((s = cuda_status(cudaMalloc(&m->d_blobs64, n64 * sizeof(double)), "cudaMalloc(blobs)")) != GF_OK ||
-        (s = cuda_status(cudaMalloc(&m->d_blobs32, n32 * sizeof(float)), "cudaMalloc(blobs)")) != GF_OK) {
+    if ((s = cuda_status(dev_alloc(&m->d_blobs64, n64 * sizeof(double)), "cudaMalloc(blobs)")) != GF_OK ||
+        (s = cuda_status(dev_alloc(&m->d_blobs32, n32 * sizeof(float)), "cudaMalloc(blobs)")) != GF_OK) {
         free_medium(m);
         return s;
     }
@@ -300,7 +361,7 @@ gf_status gf_medium_create(const gf_medium_desc *d, gf_medium *out)
                 if (std::fpclassify(v) == FP_SUBNORMAL) v = std::copysign(0.0f, v);
         }
         const float *src = subnormal ? flushed.data() : d->grid;
-        if ((s = cuda_status(cudaMalloc(&m->d_grid, nodes * 8 * sizeof(float)), "cudaMalloc(grid)")) != GF_OK ||
+        if ((s = cuda_status(dev_alloc(&m->d_grid, nodes * 8 * sizeof(float)), "cudaMalloc(grid)")) != GF_OK ||
             (s = cuda_status(cudaMemcpy(m->d_grid, src, nodes * 8 * sizeof(float),
                                         cudaMemcpyHostToDevice), "cudaMemcpy(grid)")) != GF_OK) {
             free_medium(m);

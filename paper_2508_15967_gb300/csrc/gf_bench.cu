@@ -30,7 +30,7 @@ static gf_status run_peak(int64_t iters, int bps, double *tflops, double *ms)
     const int blocks = sms * bps;
     R *out = nullptr;
     gf_status s;
-    if ((s = cuda_status(cudaMalloc(&out, sizeof(R) * blocks), "cudaMalloc")) != GF_OK) return s;
+    if ((s = cuda_status(dev_alloc(&out, sizeof(R) * blocks), "cudaMalloc")) != GF_OK) return s;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -43,7 +43,7 @@ static gf_status run_peak(int64_t iters, int bps, double *tflops, double *ms)
     cudaEventElapsedTime(&t, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(out);
+    dev_free(out);
     if ((s = cuda_status(err == cudaSuccess ? cudaGetLastError() : err, "fma_peak_kernel")) != GF_OK)
         return s;
     *ms = t;

@@ -397,16 +397,16 @@ const double *medium_device_blobs(gf_medium m);
 
 static void batch_free(gf_batch b)
 {
-    cudaFree(b->d_blobs);
-    cudaFree(b->d_pre);
-    cudaFree(b->d_pre_lim);
-    cudaFree(b->d_df);
-    cudaFree(b->d_base);
-    cudaFree(b->d_nb);
-    cudaFree(b->d_head);
-    cudaFree(b->d_item_medium);
-    cudaFree(b->d_item_begin);
-    cudaFree(b->d_item_end);
+    dev_free(b->d_blobs);
+    dev_free(b->d_pre);
+    dev_free(b->d_pre_lim);
+    dev_free(b->d_df);
+    dev_free(b->d_base);
+    dev_free(b->d_nb);
+    dev_free(b->d_head);
+    dev_free(b->d_item_medium);
+    dev_free(b->d_item_begin);
+    dev_free(b->d_item_end);
     for (auto &g : b->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     if (b->capture) cudaStreamDestroy(b->capture);
@@ -424,16 +424,18 @@ static gf_status build_items(gf_batch b, int chunk)
             beg.push_back(lo);
             end.push_back(std::min(lo + chunk, b->offsets[m + 1]));
         }
-    cudaFree(b->d_item_medium);
-    cudaFree(b->d_item_begin);
-    cudaFree(b->d_item_end);
+    dev_free(b->d_item_medium);
+    dev_free(b->d_item_begin);
+    dev_free(b->d_item_end);
     b->d_item_medium = nullptr;
     b->d_item_begin = b->d_item_end = nullptr;
+    b->chunk = 0;   // no valid item list until this build completes
+    b->n_items = 0;
     size_t n = std::max<size_t>(med.size(), 1);
     gf_status s;
-    if ((s = cuda_status(cudaMalloc(&b->d_item_medium, n * sizeof(int32_t)), "cudaMalloc(items)")) != GF_OK ||
-        (s = cuda_status(cudaMalloc(&b->d_item_begin, n * sizeof(int64_t)), "cudaMalloc(items)")) != GF_OK ||
-        (s = cuda_status(cudaMalloc(&b->d_item_end, n * sizeof(int64_t)), "cudaMalloc(items)")) != GF_OK)
+    if ((s = cuda_status(dev_alloc(&b->d_item_medium, n * sizeof(int32_t)), "cudaMalloc(items)")) != GF_OK ||
+        (s = cuda_status(dev_alloc(&b->d_item_begin, n * sizeof(int64_t)), "cudaMalloc(items)")) != GF_OK ||
+        (s = cuda_status(dev_alloc(&b->d_item_end, n * sizeof(int64_t)), "cudaMalloc(items)")) != GF_OK)
         return s;
     if (!med.empty()) {
         cudaMemcpy(b->d_item_medium, med.data(), med.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
@@ -686,14 +688,16 @@ static gf_status run_dopri5(gf_batch b, const gf_rays *rays, int32_t *rejects, d
                              "cudaStreamCreate")) != GF_OK)
             return s;
         cudaGraph_t graph = nullptr;
-        if ((s = cuda_status(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal),
-                             "cudaStreamBeginCapture")) != GF_OK)
-            return s;
-        cudaError_t le = enqueue(b, sched, t, p, r, rejects, omega, c, b->capture);
-        cudaError_t ce = cudaStreamEndCapture(b->capture, &graph);
-        if (le != cudaSuccess || ce != cudaSuccess) {
+        // a capture once begun is always ended before any status is checked, so
+        // that no error path can leave the stream (and this thread) capturing
+        const cudaError_t be = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
+        if (be != cudaSuccess) return cuda_status(be, "cudaStreamBeginCapture");
+        const cudaError_t le = enqueue(b, sched, t, p, r, rejects, omega, c, b->capture);
+        const cudaError_t ce = cudaStreamEndCapture(b->capture, &graph);
+        if ((s = cuda_status(le, "gf_trace_dopri5 capture")) != GF_OK ||
+            (s = cuda_status(ce, "cudaStreamEndCapture")) != GF_OK) {
             if (graph) cudaGraphDestroy(graph);
-            return cuda_status(le != cudaSuccess ? le : ce, "gf_trace_dopri5 capture");
+            return s;
         }
         cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
         cudaGraphDestroy(graph);
@@ -811,13 +815,13 @@ gf_status gf_batch_create(const gf_medium *media, int32_t n_media, const int64_t
     gf_status s = GF_OK;
     const size_t row = (size_t)b->nb_max * kBlobStride, prow = (size_t)b->nb_max * 4,
                  drow = (size_t)b->nb_max * kDfBlobStride;
-    if ((s = cuda_status(cudaMalloc(&b->d_blobs, row * n_media * sizeof(double)), "cudaMalloc(batch)")) != GF_OK ||
-        (s = cuda_status(cudaMalloc(&b->d_df, drow * n_media * sizeof(float)), "cudaMalloc(batch)")) != GF_OK ||
-        (s = cuda_status(cudaMalloc(&b->d_pre, prow * n_media * sizeof(float)), "cudaMalloc(batch)")) != GF_OK ||
-        (s = cuda_status(cudaMalloc(&b->d_pre_lim, pre_lim.size() * sizeof(float)), "cudaMalloc(batch)")) != GF_OK ||
-        (s = cuda_status(cudaMalloc(&b->d_base, base.size() * sizeof(double)), "cudaMalloc(batch)")) != GF_OK ||
-        (s = cuda_status(cudaMalloc(&b->d_nb, nb.size() * sizeof(int32_t)), "cudaMalloc(batch)")) != GF_OK ||
-        (s = cuda_status(cudaMalloc(&b->d_head, sizeof(int)), "cudaMalloc(batch)")) != GF_OK) {
+    if ((s = cuda_status(dev_alloc(&b->d_blobs, row * n_media * sizeof(double)), "cudaMalloc(batch)")) != GF_OK ||
+        (s = cuda_status(dev_alloc(&b->d_df, drow * n_media * sizeof(float)), "cudaMalloc(batch)")) != GF_OK ||
+        (s = cuda_status(dev_alloc(&b->d_pre, prow * n_media * sizeof(float)), "cudaMalloc(batch)")) != GF_OK ||
+        (s = cuda_status(dev_alloc(&b->d_pre_lim, pre_lim.size() * sizeof(float)), "cudaMalloc(batch)")) != GF_OK ||
+        (s = cuda_status(dev_alloc(&b->d_base, base.size() * sizeof(double)), "cudaMalloc(batch)")) != GF_OK ||
+        (s = cuda_status(dev_alloc(&b->d_nb, nb.size() * sizeof(int32_t)), "cudaMalloc(batch)")) != GF_OK ||
+        (s = cuda_status(dev_alloc(&b->d_head, sizeof(int)), "cudaMalloc(batch)")) != GF_OK) {
         batch_free(b);
         return s;
     }
@@ -929,14 +933,14 @@ gf_status gf_dopri5_autotune(gf_batch b, const gf_rays *rays, double omega, cons
     double *y = nullptr, *t = nullptr, *dres = nullptr, *dmax = nullptr;
     int32_t *st = nullptr, *steps = nullptr;
     auto release = [&]() {
-        cudaFree(y); cudaFree(t); cudaFree(dres); cudaFree(dmax); cudaFree(st); cudaFree(steps);
+        dev_free(y); dev_free(t); dev_free(dres); dev_free(dmax); dev_free(st); dev_free(steps);
     };
-    if ((s = cuda_status(cudaMalloc(&y, 6 * n * sizeof(double)), "cudaMalloc(tune)")) != GF_OK ||
-        (s = cuda_status(cudaMalloc(&t, n * sizeof(double)), "cudaMalloc(tune)")) != GF_OK ||
-        (s = cuda_status(cudaMalloc(&dres, n * sizeof(double)), "cudaMalloc(tune)")) != GF_OK ||
-        (s = cuda_status(cudaMalloc(&dmax, n * sizeof(double)), "cudaMalloc(tune)")) != GF_OK ||
-        (s = cuda_status(cudaMalloc(&st, n * sizeof(int32_t)), "cudaMalloc(tune)")) != GF_OK ||
-        (s = cuda_status(cudaMalloc(&steps, n * sizeof(int32_t)), "cudaMalloc(tune)")) != GF_OK) {
+    if ((s = cuda_status(dev_alloc(&y, 6 * n * sizeof(double)), "cudaMalloc(tune)")) != GF_OK ||
+        (s = cuda_status(dev_alloc(&t, n * sizeof(double)), "cudaMalloc(tune)")) != GF_OK ||
+        (s = cuda_status(dev_alloc(&dres, n * sizeof(double)), "cudaMalloc(tune)")) != GF_OK ||
+        (s = cuda_status(dev_alloc(&dmax, n * sizeof(double)), "cudaMalloc(tune)")) != GF_OK ||
+        (s = cuda_status(dev_alloc(&st, n * sizeof(int32_t)), "cudaMalloc(tune)")) != GF_OK ||
+        (s = cuda_status(dev_alloc(&steps, n * sizeof(int32_t)), "cudaMalloc(tune)")) != GF_OK) {
         release();
         return s;
     }
@@ -955,7 +959,8 @@ gf_status gf_dopri5_autotune(gf_batch b, const gf_rays *rays, double omega, cons
     sub.prec = b->prec;
     sub.d_base = b->d_base;
     sub.d_nb = b->d_nb;
-    if ((s = cuda_status(cudaMalloc(&sub.d_head, sizeof(int)), "cudaMalloc(tune)")) != GF_OK) {
+    if ((s = cuda_status(dev_alloc(&sub.d_head, sizeof(int)), "cudaMalloc(tune)")) != GF_OK) {
+        dev_free(sub.d_head);   // allocated when only the status check failed
         release();
         return s;
     }
@@ -1003,10 +1008,10 @@ gf_status gf_dopri5_autotune(gf_batch b, const gf_rays *rays, double omega, cons
                 }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(sub.d_head);
-    cudaFree(sub.d_item_medium);
-    cudaFree(sub.d_item_begin);
-    cudaFree(sub.d_item_end);
+    dev_free(sub.d_head);
+    dev_free(sub.d_item_medium);
+    dev_free(sub.d_item_begin);
+    dev_free(sub.d_item_end);
     sub.d_blobs = nullptr;
     sub.d_pre = sub.d_pre_lim = sub.d_df = nullptr;
     sub.d_base = nullptr;

@@ -73,6 +73,14 @@ namespace gf {
 
 void set_error(const char *fmt, ...);
 gf_status cuda_status(cudaError_t e, const char *what);
+// Device allocations of the library (counted; see gf_bench_live_allocations).
+cudaError_t dev_alloc(void **p, size_t bytes);
+template <typename T>
+inline cudaError_t dev_alloc(T **p, size_t bytes)
+{
+    return dev_alloc(reinterpret_cast<void **>(p), bytes);
+}
+void dev_free(void *p);   // NULL: no-op
 gf_status check_rays(const gf_rays *r, bool need_state);
 gf_status check_device_ptr(const void *p, const char *name);
 const MediumParams &params_of(gf_medium m);

@@ -89,3 +89,13 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(gf, "LIB_PATH", str(tmp_path / "libgf.so"))
     with pytest.raises(RuntimeError, match="libgf.so not found"):
         gf.lib()
+
+
+def test_fault_injection_and_allocation_count_on_the_host(libgf):
+    """The failure-testing hooks are host-only: arming and disarming touch no
+    device, and a process that has created nothing holds no allocation."""
+    assert libgf.gf_fault_inject(C.c_int64(5)) == gf.GF_OK
+    assert libgf.gf_fault_inject(C.c_int64(0)) == gf.GF_OK
+    assert libgf.gf_fault_inject(C.c_int64(-3)) == gf.GF_OK
+    n, nbytes = gf.gf_bench_live_allocations()
+    assert n >= 0 and nbytes >= 0
