@@ -3,7 +3,7 @@
 // of the GF_F64X mode.
 //
 // On GB300 the FP64 pipe retires 2 lanes per clock per SM against 128 for
-// FP32, so the blob terms -- 86% of the FP64 instructions of a GRIN ray step --
+// FP32, so the blob terms -- about 80% of the FP64 instructions of a GRIN ray step --
 // are computed here with error-free transformations on the FP32 pipe and only
 // their sums are returned in double:
 //   two_sum (Knuth, TAOCP vol. 2), fast_two_sum and two_prod via FMA
@@ -11,7 +11,7 @@
 //   "Tight and rigorous error bounds for basic building blocks of double-word
 //   arithmetic", ACM TOMS 44 (2017): AccurateDWPlusDW (relative error
 //   <= 3u^2 + 13u^3), SloppyDWPlusDW (where no cancellation matters),
-//   DWPlusFP, DWTimesDW2 (<= 5u^2), DWTimesFP2, u = 2^-24.
+//   DWTimesDW2 (<= 5u^2), DWTimesFP2, u = 2^-24.
 // Every operation uses explicitly rounded intrinsics so that the compiler
 // neither contracts nor reassociates them.
 #pragma once
@@ -65,13 +65,6 @@ __device__ __forceinline__ dfl df_add_sloppy(dfl x, dfl y)
     const dfl s = two_sum(x.hi, y.hi);
     const float v = __fadd_rn(x.lo, y.lo);
     return fast_two_sum(s.hi, __fadd_rn(s.lo, v));
-}
-
-// DWPlusFP
-__device__ __forceinline__ dfl df_add_f(dfl x, float y)
-{
-    const dfl s = two_sum(x.hi, y);
-    return fast_two_sum(s.hi, __fadd_rn(x.lo, s.lo));
 }
 
 // DWTimesDW2
