@@ -127,6 +127,83 @@ def oracle_throughput(wl, n_rays: int) -> dict:
                       f"({units} ray-steps, {el:.1f} s)", "seconds": el}
 
 
+def oracle_sample(name: str) -> dict:
+    """The oracle as it stands on a bounded sample of one secondary workload
+    (host cores), in the unit of that workload's GPU figure; a few seconds of
+    CPU work each.  Inputs are prepared untimed (on-shell k, Newton on k_x)."""
+    import oracle as O
+    t0 = None
+    if name == "luneburg":
+        wl = W.luneburg()
+        n = wl.n
+    elif name == "cold":
+        wl, n = W.cold(n=32768), 32768
+    elif name == "aniso":
+        wl, n = W.aniso(n=1024), 1024
+    elif name == "adjoint":
+        wl, n = W.adjoint(n=256), 256
+    elif name == "batched":
+        wl = W.batched()
+        off = wl.extra["offsets"]
+        m_end = int(np.searchsorted(off, 65536, side="left"))
+        m_end = max(1, min(m_end, len(off) - 1))
+        n = int(off[m_end])
+    else:
+        raise ValueError(name)
+    if name == "batched":
+        blobs = wl.extra["blobs"]
+        media = [O.medium(kind="luneburg", blobs=blobs[j]) for j in range(m_end)]
+        k0 = np.empty_like(wl.x0[:n])
+        for j in range(m_end):
+            lo, hi = int(off[j]), int(off[j + 1])
+            if hi > lo:
+                k0[lo:hi], _ = O.onshell(media[j], wl.x0[lo:hi], wl.d[lo:hi])
+        r = O.make_rays(wl.x0[:n], k0)
+        e = wl.extra
+        t0 = time.perf_counter()
+        O.trace_dopri5(media, off[:m_end + 1], r, wl.omega, rtol=e["rtol"], atol=e["atol"], h0=e["h0"],
+                       t_max=e["t_max"], radius=wl.radius, max_steps=e["max_steps"])
+        el = time.perf_counter() - t0
+        units = int(r.steps.astype(np.int64).sum())
+        what = f"DOPRI5 over the first {m_end} media ({n} rays), accepted steps"
+        unit = "accepted ray-steps/s"
+    else:
+        m = O.medium(**wl.medium)
+        if name == "cold":
+            k0, st, _ = O.newton_kx(m, wl.x0[:n], wl.extra["k_start"][:n], wl.omega)
+            r = O.make_rays(wl.x0[:n], k0, status=st)
+        else:
+            k0, st = O.onshell(m, wl.x0[:n], wl.d[:n], wl.omega)
+            r = O.make_rays(wl.x0[:n], k0)
+        t0 = time.perf_counter()
+        if name == "adjoint":
+            O.tangent_rk4(m, r, wl.omega, wl.dt, wl.n_steps)
+        else:
+            O.trace_rk4(m, r, wl.omega, wl.dt, wl.n_steps)
+        el = time.perf_counter() - t0
+        if name == "adjoint":
+            units = n * wl.n_steps
+            what = (f"tangent-linear gradient (the oracle's adjoint) of {n} rays x {wl.n_steps} RK4 steps, "
+                    f"{wl.medium['blobs'].shape[0]} parameters")
+            unit = "gradient ray-steps/s"
+        else:
+            units = int(r.steps.astype(np.int64).sum())
+            what = f"{n} rays x {wl.n_steps} RK4 steps"
+            unit = UNIT
+    return {"value": units / el, "unit": unit, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{what} of the same workload ({units} units, {el:.2f} s)"}
+
+
+def _with_oracle(res: dict, name: str) -> dict:
+    """Attach the oracle's figure on a sample of the same workload (never
+    fails the measurement it is attached to)."""
+    try:
+        res["cpu_baseline"] = oracle_sample(name)
+    except Exception as e:  # noqa: BLE001 -- a report field, not a result
+        res["cpu_baseline"] = {"error": f"{type(e).__name__}: {e}"}
+    return res
+
+
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -427,6 +504,8 @@ def measure_adjoint(gf, torch, n: int | None = None, n_steps: int | None = None)
         theta.grad = None
     res["backward_over_forward"] = res["backward_ms"] / res["forward_ckpt_ms"]
     res["total_over_plain_forward"] = (res["forward_ckpt_ms"] + res["backward_ms"]) / res["plain_forward_ms"]
+    # the gradient's throughput: ray-steps of the trace per second of forward + backward
+    res["gradient_ray_steps_per_s"] = wl.n * wl.n_steps / ((res["forward_ckpt_ms"] + res["backward_ms"]) / 1e3)
     res["loss"] = loss.item()
     res["workload"] = (f"{wl.n} rays, Luneburg + {len(wl.extra['theta'])} blobs, RK4 dt={wl.dt} x {wl.n_steps}, "
                        f"checkpoint every {wl.extra['checkpoint_every']}")
@@ -591,6 +670,9 @@ def run_gpu(a):
         line["aniso"] = measure_aniso(gf, torch, peak64)
         line["adjoint"] = measure_adjoint(gf, torch)
         line["batched"] = measure_batched(gf, torch)
+        if rank == 0 and not a.no_cpu_baseline:
+            for name in ("luneburg", "cold", "aniso", "adjoint", "batched"):
+                _with_oracle(line[name], name)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cb = oracle_throughput(W.grin(n=a.cpu_rays, n_steps=a.nsteps), a.cpu_rays)
         cb.pop("seconds")
@@ -622,6 +704,8 @@ def run_workload(a):
         res = measure_adjoint(gf, torch, min(a.rays, d["n"].default), min(a.nsteps, d["n_steps"].default))
     else:
         res = measure_generated(gf, torch, min(a.rays, 1 << 18), min(a.nsteps, 2000))
+    if a.workload in ("luneburg", "cold", "aniso", "adjoint", "batched") and not a.no_cpu_baseline:
+        _with_oracle(res, a.workload)
     print(json.dumps({"workload": a.workload, **res}), flush=True)
 
 

@@ -26,3 +26,16 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert "workload" in d["config"]
+
+
+def test_secondary_workload_oracle_samples():
+    """The oracle figures attached to the secondary measurements carry the
+    cpu_baseline keys and a positive rate; a failure becomes an error field,
+    never an exception."""
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench._with_oracle({}, "luneburg")["cpu_baseline"]
+    assert r["kind"] == "oracle" and r["value"] > 0 and r["cores"] >= 1
+    assert r["unit"] == "ray-steps/s" and "1024 rays x 2000 RK4 steps" in r["sample"]
+    bad = bench._with_oracle({}, "no such workload")["cpu_baseline"]
+    assert "error" in bad
