@@ -133,9 +133,10 @@ def oracle_sample(name: str) -> dict:
     CPU work each.  Inputs are prepared untimed (on-shell k, Newton on k_x)."""
     import oracle as O
     t0 = None
+    reps = 1
     if name == "luneburg":
         wl = W.luneburg()
-        n = wl.n
+        n, reps = wl.n, 25          # one trace is ~10 ms of host time: repeat it
     elif name == "cold":
         wl, n = W.cold(n=32768), 32768
     elif name == "aniso":
@@ -171,27 +172,27 @@ def oracle_sample(name: str) -> dict:
         m = O.medium(**wl.medium)
         if name == "cold":
             k0, st, _ = O.newton_kx(m, wl.x0[:n], wl.extra["k_start"][:n], wl.omega)
-            r = O.make_rays(wl.x0[:n], k0, status=st)
         else:
             k0, st = O.onshell(m, wl.x0[:n], wl.d[:n], wl.omega)
-            r = O.make_rays(wl.x0[:n], k0)
-        t0 = time.perf_counter()
+        el, units = 0.0, 0
+        for _ in range(reps):
+            r = O.make_rays(wl.x0[:n], k0, status=st if name == "cold" else None)
+            t0 = time.perf_counter()
+            if name == "adjoint":
+                O.tangent_rk4(m, r, wl.omega, wl.dt, wl.n_steps)
+            else:
+                O.trace_rk4(m, r, wl.omega, wl.dt, wl.n_steps)
+            el += time.perf_counter() - t0
+            units += n * wl.n_steps if name == "adjoint" else int(r.steps.astype(np.int64).sum())
         if name == "adjoint":
-            O.tangent_rk4(m, r, wl.omega, wl.dt, wl.n_steps)
-        else:
-            O.trace_rk4(m, r, wl.omega, wl.dt, wl.n_steps)
-        el = time.perf_counter() - t0
-        if name == "adjoint":
-            units = n * wl.n_steps
             what = (f"tangent-linear gradient (the oracle's adjoint) of {n} rays x {wl.n_steps} RK4 steps, "
                     f"{wl.medium['blobs'].shape[0]} parameters")
             unit = "gradient ray-steps/s"
         else:
-            units = int(r.steps.astype(np.int64).sum())
-            what = f"{n} rays x {wl.n_steps} RK4 steps"
+            what = f"{n} rays x {wl.n_steps} RK4 steps" + (f", {reps} times" if reps > 1 else "")
             unit = UNIT
     return {"value": units / el, "unit": unit, "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"{what} of the same workload ({units} units, {el:.2f} s)"}
+            "sample": f"{what}: {units} units in {el:.2f} s (a sample of the same workload)"}
 
 
 def _with_oracle(res: dict, name: str) -> dict:

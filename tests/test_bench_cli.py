@@ -36,6 +36,6 @@ def test_secondary_workload_oracle_samples():
     import bench
     r = bench._with_oracle({}, "luneburg")["cpu_baseline"]
     assert r["kind"] == "oracle" and r["value"] > 0 and r["cores"] >= 1
-    assert r["unit"] == "ray-steps/s" and "1024 rays x 2000 RK4 steps" in r["sample"]
+    assert r["unit"] == "ray-steps/s" and "1024 rays x 2000 RK4 steps, 25 times" in r["sample"]
     bad = bench._with_oracle({}, "no such workload")["cpu_baseline"]
     assert "error" in bad
