@@ -7,6 +7,8 @@ the objects are destroyed), and leave the library usable: the same sequence
 then runs to the same, bit-identical results."""
 from __future__ import annotations
 
+import gc
+
 import numpy as np
 import pytest
 import torch
@@ -110,6 +112,7 @@ def _same(a, b):
                          ids=["rk4_adjoint", "spline_f32", "batch_dopri5"])
 def test_injected_failures_release_everything_and_leave_the_library_usable(sequence):
     gf.gf_fault_inject(0)
+    gc.collect()                     # objects of earlier tests are gone before the baseline
     base = gf.gf_bench_live_allocations()
     ref = sequence()
     assert gf.gf_bench_live_allocations() == base
@@ -127,6 +130,7 @@ def test_injected_failures_release_everything_and_leave_the_library_usable(seque
         finally:
             gf.gf_fault_inject(0)
         torch.cuda.synchronize()
+        gc.collect()
         assert gf.gf_bench_live_allocations() == base, (n, str(gf.gf_bench_live_allocations()))
         _same(sequence(), ref)       # the library (streams, caches) still works
     else:
