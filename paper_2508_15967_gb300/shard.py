@@ -47,6 +47,34 @@ def shard_media(offsets, rank: int, world: int) -> tuple[int, int]:
     return cut(rank), cut(rank + 1)
 
 
+def ray_share(scaling: str, n: int, rank: int, world: int) -> tuple[int, int, int]:
+    """What one rank of a data-parallel run traces, as (seed shard, lo, hi):
+    weak scaling gives every rank its own independent set of n rays (seed
+    shard = rank, all of [0, n)); strong scaling splits one fixed set of n
+    rays (seed shard 0) into balanced contiguous ranges (shard_bounds)."""
+    if scaling == "weak":
+        if world < 1 or not 0 <= rank < world or n < 0:
+            raise ValueError("need world >= 1, 0 <= rank < world, n >= 0")
+        return rank, 0, n
+    if scaling == "strong":
+        return (0, *shard_bounds(n, rank, world))
+    raise ValueError(f"scaling must be 'weak' or 'strong', not {scaling!r}")
+
+
+def media_share(scaling: str, offsets, rank: int, world: int) -> tuple[int, int, int]:
+    """What one rank traces of a batch of media, as (seed shard, m_lo, m_hi):
+    weak scaling gives every rank its own independent batch (seed shard =
+    rank, every medium); strong scaling splits one fixed batch into
+    contiguous media balanced on their ray counts (shard_media)."""
+    if scaling == "weak":
+        if world < 1 or not 0 <= rank < world:
+            raise ValueError("need world >= 1 and 0 <= rank < world")
+        return rank, 0, len(offsets) - 1
+    if scaling == "strong":
+        return (0, *shard_media(offsets, rank, world))
+    raise ValueError(f"scaling must be 'weak' or 'strong', not {scaling!r}")
+
+
 def allreduce_gradient(grad: torch.Tensor, group=None) -> torch.Tensor:
     """Sum a per-rank gradient (dL/dtheta of that rank's rays) over all ranks, in place."""
     if dist.is_available() and dist.is_initialized() and dist.get_world_size(group) > 1:

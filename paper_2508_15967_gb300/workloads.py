@@ -73,9 +73,12 @@ def morton_order(p: np.ndarray) -> np.ndarray:
     return np.argsort(code, kind="stable")
 
 
-def aperture_rays(rng: np.random.Generator, n: int, radius: float):
-    """plane_disk_rays listed in Morton order of their launch points (y0, z0)."""
+def aperture_rays(rng: np.random.Generator, n: int, radius: float, morton: bool = True):
+    """plane_disk_rays listed in Morton order of their launch points (y0, z0),
+    or in the order drawn (morton = False)."""
     x0, d = plane_disk_rays(rng, n, radius)
+    if not morton:
+        return x0, d
     o = morton_order(x0[:, 1:])
     return x0[o], d[o]
 
@@ -219,23 +222,25 @@ def aniso(n: int = 262144, n_steps: int = 4000, dt: float = 1e-3, g: int = 128,
 
 
 def batched(n_media: int = 4096, n_blobs: int = 8, e_lo: int = 4, e_hi: int = 14,
-            scale_counts: float = 1.0) -> Workload:
+            scale_counts: float = 1.0, morton: bool = True, shard: int = 0) -> Workload:
     """Many Luneburg+blob media with power-of-two ray counts 2^U{e_lo..e_hi}.
 
     Rays of medium m occupy [offsets[m], offsets[m+1]) and launch as in the
     Luneburg workload (each medium's rays in Morton order of their launch
-    points).  ``scale_counts`` < 1 shrinks every count (at least 1 ray) for
-    test-sized cases while keeping the unevenness.
+    points, or in the order drawn with ``morton = False``).  ``scale_counts``
+    < 1 shrinks every count (at least 1 ray) for test-sized cases while
+    keeping the unevenness.  ``shard`` > 0 draws an independent batch (media
+    and rays) of the same shape, one per GPU of a weak-scaling run.
     """
-    rng = rng_for(BATCHED)
+    rng = rng_for(BATCHED) if shard == 0 else rng_for(BATCHED, 3 + 1000 * shard)
     exps = rng.integers(e_lo, e_hi + 1, n_media)
     counts = np.maximum(1, np.round((2.0 ** exps) * scale_counts)).astype(np.int64)
     blobs = np.stack([blob_table(rng, n_blobs, 0.02) for _ in range(n_media)])
     offsets = np.zeros(n_media + 1, dtype=np.int64)
     offsets[1:] = np.cumsum(counts)
-    rr = rng_for(BATCHED, 7)
+    rr = rng_for(BATCHED, 7 + 1000 * shard)
     x0, d = plane_disk_rays(rr, int(offsets[-1]), 0.9)
-    for m in range(n_media):
+    for m in range(n_media if morton else 0):
         lo, hi = int(offsets[m]), int(offsets[m + 1])
         o = morton_order(x0[lo:hi, 1:])
         x0[lo:hi], d[lo:hi] = x0[lo:hi][o], d[lo:hi][o]
@@ -246,18 +251,20 @@ def batched(n_media: int = 4096, n_blobs: int = 8, e_lo: int = 4, e_hi: int = 14
 
 
 def adjoint(n: int = 65536, n_steps: int = 4000, dt: float = 1e-3, n_blobs: int = 64,
-            checkpoint_every: int = 64) -> Workload:
+            checkpoint_every: int = 64, morton: bool = True, shard: int = 0) -> Workload:
     """Luneburg base + n_blobs Gaussian blobs whose amplitudes theta are the parameters.
 
     theta ~ N(0, 0.01) (seed 250815967+5), hidden theta* from seed + 1000;
     centres and widths are shared by both.  Rays launch as in the Luneburg
-    workload, in Morton order of their launch points.
+    workload, in Morton order of their launch points (or in the order drawn
+    with ``morton = False``).  ``shard`` > 0 draws an independent set of rays
+    for the same medium and parameters (one per GPU of a weak-scaling run).
     """
     rng = rng_for(ADJOINT)
     blobs = blob_table(rng, n_blobs, 0.01)
     theta_star = rng_for(ADJOINT, 1000).normal(0.0, 0.01, n_blobs)
-    rr = rng_for(ADJOINT, 7)
-    x0, d = aperture_rays(rr, n, 0.9)
+    rr = rng_for(ADJOINT, 7 + 1000 * shard)
+    x0, d = aperture_rays(rr, n, 0.9, morton)
     wl = Workload("adjoint", dict(kind="luneburg", blobs=blobs), x0, d, 1.0, dt, n_steps)
     wl.extra = dict(theta=blobs[:, 0].copy(), theta_star=theta_star,
                     checkpoint_every=checkpoint_every)

@@ -1,9 +1,14 @@
 """GPU discrete adjoint of the RK4 trace (dL/dtheta for the blob amplitudes)
 against the oracle's forward tangent-linear sensitivities (<= 1e-9, a
 different derivation of the same derivative) and against central finite
-differences of the GPU forward loss (h = 1e-6, <= 1e-5) on rays that keep
-clear of the Luneburg kink (min over stage points of ||x|^2 - 1| > 1e-5,
-computed by the oracle).  Loss: L = sum_rays |x_N - x*_N|^2."""
+differences of the GPU forward loss (h = 1e-6, <= 1e-5, every parameter) on
+rays that keep clear of the Luneburg kink (min over stage points of
+||x|^2 - 1| > 1e-5, computed by the oracle).  Loss: L = sum_rays |x_N - x*_N|^2.
+
+Errors are measured per component: |g_j - ref_j| / max(|ref_j|, 1e-3 max_i |ref_i|),
+so that a small component is held to the tolerance relative to its own size
+(down to a floor of 1e-3 of the largest component, below which a component
+is numerically zero against the others)."""
 from __future__ import annotations
 
 import numpy as np
@@ -52,12 +57,18 @@ def _rel(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
+def _rel_per_component(a, ref, floor=1e-3):
+    """max_j |a_j - ref_j| / max(|ref_j|, floor * max_i |ref_i|)."""
+    ref = np.asarray(ref)
+    return (np.abs(np.asarray(a) - ref) / np.maximum(np.abs(ref), floor * np.abs(ref).max())).max()
+
+
 def test_adjoint_matches_oracle_tangent_linear():
     """256 rays (4 blocks), 1000 steps, 64 blobs: adjoint vs tangent-linear."""
     wl, om, y0, xstar = _case(256, 1000)
     g_gpu, _, _ = _gpu_grad(wl, y0, xstar)
     g_or = _oracle_grad(om, y0, xstar, wl)
-    assert _rel(g_gpu, g_or) <= 1e-9, _rel(g_gpu, g_or)
+    assert _rel_per_component(g_gpu, g_or) <= 1e-9, _rel_per_component(g_gpu, g_or)
 
 
 def test_adjoint_full_length_trace():
@@ -66,10 +77,12 @@ def test_adjoint_full_length_trace():
     wl, om, y0, xstar = _case(100, 4000)
     g_gpu, _, _ = _gpu_grad(wl, y0, xstar)
     g_or = _oracle_grad(om, y0, xstar, wl)
-    assert _rel(g_gpu, g_or) <= 1e-9, _rel(g_gpu, g_or)
+    assert _rel_per_component(g_gpu, g_or) <= 1e-9, _rel_per_component(g_gpu, g_or)
 
 
 def test_adjoint_matches_central_differences():
+    """Central differences (h = 1e-6) of the GPU forward loss for all 64
+    amplitudes, 128 traces run concurrently on 16 streams, per component."""
     wl, om, y0, xstar = _case(192, 4000)
     r = O.make_rays(y0[:, :3], y0[:, 3:])
     kink = O.trace_rk4_kink(om, r, 1.0, wl.dt, wl.n_steps)
@@ -77,26 +90,28 @@ def test_adjoint_matches_central_differences():
     assert keep.mean() > 0.9
     y0k, xk = y0[keep], xstar[keep]
     g_gpu, _, _ = _gpu_grad(wl, y0k, xk)
-    m = gf.gf_medium_create(**wl.medium)
     y0_t = torch.from_numpy(np.ascontiguousarray(y0k.T)).cuda()
     xs = torch.from_numpy(np.ascontiguousarray(xk.T)).cuda()
-
-    def loss(theta):
-        gf.gf_medium_set_amplitudes(m, torch.tensor(theta, device="cuda"))
-        rays = gf.Rays.empty(y0k.shape[0])
-        rays.y.copy_(y0_t)
-        gf.gf_trace_rk4(m, rays, 1.0, wl.dt, wl.n_steps)
-        return ((rays.y[:3] - xs) ** 2).sum().item()
-
     th = wl.extra["theta"]
     h = 1e-6
-    scale = np.abs(g_gpu).max()
-    for j in np.random.default_rng(0).choice(64, 6, replace=False):
-        tp, tm = th.copy(), th.copy()
-        tp[j] += h
-        tm[j] -= h
-        fd = (loss(tp) - loss(tm)) / (2 * h)
-        assert abs(fd - g_gpu[j]) <= 1e-5 * scale, (j, fd, g_gpu[j])
+    streams = [torch.cuda.Stream() for _ in range(16)]
+    traces = []
+    torch.cuda.synchronize()
+    for j in range(len(th)):
+        for sign in (1.0, -1.0):
+            blobs = wl.medium["blobs"].copy()
+            blobs[j, 0] = th[j] + sign * h
+            m = gf.gf_medium_create("luneburg", blobs=blobs)
+            rays = gf.Rays.empty(y0k.shape[0], diagnostics=False)
+            rays.y.copy_(y0_t)
+            st = streams[len(traces) % len(streams)]
+            st.wait_stream(torch.cuda.current_stream())
+            gf.gf_trace_rk4(m, rays, 1.0, wl.dt, wl.n_steps, stream=st)
+            traces.append((m, rays))
+    torch.cuda.synchronize()
+    loss = [((rays.y[:3] - xs) ** 2).sum().item() for _, rays in traces]
+    fd = np.array([(loss[2 * j] - loss[2 * j + 1]) / (2 * h) for j in range(len(th))])
+    assert _rel_per_component(g_gpu, fd) <= 1e-5, _rel_per_component(g_gpu, fd)
 
 
 def test_autograd_dy0_and_direct_call_agree():
@@ -194,7 +209,7 @@ def test_full_size_adjoint_sampled_rays():
     r = O.make_rays(y0s[:, :3], y0s[:, 3:])
     S = O.tangent_rk4(O.medium(**wl.medium), r, 1.0, wl.dt, wl.n_steps)
     g_or = O.loss_grad(r.y, xstar[:, idx].T.cpu().numpy(), S)
-    assert _rel(dth.cpu().numpy(), g_or) <= 1e-9
+    assert _rel_per_component(dth.cpu().numpy(), g_or) <= 1e-9
     # additivity over disjoint ray sets
     lam = torch.zeros_like(rays.y)
     lam[:3] = 2 * (rays.y[:3] - xstar)

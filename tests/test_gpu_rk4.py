@@ -42,6 +42,25 @@ def test_luneburg_workload_full_size():
     assert_parity(g, o, 1e-9)
 
 
+def test_luneburg_focus_on_gpu():
+    """The Luneburg workload's 1024 rays traced on the GPU to t = 1 + pi/2 (2571
+    RK4 steps): every ray reaches the focus (1, 0, 0) (the closed form: all rays
+    from the plane x = -1 meet there at that time; the O(dt) kink error at the
+    lens surface bounds the distance by 1e-3), and the endpoints match the
+    oracle's within 1e-9."""
+    wl = W.luneburg()
+    k0 = _onshell(wl.medium, wl.x0, wl.d)
+    n = 2571
+    dt = (1 + math.pi / 2) / n
+    g = gpu_rk4(wl.medium, wl.x0, k0, 1.0, dt, n)
+    o, _ = oracle_rk4(wl.medium, wl.x0, k0, 1.0, dt, n)
+    assert_parity(g, o, 1e-9)
+    dist = np.linalg.norm(g.y[:, :3] - np.array([1.0, 0.0, 0.0]), axis=1)
+    assert dist.max() < 1e-3, dist.max()
+    # on shell at the focus, which lies on the lens surface: |k| = w n = 1
+    np.testing.assert_allclose(np.linalg.norm(g.y[:, 3:], axis=1), 1.0, atol=5e-3)
+
+
 def test_grin_f64_parity_ragged():
     """GRIN + 16 blobs, 1000 rays (7 full blocks + a tail of 104), 10,000 steps."""
     wl = W.grin(n=1000)

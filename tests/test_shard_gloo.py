@@ -1,8 +1,11 @@
-"""Multi-process (world_size 2, gloo, CPU) checks of the data-parallel path:
-shards cover every ray once; the sum of per-shard adjoint gradients equals the
-single-process gradient (oracle tangent-linear sensitivities on each shard);
-a batch of media sharded by ray counts traces, rank by rank, exactly what one
-process traces; the job time is the slowest rank's."""
+"""Multi-process (world_size 2, gloo, CPU) checks of the data-parallel path,
+with the rank logic the benchmark uses (ray_share, media_share): shards cover
+every ray once; the sum of per-shard adjoint gradients equals the
+single-process gradient (oracle tangent-linear sensitivities on each shard),
+for one ray set split across the ranks (strong scaling) and for every rank's
+own ray set (weak scaling); a batch of media sharded by ray counts traces,
+rank by rank, exactly what one process traces; the job time is the slowest
+rank's."""
 from __future__ import annotations
 
 import os
@@ -13,7 +16,8 @@ import pytest
 import torch
 import torch.multiprocessing as mp
 
-from paper_2508_15967_gb300.shard import allreduce_gradient, max_over_ranks, shard_bounds, shard_media
+from paper_2508_15967_gb300.shard import (allreduce_gradient, max_over_ranks, media_share, ray_share,
+                                          shard_bounds, shard_media)
 
 
 def test_shard_bounds_partition():
@@ -34,10 +38,31 @@ def _free_port() -> int:
         return s.getsockname()[1]
 
 
-def _grad_of_rays(idx):
+def test_ray_and_media_share():
+    from paper_2508_15967_gb300 import workloads as W
+    for world in (1, 2, 3, 8):
+        weak = [ray_share("weak", 100, r, world) for r in range(world)]
+        assert weak == [(r, 0, 100) for r in range(world)]          # own seeds, whole sets
+        strong = [ray_share("strong", 100, r, world) for r in range(world)]
+        assert all(sd == 0 for sd, _, _ in strong)                   # one shared set ...
+        assert [(lo, hi) for _, lo, hi in strong] == [shard_bounds(100, r, world) for r in range(world)]
+    off = W.batched(n_media=64).extra["offsets"]
+    assert [media_share("weak", off, r, 4) for r in range(4)] == [(r, 0, 64) for r in range(4)]
+    assert [media_share("strong", off, r, 4)[1:] for r in range(4)] == [shard_media(off, r, 4) for r in range(4)]
+    with pytest.raises(ValueError):
+        ray_share("diagonal", 10, 0, 1)
+    # weak-scaling seeds give independent inputs of the same shape
+    a, b = W.adjoint(n=16, shard=0), W.adjoint(n=16, shard=1)
+    assert a.x0.shape == b.x0.shape and not np.allclose(a.x0, b.x0)
+    assert np.array_equal(a.medium["blobs"], b.medium["blobs"])   # the parameters are shared
+    c, d = W.batched(n_media=8, shard=0), W.batched(n_media=8, shard=1)
+    assert not np.array_equal(c.extra["blobs"], d.extra["blobs"])
+
+
+def _grad_of_rays(idx, shard=0):
     import oracle as O
     from paper_2508_15967_gb300 import workloads as W
-    wl = W.adjoint(n=24, n_steps=150, n_blobs=6)
+    wl = W.adjoint(n=24, n_steps=150, n_blobs=6, shard=shard)
     m = O.medium(**wl.medium)
     k0, _ = O.onshell(m, wl.x0, wl.d)
     xstar = wl.x0 + 0.05
@@ -46,11 +71,11 @@ def _grad_of_rays(idx):
     return O.loss_grad(r.y, xstar[idx], S)
 
 
-def _worker(rank, world, port, out):
+def _worker(rank, world, port, out, scaling="strong"):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     torch.distributed.init_process_group("gloo", rank=rank, world_size=world)
-    lo, hi = shard_bounds(24, rank, world)
-    g = torch.tensor(_grad_of_rays(np.arange(lo, hi)))
+    seed_shard, lo, hi = ray_share(scaling, 24, rank, world)
+    g = torch.tensor(_grad_of_rays(np.arange(lo, hi), seed_shard))
     allreduce_gradient(g)
     t = max_over_ranks(0.5 + rank)
     out[rank] = (g.numpy(), t)
@@ -68,6 +93,19 @@ def test_data_parallel_adjoint_gradient_gloo_world2():
         g, t = res[rank]
         np.testing.assert_allclose(g, full, rtol=1e-12, atol=1e-15)
         assert t == 1.5
+
+
+def test_weak_scaling_adjoint_gradient_gloo_world2():
+    """Every rank its own rays (seed shard = rank): the all-reduced gradient is
+    the gradient of the sum of both ranks' losses."""
+    world = 2
+    with mp.Manager() as mgr:
+        out = mgr.dict()
+        mp.spawn(_worker, args=(world, _free_port(), out, "weak"), nprocs=world, join=True)
+        res = dict(out)
+    total = _grad_of_rays(np.arange(24), 0) + _grad_of_rays(np.arange(24), 1)
+    for rank in range(world):
+        np.testing.assert_allclose(res[rank][0], total, rtol=1e-12, atol=1e-15)
 
 
 def test_shard_media_partition_and_balance():
@@ -105,7 +143,7 @@ def _media_worker(rank, world, port, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     torch.distributed.init_process_group("gloo", rank=rank, world_size=world)
     wl, om, off, k0, ctl = _batch_case()
-    m_lo, m_hi = shard_media(off, rank, world)
+    _, m_lo, m_hi = media_share("strong", off, rank, world)
     lo, hi = int(off[m_lo]), int(off[m_hi])
     r = O.make_rays(wl.x0[lo:hi], k0[lo:hi])
     O.trace_dopri5(om[m_lo:m_hi], np.asarray(off[m_lo:m_hi + 1]) - lo, r, 1.0, **ctl)
