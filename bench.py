@@ -62,6 +62,12 @@ def parse():
     ap.add_argument("--media", type=int, default=4096, help="batched: number of media")
     ap.add_argument("--tune-cache", default=None,
                     help="batched: autotuner cache file (written after tuning, reused when it holds the shape)")
+    ap.add_argument("--scaling", choices=["weak", "strong"], default="weak",
+                    help="N > 1: weak = every rank its own batch of the workload's size; strong = one "
+                         "batch split across the ranks (grin, batched, adjoint)")
+    ap.add_argument("--drawn-order", action="store_true",
+                    help="batched, adjoint: rays in the order drawn, not sorted along a Morton curve of "
+                         "their launch points")
     return ap.parse_args()
 
 
@@ -112,6 +118,25 @@ class ClockSampler:
 
 # --------------------------------------------------------------------------- oracle leg
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:  # noqa: BLE001 -- a report field
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def oracle_throughput(wl, n_rays: int) -> dict:
     """Plain FP64 oracle on the first n_rays rays of the workload (host cores)."""
     import oracle as O
@@ -122,7 +147,8 @@ def oracle_throughput(wl, n_rays: int) -> dict:
     O.trace_rk4(m, r, wl.omega, wl.dt, wl.n_steps)
     el = time.perf_counter() - t0
     units = int(r.steps.astype(np.int64).sum())
-    return {"value": units / el, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+    return {"value": units / el, "unit": UNIT, "cores": O.num_threads(), "cpu_model": cpu_model(),
+            "kind": "oracle",
             "sample": f"{n_rays} rays x {wl.n_steps} RK4 steps of the same workload "
                       f"({units} ray-steps, {el:.1f} s)", "seconds": el}
 
@@ -191,7 +217,8 @@ def oracle_sample(name: str) -> dict:
         else:
             what = f"{n} rays x {wl.n_steps} RK4 steps" + (f", {reps} times" if reps > 1 else "")
             unit = UNIT
-    return {"value": units / el, "unit": unit, "cores": O.num_threads(), "kind": "oracle",
+    return {"value": units / el, "unit": unit, "cores": O.num_threads(), "cpu_model": cpu_model(),
+            "kind": "oracle",
             "sample": f"{what}: {units} units in {el:.2f} s (a sample of the same workload)"}
 
 
@@ -224,8 +251,8 @@ def run_reference(a):
             "data": "synthetic",
             "config": {"workload": f"grin_fibre_16_blobs rays={a.cpu_rays} (sample of {a.rays}) "
                                    f"rk4_steps={a.nsteps} dt=5e-4", "parallelism": "host cores"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
-                             "sample": r["sample"]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": r["cores"], "cpu_model": r["cpu_model"],
+                             "kind": "oracle", "sample": r["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -257,18 +284,62 @@ def algorithmic_flops(evals: int, live: int, n_blobs: int, ray_steps: int) -> in
     return FLOPS_LIVE_TERM * live + FLOPS_CULLED_TERM * culled + FLOPS_EVAL * evals + FLOPS_STEP * ray_steps
 
 
-def measure_batched(gf, torch, tune_cache: str | None = None, n_media: int = 4096) -> dict:
-    """Batched DOPRI5 workload (4096 Luneburg + 8-blob media, ~12.56M rays,
-    rtol = atol = 1e-9, exit at r = 1.5): persistent work-stealing graph launch
-    vs one launch per medium (also a graph), each timed once after a warm-up."""
-    wl = W.batched(n_media=n_media)
-    blobs, off = wl.extra["blobs"], wl.extra["offsets"]
-    media = [gf.gf_medium_create("luneburg", blobs=blobs[j]) for j in range(len(off) - 1)]
-    batch = gf.gf_batch_create(media, off)
+# Per-unit algorithmic counts from the workload descriptions (FP64 flops, fma = 2;
+# exponentials and divisions are not counted, every blob term is charged whether
+# or not the kernel culls it).  These give each roofline's primary fraction; the
+# counted-work model above (live and culled terms from the kernel's counters)
+# is reported beside the headline's.
+#   GRIN + 16 blobs, per ray-step: 4 evaluations x (16 blob terms x 18 + index
+#     law 6 + right-hand side 8) + RK4 combination 84
+#   batched DOPRI5, 8 blobs, per attempted step (accepted or rejected):
+#     6 evaluations x (8 x 18 + 13) + stage combination and error norm 150
+#   adjoint medium, 64 blobs, per ray-step of a forward trace: 4 x (64 x 18 + 14) + 84
+#   cold plasma, two species, per ray-step, counted from the evaluator: per
+#     species 49 flops (and a reciprocal), D, its partials and f 83 (and a
+#     reciprocal; D formed at every evaluation), stage update 24, RK4 18
+MODEL_GRIN_RAY_STEP = 4 * (16 * 18 + 6 + 8) + 84
+MODEL_DOPRI5_ATTEMPT = 6 * (8 * 18 + 13) + 150
+MODEL_ADJ_FWD_RAY_STEP = 4 * (64 * 18 + 6 + 8) + 84
+MODEL_COLD_RAY_STEP = 4 * (2 * 49 + 83 + 24) + 18
+#   adjoint backward, per ray-step: the forward recomputation (as above) and the
+#     vector-Jacobian product of each of the 4 stages: per blob term 27 (x - c 3,
+#     (x - c).Kbar 5, the theta-bar update 5, the Hessian-vector term 14), per
+#     stage 50 (Kbar, the quotient-rule scalar, base Hessian, ybar), lambda 6
+MODEL_ADJ_BWD_RAY_STEP = MODEL_ADJ_FWD_RAY_STEP + 4 * (64 * 27 + 50) + 6
+MODEL_TEXT = {
+    "grin": f"{MODEL_GRIN_RAY_STEP} flops per ray-step: 4 evaluations x (16 blob terms x 18 + index law 6 + "
+            "right-hand side 8) + RK4 combination 84; exponentials and divisions not counted",
+    "dopri5": f"{MODEL_DOPRI5_ATTEMPT} flops per attempted step: 6 evaluations x (8 blob terms x 18 + 13) "
+              "+ stage combination and error norm 150; exponentials and divisions not counted",
+    "adj_fwd": f"{MODEL_ADJ_FWD_RAY_STEP} flops per ray-step: 4 evaluations x (64 blob terms x 18 + 14) + 84",
+    "adj_bwd": f"{MODEL_ADJ_BWD_RAY_STEP} flops per ray-step: recomputation {MODEL_ADJ_FWD_RAY_STEP} + 4 stages x "
+               "(64 blob terms x 27 + 50) + 6 for the vector-Jacobian products; exponentials not counted",
+    "cold": f"{MODEL_COLD_RAY_STEP} flops per ray-step: 4 evaluations x (2 species x 49 + D and partials 83 + "
+            "stage update 24) + 18; reciprocals not counted",
+}
+
+
+def fp64_peak_tflops(sm_mhz: float) -> float:
+    """Non-tensor FP64 peak from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flops."""
+    return SMS * 2 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def fp32_peak_tflops(sm_mhz: float) -> float:
+    """Non-tensor FP32 peak: 152 SMs x 128 FFMA/clk x 2 flops."""
+    return SMS * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def roofline_of(flops: float, seconds: float, peak: float) -> dict:
+    a = flops / seconds / 1e12
+    return {"achieved_tflops": a, "frac": a / peak}
+
+
+def _batch_rays(gf, torch, wl, media, off):
+    """Device rays of a batch with k set on shell per medium (gf_rays_onshell)."""
     init = gf.Rays.from_numpy(wl.x0, None)
     dirs = torch.from_numpy(np.ascontiguousarray(wl.d.T)).cuda()
     stream = torch.cuda.current_stream().cuda_stream
-    for j, m in enumerate(media):                      # on-shell k per medium
+    for j, m in enumerate(media):
         lo, hi = int(off[j]), int(off[j + 1])
         if hi > lo:
             s = gf.GfRays(hi - lo, init.y.stride(0), init.y.data_ptr() + 8 * lo, init.t.data_ptr() + 8 * lo,
@@ -276,6 +347,28 @@ def measure_batched(gf, torch, tune_cache: str | None = None, n_media: int = 409
                           init.d_res.data_ptr() + 8 * lo, init.d_max.data_ptr() + 8 * lo)
             gf._check("gf_rays_onshell", gf.lib().gf_rays_onshell(m.handle, gf.GF_F64, gf.C.byref(s),
                                                                   dirs.data_ptr() + 8 * lo, 1.0, stream))
+    return init
+
+
+def measure_batched(gf, torch, tune_cache: str | None = None, n_media: int = 4096, peak: float | None = None,
+                    morton: bool = True, shard: int = 0, media_range: tuple[int, int] | None = None,
+                    full: bool = True, barrier=None) -> dict:
+    """Batched DOPRI5 workload (4096 Luneburg + 8-blob media, ~12.56M rays,
+    rtol = atol = 1e-9, exit at r = 1.5): persistent work-stealing graph launch
+    vs one launch per medium (also a graph) and the persistent launch in
+    GF_F64X, each timed once after a warm-up.  media_range = (m_lo, m_hi)
+    traces only those media (a strong-scaling shard); full = False times the
+    persistent launch alone."""
+    peak = fp64_peak_tflops(2070.0) if peak is None else peak
+    wl = W.batched(n_media=n_media, morton=morton, shard=shard)
+    blobs, off = wl.extra["blobs"], wl.extra["offsets"]
+    m_lo, m_hi = (0, len(off) - 1) if media_range is None else media_range
+    sub_off = np.asarray(off[m_lo:m_hi + 1]) - int(off[m_lo])
+    r_lo, r_hi = int(off[m_lo]), int(off[m_hi])
+    wl.x0, wl.d = wl.x0[r_lo:r_hi], wl.d[r_lo:r_hi]
+    media = [gf.gf_medium_create("luneburg", blobs=blobs[j]) for j in range(m_lo, m_hi)]
+    batch = gf.gf_batch_create(media, sub_off)
+    init = _batch_rays(gf, torch, wl, media, sub_off)
     e = wl.extra
     ctl = gf.step_ctl(rtol=e["rtol"], atol=e["atol"], h0=e["h0"], t_max=e["t_max"], radius=wl.radius,
                       max_steps=e["max_steps"])
@@ -284,13 +377,15 @@ def measure_batched(gf, torch, tune_cache: str | None = None, n_media: int = 409
     tune_s = time.perf_counter() - t0
     rays = init.clone()
     rej = torch.zeros(rays.n, dtype=torch.int32, device="cuda")
-    out = {}
-    for name, sched in (("persistent", gf.GF_SCHED_PERSISTENT), ("per_medium", gf.GF_SCHED_PER_MEDIUM)):
+
+    def timed(sched):
         ms = []
-        for _ in range(2):                             # warm-up (graph capture), then timed
+        for it in range(2):                            # warm-up (graph capture), then timed
             for src, dst in zip((init.y, init.t, init.status, init.steps, init.d_max),
                                 (rays.y, rays.t, rays.status, rays.steps, rays.d_max)):
                 dst.copy_(src)
+            if it == 1 and barrier is not None:
+                barrier()
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             ev0.record()
             gf.gf_trace_dopri5(batch, rays, rej, 1.0, ctl, sched, None)
@@ -298,32 +393,26 @@ def measure_batched(gf, torch, tune_cache: str | None = None, n_media: int = 409
             torch.cuda.synchronize()
             ms.append(ev0.elapsed_time(ev1))
         steps = int(rays.steps.to(torch.int64).sum().item())
-        out[name] = {"ms": ms[-1], "accepted_ray_steps": steps,
-                     "rejected": int(rej.to(torch.int64).sum().item()),
-                     "ray_steps_per_s": steps / (ms[-1] / 1e3)}
-    # the same batch with double-float blob sums (GF_F64X), tuned for that mode
-    gf.gf_batch_set_precision(batch, gf.GF_F64X)
-    gf.gf_dopri5_autotune(batch, init, 1.0, ctl, None)
-    ms = []
-    for _ in range(2):
-        for src, dst in zip((init.y, init.t, init.status, init.steps, init.d_max),
-                            (rays.y, rays.t, rays.status, rays.steps, rays.d_max)):
-            dst.copy_(src)
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record()
-        gf.gf_trace_dopri5(batch, rays, rej, 1.0, ctl, gf.GF_SCHED_PERSISTENT, None)
-        ev1.record()
-        torch.cuda.synchronize()
-        ms.append(ev0.elapsed_time(ev1))
-    steps = int(rays.steps.to(torch.int64).sum().item())
-    out["persistent_f64x"] = {"ms": ms[-1], "accepted_ray_steps": steps,
-                              "rejected": int(rej.to(torch.int64).sum().item()),
-                              "ray_steps_per_s": steps / (ms[-1] / 1e3)}
-    gf.gf_batch_set_precision(batch, gf.GF_F64)
-    return {"workload": f"{n_media} Luneburg+8-blob media, {wl.n} rays, DOPRI5 rtol=atol=1e-9, exit r=1.5",
-            "persistent": out["persistent"], "per_medium": out["per_medium"],
-            "persistent_f64x": out["persistent_f64x"],
-            "speedup_persistent_vs_per_medium": out["per_medium"]["ms"] / out["persistent"]["ms"],
+        rejected = int(rej.to(torch.int64).sum().item())
+        return {"ms": ms[-1], "accepted_ray_steps": steps, "rejected": rejected,
+                "ray_steps_per_s": steps / (ms[-1] / 1e3),
+                **roofline_of(MODEL_DOPRI5_ATTEMPT * (steps + rejected), ms[-1] / 1e3, peak)}
+
+    out = {"persistent": timed(gf.GF_SCHED_PERSISTENT)}
+    if full:
+        out["per_medium"] = timed(gf.GF_SCHED_PER_MEDIUM)
+        # the same batch with double-float blob sums (GF_F64X), tuned for that mode
+        gf.gf_batch_set_precision(batch, gf.GF_F64X)
+        gf.gf_dopri5_autotune(batch, init, 1.0, ctl, None)
+        out["persistent_f64x"] = timed(gf.GF_SCHED_PERSISTENT)
+        out["persistent_f64x"]["note"] = ("GF_F64X: double state and controller, double-float blob sums on "
+                                          "the FP32 pipes; the fraction is of the FP64 peak")
+        gf.gf_batch_set_precision(batch, gf.GF_F64)
+        out["speedup_persistent_vs_per_medium"] = out["per_medium"]["ms"] / out["persistent"]["ms"]
+    order = "Morton order per medium" if morton else "drawn order"
+    return {"workload": f"{m_hi - m_lo} Luneburg+8-blob media, {wl.n} rays ({order}), DOPRI5 rtol=atol=1e-9, "
+                        f"exit r=1.5",
+            **out, "roofline_model": MODEL_TEXT["dopri5"], "peak_tflops": peak,
             "tune": {"block": tune.block, "rays_per_thread": tune.rays_per_thread,
                      "compaction": tune.compaction, "chunk": tune.chunk, "seconds": tune_s}}
 
@@ -385,7 +474,7 @@ def measure_luneburg(gf, torch) -> dict:
             "ms": t, "ray_steps_per_s": wl.n * wl.n_steps / (t / 1e3), "us_per_step": 1e3 * t / wl.n_steps}
 
 
-def measure_cold(gf, torch) -> dict:
+def measure_cold(gf, torch, peak: float | None = None) -> dict:
     """Cold-plasma workload (1,048,576 rays in the magnetised slab of Sec. 4.1
     with the Eq. 4 density gradient, O branch, RK4 dt = 1e-2 x 1500, FP64),
     the counterpart of the paper's own benchmark (1e6 cold-plasma rays, timed
@@ -406,9 +495,12 @@ def measure_cold(gf, torch) -> dict:
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
     units = int(rays.steps.to(torch.int64).sum().item())
+    peak = fp64_peak_tflops(2070.0) if peak is None else peak
     return {"workload": f"{wl.n} rays, cold plasma slab (electrons + ions, f = 1 + 0.1 x), O branch, "
                         f"RK4 dt={wl.dt} x {wl.n_steps}, FP64",
-            "ms": ms[-1], "ray_steps_per_s": units / (ms[-1] / 1e3), "newton_converged": ok,
+            "ms": ms[-1], "ray_steps_per_s": units / (ms[-1] / 1e3),
+            **roofline_of(MODEL_COLD_RAY_STEP * units, ms[-1] / 1e3, peak),
+            "roofline_model": MODEL_TEXT["cold"], "peak_tflops": peak, "newton_converged": ok,
             "reflected": int(((rays.y[3] < 0) & (init.status == 0)).sum().item()),
             "max_abs_D": rays.d_max[init.status == 0].max().item()}
 
@@ -432,6 +524,50 @@ def measure_f64x(gf, torch, wl, m, x0, dirs, rays) -> dict:
     return {"ray_steps_per_s": units / (ms[-1] / 1e3), "ms": ms[-1], "max_abs_D": rays.d_max.max().item(),
             "dtype": "f64 state and integrator, f32x2 (double-float) blob sums",
             "parity": "<= 1e-9 relative to the FP64 oracle in tests/test_gpu_f64x.py"}
+
+
+def measure_f32(gf, torch, wl, m, peak32: float) -> dict:
+    """The headline workload on the FP32 path (FP32 state with Kahan-compensated
+    updates, FP32 blob sums with the hardware base-2 exponential): one warm-up
+    and one timed trace, then an untimed pass with work counters; rooflines
+    against the FP32 non-tensor peak."""
+    x0 = torch.from_numpy(np.ascontiguousarray(wl.x0.T)).to("cuda", torch.float32)
+    dirs = torch.from_numpy(np.ascontiguousarray(wl.d.T)).to("cuda", torch.float32)
+    rays = gf.Rays.empty(wl.n, torch.float32)
+
+    def trace(counters=None):
+        rays.y[:3].copy_(x0)
+        for t in (rays.t, rays.status, rays.steps, rays.d_max):
+            t.zero_()
+        gf.gf_rays_onshell(m, rays, dirs, wl.omega)
+        if counters is not None:
+            gf.gf_bench_set_counters(counters)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        gf.gf_trace_rk4(m, rays, wl.omega, wl.dt, wl.n_steps)
+        e1.record()
+        torch.cuda.synchronize()
+        if counters is not None:
+            gf.gf_bench_set_counters(None)
+        return e0.elapsed_time(e1)
+
+    trace()
+    ms = trace()
+    units = int(rays.steps.to(torch.int64).sum().item())
+    counters = torch.zeros(2, dtype=torch.int64, device="cuda")
+    trace(counters)
+    evals, live = (int(v) for v in counters.tolist())
+    counted = algorithmic_flops(evals, live, wl.medium["blobs"].shape[0], units)
+    return {"workload": f"grin_fibre_16_blobs rays={wl.n} rk4_steps={wl.n_steps} dt={wl.dt}, FP32",
+            "dtype": "f32", "ms": ms, "ray_steps_per_s": units / (ms / 1e3),
+            "roofline": {"bound": "alu", "unit": "TFLOP/s", "peak": peak32,
+                         **roofline_of(MODEL_GRIN_RAY_STEP * units, ms / 1e3, peak32),
+                         "model": MODEL_TEXT["grin"],
+                         "counted_work": roofline_of(counted, ms / 1e3, peak32),
+                         "peak_basis": "152 SM x 128 FFMA/clk x 2 flop at the sampled clock"},
+            "max_abs_D": rays.d_max.max().item(),
+            "parity": "<= 1e-4 relative to the FP64 oracle on the same FP32-rounded launch states "
+                      "(tests/test_gpu_rk4.py)"}
 
 
 def measure_generated(gf, torch, n_rays: int, n_steps: int) -> dict:
@@ -465,12 +601,20 @@ def measure_generated(gf, torch, n_rays: int, n_steps: int) -> dict:
             "max_abs_state_difference": dev}
 
 
-def measure_adjoint(gf, torch, n: int | None = None, n_steps: int | None = None) -> dict:
+def measure_adjoint(gf, torch, n: int | None = None, n_steps: int | None = None, peak: float | None = None,
+                    morton: bool = True, shard: int = 0, ray_range: tuple[int, int] | None = None,
+                    allreduce=None, barrier=None) -> dict:
     """Adjoint workload (65,536 rays, Luneburg + 64 blobs, RK4 dt 1e-3 x 4000,
     checkpoints every 64; n and n_steps shrink it): forward with checkpoints
     and backward through the autograd Function, plus a plain forward, each
-    timed after a warm-up."""
-    wl = W.adjoint(**({} if n is None else {"n": n}), **({} if n_steps is None else {"n_steps": n_steps}))
+    timed after a warm-up.  ray_range = (lo, hi) traces only those rays (a
+    strong-scaling shard); allreduce(grad) sums the parameter gradient over
+    the ranks inside the timed backward."""
+    peak = fp64_peak_tflops(2070.0) if peak is None else peak
+    wl = W.adjoint(**({} if n is None else {"n": n}), **({} if n_steps is None else {"n_steps": n_steps}),
+                   morton=morton, shard=shard)
+    if ray_range is not None:
+        wl.x0, wl.d = wl.x0[ray_range[0]:ray_range[1]], wl.d[ray_range[0]:ray_range[1]]
     m = gf.gf_medium_create(**wl.medium)
     init = gf.Rays.empty(wl.n)
     init.y[:3].copy_(torch.from_numpy(np.ascontiguousarray(wl.x0.T)).cuda())
@@ -484,32 +628,66 @@ def measure_adjoint(gf, torch, n: int | None = None, n_steps: int | None = None)
     xstar = star.y[:3].clone()
     theta = torch.tensor(wl.extra["theta"], device="cuda", requires_grad=True)
     gf.gf_medium_set_amplitudes(m, theta.detach())
+    every = wl.extra["checkpoint_every"]
     ev = lambda: torch.cuda.Event(enable_timing=True)
     res = {}
-    for _ in range(2):
+    for it in range(2):
+        if it == 1 and barrier is not None:
+            barrier()
         e0, e1, e2, e3, e4 = ev(), ev(), ev(), ev(), ev()
         e0.record()
         plain = gf.Rays.empty(wl.n, diagnostics=False)
         plain.y.copy_(y0)
         gf.gf_trace_rk4(m, plain, 1.0, wl.dt, wl.n_steps)
         e1.record()
-        yN = gf.trace_rk4_autograd(m, theta, y0, 1.0, wl.dt, wl.n_steps, wl.extra["checkpoint_every"])
+        yN = gf.trace_rk4_autograd(m, theta, y0, 1.0, wl.dt, wl.n_steps, every)
         e2.record()
         loss = ((yN[:3] - xstar) ** 2).sum()
         e3.record()
         loss.backward()
+        if allreduce is not None:
+            allreduce(theta.grad)
         e4.record()
         torch.cuda.synchronize()
         res = {"plain_forward_ms": e0.elapsed_time(e1), "forward_ckpt_ms": e1.elapsed_time(e2),
                "backward_ms": e3.elapsed_time(e4)}
+        grad = theta.grad.clone()
         theta.grad = None
     res["backward_over_forward"] = res["backward_ms"] / res["forward_ckpt_ms"]
     res["total_over_plain_forward"] = (res["forward_ckpt_ms"] + res["backward_ms"]) / res["plain_forward_ms"]
     # the gradient's throughput: ray-steps of the trace per second of forward + backward
-    res["gradient_ray_steps_per_s"] = wl.n * wl.n_steps / ((res["forward_ckpt_ms"] + res["backward_ms"]) / 1e3)
+    units = wl.n * wl.n_steps
+    res["gradient_ray_steps_per_s"] = units / ((res["forward_ckpt_ms"] + res["backward_ms"]) / 1e3)
+    res["roofline"] = {
+        "forward": roofline_of(MODEL_ADJ_FWD_RAY_STEP * units, res["plain_forward_ms"] / 1e3, peak),
+        "forward_ckpt": roofline_of(MODEL_ADJ_FWD_RAY_STEP * units, res["forward_ckpt_ms"] / 1e3, peak),
+        # the backward's FP64 work is the recomputation (the forward's flops); its reverse sweep
+        # (vector-Jacobian products, MODEL_ADJ_BWD_RAY_STEP - MODEL_ADJ_FWD_RAY_STEP flops per
+        # ray-step algorithmically) runs in double-float on the FP32 pipes
+        "backward_fp64_recomputation": roofline_of(MODEL_ADJ_FWD_RAY_STEP * units, res["backward_ms"] / 1e3, peak),
+        "model": {"forward": MODEL_TEXT["adj_fwd"], "backward": MODEL_TEXT["adj_bwd"]},
+        "peak_tflops": peak}
+    # untimed backward with work counters: recomputed evaluations and blob terms, swept blob
+    # terms, and recomputed segment ends that differ from the forward trace's checkpoints
+    yN = gf.trace_rk4_autograd(m, theta, y0, 1.0, wl.dt, wl.n_steps, every)
+    counters = torch.zeros(4, dtype=torch.int64, device="cuda")
+    gf.gf_bench_set_counters(counters)
+    try:
+        ((yN[:3] - xstar) ** 2).sum().backward()
+        torch.cuda.synchronize()
+    finally:
+        gf.gf_bench_set_counters(None)
+    c = [int(v) for v in counters.tolist()]
+    theta.grad = None
+    res["backward_work"] = {"recomputed_evaluations": c[0], "recomputed_blob_terms": c[1],
+                            "swept_blob_terms": c[2], "segment_ends_differing_from_checkpoints": c[3],
+                            "note": "the sweep's blob terms run in double-float on the FP32 pipes"}
+    res["scratch_bytes"] = gf.gf_adjoint_scratch_bytes(m, wl.n, every)
     res["loss"] = loss.item()
-    res["workload"] = (f"{wl.n} rays, Luneburg + {len(wl.extra['theta'])} blobs, RK4 dt={wl.dt} x {wl.n_steps}, "
-                       f"checkpoint every {wl.extra['checkpoint_every']}")
+    res["grad_norm"] = float(grad.norm().item())
+    order = "Morton order" if morton else "drawn order"
+    res["workload"] = (f"{wl.n} rays ({order}), Luneburg + {len(wl.extra['theta'])} blobs, RK4 dt={wl.dt} x "
+                       f"{wl.n_steps}, checkpoint every {every}")
     return res
 
 
@@ -531,7 +709,10 @@ def run_gpu(a):
 
     dtype = torch.float32 if a.precision == "f32" else torch.float64
     prec = {"f64": gf.GF_F64, "f32": gf.GF_F32, "f64x": gf.GF_F64X}[a.precision]
-    wl = W.grin(n=a.rays, n_steps=a.nsteps, shard=rank)
+    from paper_2508_15967_gb300.shard import ray_share
+    seed_shard, r_lo, r_hi = ray_share(a.scaling, a.rays, rank, world)
+    wl = W.grin(n=a.rays, n_steps=a.nsteps, shard=seed_shard)
+    wl.x0, wl.d = wl.x0[r_lo:r_hi], wl.d[r_lo:r_hi]
     m = gf.gf_medium_create(**wl.medium)
     x0 = torch.from_numpy(np.ascontiguousarray(wl.x0.T)).to("cuda", dtype)
     dirs = torch.from_numpy(np.ascontiguousarray(wl.d.T)).to("cuda", dtype)
@@ -628,13 +809,16 @@ def run_gpu(a):
     evals, live = (int(v) for v in counters.tolist())
     n_blobs = wl.medium["blobs"].shape[0]
     flops = algorithmic_flops(evals, live, n_blobs, units)
+    model_flops = MODEL_GRIN_RAY_STEP * units
     k_sec = statistics.mean(kern_ms) / 1e3
-    achieved = flops / k_sec / 1e12
+    achieved = model_flops / k_sec / 1e12
+    achieved_counted = flops / k_sec / 1e12
     sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
     # non-tensor peaks from unit counts and clock: 152 SMs x 2 DFMA/clk (FP64) or
     # 128 FFMA/clk (FP32) x 2 flops
-    peak64 = SMS * 2 * 2 * sm_mhz * 1e6 / 1e12
-    peak = peak64 if dtype == torch.float64 else SMS * 128 * 2 * sm_mhz * 1e6 / 1e12
+    peak64 = fp64_peak_tflops(sm_mhz)
+    peak32 = fp32_peak_tflops(sm_mhz)
+    peak = peak64 if dtype == torch.float64 else peak32
     basis = (f"152 SM x 2 DFMA/clk x 2 flop x {sm_mhz:.0f} MHz (sampled)" if dtype == torch.float64
              else f"152 SM x 128 FFMA/clk x 2 flop x {sm_mhz:.0f} MHz (sampled)")
     kname = {"f64": "rk4_kernel<double, GRIN>", "f32": "rk4_kernel<float, GRIN>",
@@ -644,17 +828,23 @@ def run_gpu(a):
     line = {
         "metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": 1e3 * t_max / a.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+        "scaling": a.scaling, "vs_baseline": None,
         "dtype": {"f64": "f64", "f32": "f32", "f64x": "f64 state, f32x2 blob sums"}[a.precision],
         "data": "synthetic",
-        "config": {"workload": f"grin_fibre_16_blobs rays={wl.n} rk4_steps={wl.n_steps} dt={wl.dt}",
-                   "rays_per_gpu": wl.n, "rk4_steps": wl.n_steps, "parallelism": f"ray shards x{world}",
+        "config": {"workload": f"grin_fibre_16_blobs rays={a.rays} rk4_steps={wl.n_steps} dt={wl.dt}",
+                   "rays_per_gpu": wl.n, "rk4_steps": wl.n_steps,
+                   "parallelism": f"ray shards x{world} ({a.scaling} scaling)",
                    "l2": "256 MiB buffer written between timed steps"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak,
+                     "frac": achieved / peak, "model": MODEL_TEXT["grin"],
+                     "flops_per_launch": model_flops,
                      "traffic": TRAFFIC_BYTES_1M if (wl.n == 1 << 20 and a.precision == "f64") else None,
                      "kernel": kname, "kernel_ms": 1e3 * k_sec,
-                     "flops_per_launch": flops, "evaluations": evals, "blob_terms_live": live,
+                     "counted_work": {"achieved": achieved_counted, "frac": achieved_counted / peak,
+                                      "flops_per_launch": flops,
+                                      "model": "live blob term 26 (8-flop table exponential), culled term 9, "
+                                               "evaluation 51, ray-step 18, from the kernel's work counters"},
+                     "evaluations": evals, "blob_terms_live": live,
                      "blob_terms_total": evals * n_blobs,
                      "peak_basis": basis,
                      "fma_peak_measured_tflops": {"f64": fma64, "f32": fma32}},
@@ -666,11 +856,12 @@ def run_gpu(a):
     if world == 1 and not a.no_extras:
         if a.precision == "f64":
             line["f64x"] = measure_f64x(gf, torch, wl, m, x0, dirs, rays)
+            line["f32"] = measure_f32(gf, torch, wl, m, peak32)
         line["luneburg"] = measure_luneburg(gf, torch)
-        line["cold"] = measure_cold(gf, torch)
+        line["cold"] = measure_cold(gf, torch, peak64)
         line["aniso"] = measure_aniso(gf, torch, peak64)
-        line["adjoint"] = measure_adjoint(gf, torch)
-        line["batched"] = measure_batched(gf, torch)
+        line["adjoint"] = measure_adjoint(gf, torch, peak=peak64)
+        line["batched"] = measure_batched(gf, torch, peak=peak64)
         if rank == 0 and not a.no_cpu_baseline:
             for name in ("luneburg", "cold", "aniso", "adjoint", "batched"):
                 _with_oracle(line[name], name)
@@ -685,29 +876,73 @@ def run_gpu(a):
 
 
 def run_workload(a):
-    """One secondary measurement alone (rank 0, one GPU), as a JSON line."""
+    """One secondary measurement as a JSON line.  batched and adjoint also run
+    data-parallel under torchrun (one rank per GPU): weak scaling gives every
+    rank its own batch of the workload's size, strong scaling splits one batch
+    (media balanced on ray counts, or ray ranges); the adjoint's one exchange
+    is the all-reduce of the parameter gradient (NCCL), inside the timed
+    backward; the job's time is the slowest rank's."""
     import torch
+    import torch.distributed as dist
     import paper_2508_15967_gb300 as gf
+    from paper_2508_15967_gb300.shard import allreduce_gradient, max_over_ranks, media_share, ray_share
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    sm = 2070.0
-    peak = SMS * 2 * 2 * sm * 1e6 / 1e12
+    if world > 1:
+        if a.workload not in ("batched", "adjoint"):
+            raise SystemExit(f"--workload {a.workload} runs on one GPU; batched and adjoint run data-parallel")
+        dist.init_process_group("nccl", device_id=torch.device("cuda", torch.cuda.current_device()))
+    barrier = (lambda: dist.barrier()) if world > 1 else None
+    peak = fp64_peak_tflops(2070.0)
+    morton = not a.drawn_order
     if a.workload == "batched":
-        res = measure_batched(gf, torch, tune_cache=a.tune_cache, n_media=a.media)
+        off = W.batched(n_media=a.media).extra["offsets"]
+        seed_shard, m_lo, m_hi = media_share(a.scaling, off, rank, world)
+        res = measure_batched(gf, torch, tune_cache=a.tune_cache, n_media=a.media, peak=peak, morton=morton,
+                              shard=seed_shard, media_range=(m_lo, m_hi), full=world == 1, barrier=barrier)
+        if world > 1:
+            p = res["persistent"]
+            t = max_over_ranks(p["ms"] / 1e3, "cuda")
+            tot = torch.tensor([p["accepted_ray_steps"], p["rejected"]], dtype=torch.int64, device="cuda")
+            dist.all_reduce(tot)
+            acc, rej = (int(v) for v in tot.tolist())
+            res = {"metric": "accepted ray-steps/s, batched DOPRI5 (persistent launch)",
+                   "value": acc / t, "unit": "accepted ray-steps/s", "n_gpus": world, "scaling": a.scaling,
+                   "ms": 1e3 * t, "accepted_ray_steps": acc, "rejected": rej,
+                   **roofline_of(MODEL_DOPRI5_ATTEMPT * (acc + rej), t, peak * world),
+                   "roofline_model": MODEL_TEXT["dopri5"], "rank0": res}
     elif a.workload == "luneburg":
         res = measure_luneburg(gf, torch)
     elif a.workload == "cold":
-        res = measure_cold(gf, torch)
+        res = measure_cold(gf, torch, peak)
     elif a.workload == "aniso":
         full = inspect.signature(W.aniso).parameters["n_steps"].default
         res = measure_aniso(gf, torch, peak, min(a.nsteps, full))
     elif a.workload == "adjoint":
         d = inspect.signature(W.adjoint).parameters
-        res = measure_adjoint(gf, torch, min(a.rays, d["n"].default), min(a.nsteps, d["n_steps"].default))
+        n = min(a.rays, d["n"].default)
+        seed_shard, lo, hi = ray_share(a.scaling, n, rank, world)
+        res = measure_adjoint(gf, torch, n, min(a.nsteps, d["n_steps"].default), peak=peak, morton=morton,
+                              shard=seed_shard, ray_range=(lo, hi),
+                              allreduce=allreduce_gradient if world > 1 else None, barrier=barrier)
+        if world > 1:
+            t = max_over_ranks((res["forward_ckpt_ms"] + res["backward_ms"]) / 1e3, "cuda")
+            units = torch.tensor([(hi - lo) * min(a.nsteps, d["n_steps"].default)], dtype=torch.int64,
+                                 device="cuda")
+            dist.all_reduce(units)
+            res = {"metric": "gradient ray-steps/s (forward with checkpoints + backward + gradient all-reduce)",
+                   "value": int(units.item()) / t, "unit": "gradient ray-steps/s", "n_gpus": world,
+                   "scaling": a.scaling, "ms": 1e3 * t, "rank0": res}
     else:
         res = measure_generated(gf, torch, min(a.rays, 1 << 18), min(a.nsteps, 2000))
-    if a.workload in ("luneburg", "cold", "aniso", "adjoint", "batched") and not a.no_cpu_baseline:
+    if world == 1 and a.workload in ("luneburg", "cold", "aniso", "adjoint", "batched") and not a.no_cpu_baseline:
         _with_oracle(res, a.workload)
-    print(json.dumps({"workload": a.workload, **res}), flush=True)
+    if rank == 0:
+        print(json.dumps({"workload": a.workload, **res}), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def main():

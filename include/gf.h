@@ -262,8 +262,10 @@ gf_status gf_jit_compile_check(const char *source, const char *arch, char *log, 
 /*
  * gf_adjoint_scratch_bytes -- bytes of device scratch gf_trace_adjoint needs
  * for n rays, the medium's blob count and segments of checkpoint_every steps:
- * 8 * (ceil(n/64) * n_blobs + checkpoint_every * 4 * (10 + n_blobs) * n) + 256.
- * Returns 0 for invalid arguments.
+ * 8 * (n_blobs * n + checkpoint_every * 4 * 10 * n) + 256 (the parameter
+ * gradient of every ray, then the point, n^2 and grad n^2 of every stage of
+ * one segment; 1.38 GB for 65,536 rays, 64 blobs and checkpoints every 64
+ * steps).  Returns 0 for invalid arguments.
  */
 size_t gf_adjoint_scratch_bytes(gf_medium m, int64_t n, int64_t checkpoint_every);
 
@@ -284,7 +286,12 @@ size_t gf_adjoint_scratch_bytes(gf_medium m, int64_t n, int64_t checkpoint_every
  * (device): dL_dtheta [n_blobs] doubles, overwritten; dL_dy0 [6][ld] or NULL.
  * scratch: device, >= gf_adjoint_scratch_bytes(m, n, checkpoint_every) bytes,
  * contents overwritten.  The medium must hold the amplitudes of the forward
- * trace.  Deterministic (fixed-order reductions).
+ * trace.  Each segment is recomputed from its checkpoint with the forward
+ * kernel's arithmetic (the recomputed states are the forward trace's bits);
+ * the blob terms of the reverse sweep are evaluated in double-float (float
+ * pairs, ~48-bit significands; relative error ~1e-14 in the derivative
+ * factors).  Deterministic (per-ray accumulators updated in program order,
+ * fixed-order reductions), and independent of checkpoint_every bit for bit.
  * Errors: GF_ERR_INVALID_ARG (no blobs, spline medium, bad sizes, small
  * scratch, non-device pointers), GF_ERR_CUDA.
  */
@@ -302,19 +309,24 @@ gf_status gf_trace_adjoint(gf_medium m, int64_t n, double omega, double dt, int6
  * timing, or a host code whose device memory is reserved up front by its own
  * pool.  The paper has no counterpart; this is a deployment variant.
  * Same arguments, layouts, result and errors as gf_trace_adjoint (identical
- * kernels, so identical results), except that the scratch is a fixed 64 MiB
- * device array inside the library: calls needing more than
- * gf_adjoint_scratch_bytes(m, n, checkpoint_every) <= 64 MiB (about 440 rays
- * with 64 blobs and checkpoints every 64 steps, 1,750 with checkpoints every
- * 16) fail with GF_ERR_INVALID_ARG before anything is enqueued.  The array is
- * held by every GPU on which the library's adjoint module is loaded, until
- * the process exits.  The first call on each device looks up the array's
- * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  All calls share the one array: calls whose work overlaps
- * on the GPU (different streams, or different threads on the same device)
- * race on it and must be serialised by the caller.  Nothing in the array
- * needs to start at zero: every word a call reads is written earlier in the
- * same call.
+ * kernels, so bit-identical results), except that the scratch is a fixed
+ * 64 MiB device array inside the library: calls needing more than
+ * gf_adjoint_scratch_bytes(m, n, checkpoint_every) <= 64 MiB (about 3,190
+ * rays with 64 blobs and checkpoints every 64 steps, 11,900 with checkpoints
+ * every 16) fail with GF_ERR_INVALID_ARG before anything is enqueued.  The
+ * array is held by every GPU on which the library's adjoint module is loaded,
+ * until the process exits.  Every call looks up the array's device address
+ * in the current context (cudaGetSymbolAddress; nothing is cached, so a
+ * context created anew after a device reset is handled).  Under CUDA's lazy
+ * module loading the first call on a device may itself load the module and
+ * map the 64 MiB, which can block or synchronise the device: make one
+ * warm-up call per device before the time-critical loop and before any
+ * stream capture (n = 0 serves: it loads the module, sets dL_dtheta to zero
+ * and launches nothing else).  All calls share the one array: calls whose
+ * work overlaps on the GPU (different streams, or different threads on the
+ * same device) race on it and must be serialised by the caller.  The call
+ * zeroes what must start at zero (the per-ray gradient accumulators) itself;
+ * every other word it reads is written earlier in the same call.
  */
 gf_status gf_trace_adjoint_static(gf_medium m, int64_t n, double omega, double dt, int64_t n_steps,
                                   int64_t checkpoint_every, const double *ckpt, const int32_t *steps_done,

@@ -28,11 +28,17 @@ gf_status gf_bench_fma_peak(gf_precision prec, int64_t iters, int32_t blocks_per
                             double *out_tflops, double *out_ms);
 
 /*
- * gf_bench_set_counters -- from the next launch on, gf_trace_rk4 kernels add
- * their work to counters[0] (right-hand-side evaluations) and counters[1]
- * (blob terms actually evaluated, i.e. not skipped as negligible), two device
- * unsigned 64-bit words owned by the caller; NULL turns counting off.  The
- * setting is process-wide and not thread-safe (a measurement aid).
+ * gf_bench_set_counters -- from the next launch on, kernels add their work
+ * to device unsigned 64-bit words owned by the caller; NULL turns counting
+ * off.  gf_trace_rk4 (two words): counters[0]
+ * right-hand-side evaluations, counters[1] blob terms actually evaluated
+ * (not skipped as negligible).  gf_trace_adjoint and gf_trace_adjoint_static
+ * (four words): counters[0] evaluations of the forward recomputation,
+ * counters[1] their blob terms, counters[2] blob terms of the reverse sweep,
+ * counters[3] recomputed segment-end states that differ in any bit from the
+ * next checkpoint of the forward trace (0 when the recomputation reproduces
+ * the forward trace).  The setting is process-wide and not thread-safe (a
+ * measurement aid).
  * Errors: GF_ERR_INVALID_ARG (not device memory).
  */
 gf_status gf_bench_set_counters(unsigned long long *counters);

@@ -15,33 +15,36 @@
 //     thetabar_j += G_j (C + 2 b s_j (x - c_j).Kbar_k),
 //     H Kbar_k = H_base Kbar_k + sum_j A_j G_j 2 s_j (2 s_j ((x - c_j).Kbar_k)(x - c_j) + Kbar_k).
 //
-// Checkpoints of the forward trace every E steps bound the memory: each
-// segment is recomputed forward from its checkpoint, storing for every step
-// and stage Y_i, n^2, g and all G_j in scratch, then swept in reverse without
-// re-evaluating any exponential.  Per-thread thetabar columns live in shared
-// memory and are reduced block -> grid in a fixed order (deterministic).
+// Checkpoints of the forward trace every E steps bound the memory.  Each
+// segment is recomputed forward from its checkpoint with the forward kernel's
+// own arithmetic (the same evaluator and the same explicitly rounded RK4
+// combination, so the recomputed states are the forward trace's bits: each
+// segment ends exactly on the next checkpoint, which the work counters
+// check), storing only every stage's point, n^2 and grad n^2.  The reverse
+// sweep then evaluates the Gaussians again, and with them the blob terms of
+// the vector-Jacobian product, in double-float arithmetic (float pairs,
+// ~48-bit significands) on the FP32 pipes, which the FP64-bound
+// recomputation leaves idle: the FP64 pipe carries only the per-stage
+// algebra.  The products enter the gradient and lambda as derivative factors
+// with ~1e-14 relative error, far inside the 1e-9 gradient gate; the
+// trajectory itself is the FP64 recomputation.  thetabar_j of every ray is
+// accumulated in a per-ray global array (L2-resident) with fire-and-forget
+// atomic adds -- one thread per address, so the adds apply in program order
+// and the sums are deterministic -- and reduced over rays in a fixed order.
 #include <cmath>
-#include <mutex>
 
-#include "gf_internal.cuh"
+#include "gf_dfloat.cuh"
 
 namespace gf {
 
-constexpr int kAdjBlock = 64;
-constexpr int kStageVals = 10;   // Y (6), n^2, g (3)
+constexpr int kAdjBlock = 128;
+constexpr int kStageVals = 10;   // Y (6), n^2, grad n^2 (3)
+constexpr int kSwRow = 12;       // sweep row: c (hi 3, lo 3), then the pairs of s/ln2, 2 s and 2 s A
 
 struct AdjScratch {
     double *tb;         // nb x n: thetabar_j of every ray, reduced over rays at the end
     double *stage;      // every x 4 x kStageVals x n
-    double *G;          // every x 4 x nb x n
 };
-
-template <int KIND>
-__device__ __forceinline__ void base_index(const MediumParams &m, const double *x, double &n2, double *g)
-{
-    EvalCtx<double> cx;
-    iso_index<double, KIND>(m, nullptr, 0, x, n2, g, cx);
-}
 
 // H_base v for the base index law (Luneburg inside / quadratic: -2 I; GRIN:
 // diag(0, -2c, -2c); homogeneous and Luneburg outside: 0).
@@ -50,8 +53,7 @@ __device__ __forceinline__ void base_hess_vec(const MediumParams &m, const doubl
                                               double *out)
 {
     if constexpr (KIND == K_LUNEBURG) {
-        const double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
-        const double h = r2 <= 1.0 ? -2.0 : 0.0;
+        const double h = norm2_fixed(x) <= 1.0 ? -2.0 : 0.0;
         out[0] = h * v[0];
         out[1] = h * v[1];
         out[2] = h * v[2];
@@ -68,36 +70,67 @@ __device__ __forceinline__ void base_hess_vec(const MediumParams &m, const doubl
     }
 }
 
-template <int KIND>
-// 7 resident blocks of 64 per SM (registers capped at 146): the 65,536-ray
-// adjoint workload (2,048 warps) is resident in one wave on 152 SMs.
-__global__ void __launch_bounds__(kAdjBlock, 7) adjoint_kernel(
-    const MediumParams m, const int64_t n, const double omega, const double dt, const int64_t n_steps,
-    const int64_t every, const double *__restrict__ ckpt, const int32_t *__restrict__ steps_done,
-    const double *__restrict__ lambda, const int64_t ld, double *__restrict__ dy0, const AdjScratch S)
+// Sweep rows in shared memory: the medium's double-float rows (c, s/ln2,
+// 2 s A) with the A pair replaced by 2 s, split from the plain FP64 rows.
+__device__ __forceinline__ void stage_sweep_rows(const MediumParams &m, float *sw)
 {
-    __shared__ double sb[kBlobStride * GF_MAX_BLOBS];    // plain rows (reverse sweep)
-    __shared__ double sbs[kBlobStride * GF_MAX_BLOBS];   // scaled rows (recompute)
-    __shared__ double sT[kExpTabN];
-    __shared__ float sp[4 * GF_MAX_BLOBS];               // FP32 pre-test rows (recompute)
-    const int nb = m.n_blobs;
-    for (int j = threadIdx.x; j < nb * kBlobStride; j += blockDim.x) {
-        sb[j] = m.blobs64[j];
-        sbs[j] = m.blobs64s[j];
+    for (int j = threadIdx.x; j < m.n_blobs; j += blockDim.x) {
+        const float *src = m.dfrows + kDfBlobStride * j;
+        float *dst = sw + kSwRow * j;
+        for (int f = 0; f < kSwRow; ++f) dst[f] = src[f];
+        const dfl t = df_from_double(m.blobs64[kBlobStride * j + 5]);   // 2 s
+        dst[8] = t.hi;
+        dst[9] = t.lo;
     }
-    for (int j = threadIdx.x; j < nb * 4; j += blockDim.x) sp[j] = m.pre32[j];
+}
+
+// Warp-aggregated add of per-thread counts to counters[0..3].
+__device__ __forceinline__ void add_adjoint_work(unsigned long long *counters, const long long *v)
+{
+    if (counters == nullptr) return;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        long long x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) == 0 && x != 0) atomicAdd(counters + k, (unsigned long long)x);
+    }
+}
+
+template <int KIND>
+// 4 resident blocks of 128 per SM (registers capped at 128): the 65,536-ray
+// adjoint workload (512 blocks) is resident in one wave on 152 SMs.
+__global__ void __launch_bounds__(kAdjBlock, 4) adjoint_kernel(
+    const MediumParams m, const int64_t n, const Omega<double> om, const double dt, const int64_t n_steps,
+    const int64_t every, const double *__restrict__ ckpt, const int32_t *__restrict__ steps_done,
+    const double *__restrict__ lambda, const int64_t ld, double *__restrict__ dy0, const AdjScratch S,
+    unsigned long long *counters)
+{
+    __shared__ double sbs[kBlobStride * GF_MAX_BLOBS];   // scaled FP64 rows (recomputation)
+    __shared__ double sT[kExpTabN];                      // 2^(j/2048) (recomputation)
+    __shared__ float sp[4 * GF_MAX_BLOBS];               // FP32 pre-test rows (recomputation)
+    __shared__ float sw[kSwRow * GF_MAX_BLOBS];          // double-float sweep rows
+    __shared__ float sdT[2 * kDfExpN];                   // double-float 2^(j/2048) (sweep)
+    const int nb = m.n_blobs;
+    stage_blobs<double>(m, sbs);
+    stage_pretest(m, sp);
     stage_exp_table(sT);
+    stage_sweep_rows(m, sw);
+    stage_dfexp_table(sdT);
     __syncthreads();
+    EvalCtx<double> cx;
+    cx.T = sT;
+    cx.pre = sp;
+    long long work[4] = {0, 0, 0, 0};   // recomputed evaluations, their blob terms, swept blob terms,
+                                        // segment ends that differ from the next checkpoint
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
-        double *acc_t = S.tb + i;   // thetabar_j of this ray at acc_t[j * n]
-        for (int j = 0; j < nb; ++j) acc_t[(int64_t)j * n] = 0.0;
+        double *acc_t = S.tb + i;   // thetabar_j of this ray at acc_t[j * n] (zeroed before the launch)
         const int sd = steps_done[i];
         double lam[6];
 #pragma unroll
         for (int c = 0; c < 6; ++c) lam[c] = lambda[c * ld + i];
-        const double aa[4] = {0.0, 0.5 * dt, 0.5 * dt, dt};
-        const double bb[4] = {dt / 6.0, dt / 3.0, dt / 3.0, dt / 6.0};
+        const double h2 = dt * 0.5, h6 = dt / 6.0, h3 = dt / 3.0;
         const int64_t nseg = (n_steps + every - 1) / every;
         for (int64_t seg = nseg - 1; seg >= 0; --seg) {
             const int64_t s0 = seg * every;
@@ -106,82 +139,91 @@ __global__ void __launch_bounds__(kAdjBlock, 7) adjoint_kernel(
             double y[6];
 #pragma unroll
             for (int c = 0; c < 6; ++c) y[c] = ckpt[(seg * 6 + c) * n + i];
-            // ---- forward recompute of the segment, storing every stage
+            // ---- forward recomputation of the segment (the forward kernel's step), storing every stage
             for (int s = 0; s < ns; ++s) {
-                double K[6], acc[6];
+                double K[6], acc[6], Y[6], D;
+                double *Ss = S.stage + ((int64_t)(s * 4) * kStageVals) * n + i;
 #pragma unroll
                 for (int st = 0; st < 4; ++st) {
-                    double Y[6];
+                    const double *P = st == 0 ? y : Y;
 #pragma unroll
-                    for (int c = 0; c < 6; ++c) Y[c] = st == 0 ? y[c] : y[c] + aa[st] * K[c];
-                    double n2, g[3];
-                    base_index<KIND>(m, Y, n2, g);
-                    // blob terms with the forward evaluator's arithmetic (scaled rows,
-                    // FP32 pre-test); negligible terms (see kBlobCull2) are stored as G = 0
-                    double *Gs = S.G + ((int64_t)(s * 4 + st) * nb) * n + i;
-                    const PreX px = pretest_point(m, Y);
-                    int live = 0;
-                    for (int j = 0; j < nb; ++j)
-                        Gs[(int64_t)j * n] = (px.on && pretest_negligible(sp + 4 * j, 1, px))
-                                                 ? 0.0
-                                                 : blob_term_scaled(sbs + kBlobStride * j, 1, Y, n2, g, sT, live);
-                    double *Ss = S.stage + ((int64_t)(s * 4 + st) * kStageVals) * n + i;
+                    for (int c = 0; c < 6; ++c) Ss[c * n] = P[c];
+                    double ng[4];
+                    rhs_iso<double, KIND, false>(m, sbs, nb, om, P, K, D, cx, 1, ng);
 #pragma unroll
-                    for (int c = 0; c < 6; ++c) Ss[c * n] = Y[c];
-                    Ss[6 * n] = n2;
-                    Ss[7 * n] = g[0];
-                    Ss[8 * n] = g[1];
-                    Ss[9 * n] = g[2];
-                    const double inv = recip_pos(n2);
-                    const double a = inv / omega, bq = 0.5 * omega * inv;
-                    K[0] = a * Y[3];
-                    K[1] = a * Y[4];
-                    K[2] = a * Y[5];
-                    K[3] = bq * g[0];
-                    K[4] = bq * g[1];
-                    K[5] = bq * g[2];
+                    for (int c = 0; c < 4; ++c) Ss[(6 + c) * n] = ng[c];
+                    Ss += (int64_t)kStageVals * n;
+                    if (st == 0) {
 #pragma unroll
-                    for (int c = 0; c < 6; ++c) acc[c] = st == 0 ? K[c] : (st == 3 ? acc[c] + K[c] : acc[c] + 2.0 * K[c]);
+                        for (int c = 0; c < 6; ++c) { acc[c] = K[c]; Y[c] = rk_axpy(h2, K[c], y[c]); }
+                    } else if (st < 3) {
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) {
+                            acc[c] = rk_acc2(acc[c], K[c]);
+                            Y[c] = rk_axpy(st == 1 ? h2 : dt, K[c], y[c]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) y[c] = __dadd_rn(y[c], rk_inc(h6, acc[c], K[c]));
+                    }
                 }
+            }
+            work[0] += 4 * (long long)ns;
+            if ((seg + 1) * every < sd) {   // the forward trace wrote the next checkpoint: same bits
 #pragma unroll
-                for (int c = 0; c < 6; ++c) y[c] = y[c] + (dt / 6.0) * acc[c];
+                for (int c = 0; c < 6; ++c)
+                    work[3] += __double_as_longlong(y[c]) != __double_as_longlong(ckpt[((seg + 1) * 6 + c) * n + i]);
             }
             // ---- reverse sweep over the segment
             for (int s = ns - 1; s >= 0; --s) {
                 double ybar_next[6] = {0, 0, 0, 0, 0, 0}, ysum[6] = {0, 0, 0, 0, 0, 0};
-#pragma unroll
+#pragma unroll 1
                 for (int st = 3; st >= 0; --st) {
+                    // Kbar_i = dt b_i lambda + dt a_{i+1} Ybar_{i+1}
+                    const double b_i = (st == 0 || st == 3) ? h6 : h3, a_next = st == 2 ? dt : h2;
                     double Kb[6];
 #pragma unroll
-                    for (int c = 0; c < 6; ++c) Kb[c] = bb[st] * lam[c] + (st < 3 ? aa[st + 1] * ybar_next[c] : 0.0);
+                    for (int c = 0; c < 6; ++c) Kb[c] = st < 3 ? fma(a_next, ybar_next[c], b_i * lam[c]) : b_i * lam[c];
                     const double *Ss = S.stage + ((int64_t)(s * 4 + st) * kStageVals) * n + i;
                     double Y[6];
 #pragma unroll
                     for (int c = 0; c < 6; ++c) Y[c] = Ss[c * n];
                     const double n2 = Ss[6 * n], g0 = Ss[7 * n], g1 = Ss[8 * n], g2 = Ss[9 * n];
                     const double u = recip_pos(n2);
-                    const double a = u / omega, bq = 0.5 * omega * u;
+                    const double a = u * om.inv_w, bq = om.half_w * u;
                     const double C = -u * (a * (Y[3] * Kb[0] + Y[4] * Kb[1] + Y[5] * Kb[2]) +
                                            bq * (g0 * Kb[3] + g1 * Kb[4] + g2 * Kb[5]));
                     double HK[3];
                     base_hess_vec<KIND>(m, Y, Kb + 3, HK);
-                    const double *Gs = S.G + ((int64_t)(s * 4 + st) * nb) * n + i;
+                    // blob terms in double-float
+                    const dfl X0 = df_from_double(Y[0]), X1 = df_from_double(Y[1]), X2 = df_from_double(Y[2]);
+                    const dfl B0 = df_from_double(Kb[3]), B1 = df_from_double(Kb[4]), B2 = df_from_double(Kb[5]);
+                    const dfl Cd = df_from_double(C), Bq = df_from_double(bq);
+                    dfl H0 = {0.f, 0.f}, H1 = {0.f, 0.f}, H2 = {0.f, 0.f};
                     for (int j = 0; j < nb; ++j) {
-                        const double G = Gs[(int64_t)j * n];
-                        // negligible term (stored as +0): no contribution; tested on the
-                        // bit pattern, since an FP64 compare would occupy the FP64 pipe
-                        if (__double_as_longlong(G) == 0ll) continue;
-                        const double *b = sb + kBlobStride * j;
-                        const double dx = Y[0] - b[1], dy = Y[1] - b[2], dz = Y[2] - b[3];
-                        const double dK = dx * Kb[3] + dy * Kb[4] + dz * Kb[5];
-                        const double s2 = b[5];
-                        acc_t[(int64_t)j * n] += G * (C + bq * s2 * dK);
-                        const double t = s2 * b[0] * G;
-                        const double w = s2 * dK;
-                        HK[0] += t * (w * dx + Kb[3]);
-                        HK[1] += t * (w * dy + Kb[4]);
-                        HK[2] += t * (w * dz + Kb[5]);
+                        const float *w = sw + kSwRow * j;
+                        const float ex = X0.hi - w[0], ey = X1.hi - w[1], ez = X2.hi - w[2];
+                        if ((ex * ex + ey * ey + ez * ez) * w[6] < -kDfPreCull2) continue;
+                        const dfl d0 = df_add(X0, dfl{-w[0], -w[3]});
+                        const dfl d1 = df_add(X1, dfl{-w[1], -w[4]});
+                        const dfl d2 = df_add(X2, dfl{-w[2], -w[5]});
+                        const dfl q = df_add_sloppy(df_add_sloppy(df_sqr(d0), df_sqr(d1)), df_sqr(d2));
+                        const dfl ea = df_mul(dfl{w[6], w[7]}, q);
+                        if (ea.hi < (float)kBlobCull2) continue;
+                        const dfl E = df_exp2(ea, sdT);                                   // G_j
+                        const dfl dK = df_add(df_add(df_mul(d0, B0), df_mul(d1, B1)), df_mul(d2, B2));
+                        const dfl wv = df_mul(dfl{w[8], w[9]}, dK);                        // 2 s (x - c).Kbar_k
+                        const dfl v = df_mul(E, df_add(Cd, df_mul(Bq, wv)));
+                        atomicAdd(acc_t + (int64_t)j * n, df_to_double(v));
+                        const dfl BE = df_mul(dfl{w[10], w[11]}, E);                       // 2 s A G
+                        H0 = df_add_sloppy(H0, df_mul(BE, df_add(df_mul(wv, d0), B0)));
+                        H1 = df_add_sloppy(H1, df_mul(BE, df_add(df_mul(wv, d1), B1)));
+                        H2 = df_add_sloppy(H2, df_mul(BE, df_add(df_mul(wv, d2), B2)));
+                        ++work[2];
                     }
+                    HK[0] += df_to_double(H0);
+                    HK[1] += df_to_double(H1);
+                    HK[2] += df_to_double(H2);
                     double yb[6];
                     yb[0] = bq * HK[0] + C * g0;
                     yb[1] = bq * HK[1] + C * g1;
@@ -204,6 +246,8 @@ __global__ void __launch_bounds__(kAdjBlock, 7) adjoint_kernel(
             for (int c = 0; c < 6; ++c) dy0[c * ld + i] = lam[c];
         }
     }
+    work[1] = cx.live;
+    add_adjoint_work(counters, work);
 }
 
 // dL/dtheta_j = sum over rays of thetabar_j, one block per blob in a fixed
@@ -228,7 +272,7 @@ __global__ void __launch_bounds__(kRedBlock) adjoint_reduce_kernel(const double 
 
 size_t adjoint_scratch_bytes(int nb, int64_t n, int64_t every)
 {
-    return sizeof(double) * ((size_t)nb * n + (size_t)every * 4 * (kStageVals + nb) * (size_t)n) + 256;
+    return sizeof(double) * ((size_t)nb * n + (size_t)every * 4 * kStageVals * (size_t)n) + 256;
 }
 
 cudaError_t launch_adjoint(const MediumParams &m, int64_t n, double omega, double dt, int64_t n_steps,
@@ -241,11 +285,14 @@ cudaError_t launch_adjoint(const MediumParams &m, int64_t n, double omega, doubl
     AdjScratch S;
     S.tb = (double *)base;
     S.stage = S.tb + (int64_t)nb * n;
-    S.G = S.stage + every * 4 * kStageVals * n;
-#define GF_ADJ(K)                                                                                      \
-    case K:                                                                                            \
-        adjoint_kernel<K><<<(unsigned)blocks, kAdjBlock, 0, s>>>(m, n, omega, dt, n_steps, every, ckpt, \
-                                                                 steps_done, lambda, ld, dy0, S);     \
+    cudaError_t e = cudaMemsetAsync(S.tb, 0, sizeof(double) * (size_t)nb * n, s);
+    if (e != cudaSuccess) return e;
+    const Omega<double> om = make_omega<double>(omega);
+    unsigned long long *counters = work_counters();
+#define GF_ADJ(K)                                                                                          \
+    case K:                                                                                                \
+        adjoint_kernel<K><<<(unsigned)blocks, kAdjBlock, 0, s>>>(m, n, om, dt, n_steps, every, ckpt,        \
+                                                                 steps_done, lambda, ld, dy0, S, counters); \
         break;
     switch (m.kind) {
         GF_ADJ(K_HOMOG)
@@ -256,7 +303,7 @@ cudaError_t launch_adjoint(const MediumParams &m, int64_t n, double omega, doubl
         return cudaErrorInvalidValue;
     }
 #undef GF_ADJ
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (nb > 0) adjoint_reduce_kernel<<<nb, kRedBlock, 0, s>>>(S.tb, n, dtheta);
     return cudaGetLastError();
@@ -274,29 +321,18 @@ namespace gf {
 constexpr size_t kStaticAdjointScratchBytes = (size_t)64 << 20;
 static __device__ __align__(256) unsigned char g_adjoint_scratch[kStaticAdjointScratchBytes];
 
-constexpr int kMaxStaticDevices = 64;
-static std::mutex g_static_mutex;
-static void *g_static_ptr[kMaxStaticDevices] = {};
-
-// Device address of g_adjoint_scratch on the current device, looked up once
-// per device (host code cannot use the symbol itself as a device address).
+// Device address of g_adjoint_scratch in the current device's context, looked
+// up on every call (host code cannot use the symbol itself as a device
+// address).  Not cached: a context that is torn down and created again (for
+// example after cudaDeviceReset) loads the module anew, and the array may
+// then sit at another address.  The first lookup on a device may load this
+// file's module (lazy loading), which maps the array.
 static gf_status static_scratch(void **out)
 {
-    int dev = -1;
-    gf_status s = cuda_status(cudaGetDevice(&dev), "cudaGetDevice");
+    void *p = nullptr;
+    gf_status s = cuda_status(cudaGetSymbolAddress(&p, g_adjoint_scratch), "cudaGetSymbolAddress");
     if (s != GF_OK) return s;
-    if (dev < 0 || dev >= kMaxStaticDevices) {
-        set_error("gf_trace_adjoint_static: device ordinal %d >= %d", dev, kMaxStaticDevices);
-        return GF_ERR_UNSUPPORTED;
-    }
-    std::lock_guard<std::mutex> lock(g_static_mutex);
-    if (g_static_ptr[dev] == nullptr) {
-        void *p = nullptr;
-        if ((s = cuda_status(cudaGetSymbolAddress(&p, g_adjoint_scratch), "cudaGetSymbolAddress")) != GF_OK)
-            return s;
-        g_static_ptr[dev] = p;
-    }
-    *out = g_static_ptr[dev];
+    *out = p;
     return GF_OK;
 }
 
@@ -341,6 +377,10 @@ extern "C" gf_status gf_trace_adjoint_static(gf_medium m, int64_t n, double omeg
     }
     if ((s = check_device_ptr(dL_dtheta, "dL_dtheta")) != GF_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
+    // the lookup comes first, so that a call with n = 0 serves as the warm-up
+    // call that loads the module on this device
+    void *scratch = nullptr;
+    if ((s = static_scratch(&scratch)) != GF_OK) return s;
     if (n == 0)
         return cuda_status(cudaMemsetAsync(dL_dtheta, 0, sizeof(double) * p.n_blobs, st),
                            "gf_trace_adjoint_static memset");
@@ -348,8 +388,6 @@ extern "C" gf_status gf_trace_adjoint_static(gf_medium m, int64_t n, double omeg
         (s = check_device_ptr(lambda, "lambda")) != GF_OK)
         return s;
     if (dL_dy0 && (s = check_device_ptr(dL_dy0, "dL_dy0")) != GF_OK) return s;
-    void *scratch = nullptr;
-    if ((s = static_scratch(&scratch)) != GF_OK) return s;
     // every scratch word the kernels read is written earlier in the same call
     // (block partials, then the stage values of each segment), so nothing
     // needs clearing between calls

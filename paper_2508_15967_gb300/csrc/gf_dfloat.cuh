@@ -220,17 +220,7 @@ __device__ __forceinline__ bool rhs_df(const MediumParams &m, const float *__res
     EvalCtx<double> base;
     iso_index<double, KIND>(m, nullptr, 0, y, n2, g, base);
     blobs_df(sd, nb, y, n2, g, dT, live, stride);
-    if constexpr (WANT_D) D = y[3] * y[3] + y[4] * y[4] + y[5] * y[5] - om.w * om.w * n2;
-    if (!positive(n2)) return false;
-    const double inv = recip_pos(n2);
-    const double a = inv * om.inv_w, b = om.half_w * inv;
-    f[0] = a * y[3];
-    f[1] = a * y[4];
-    f[2] = a * y[5];
-    f[3] = b * g[0];
-    f[4] = b * g[1];
-    f[5] = b * g[2];
-    return true;
+    return rhs_iso_from_index<double, WANT_D>(om, y, n2, g, f, D);
 }
 
 }  // namespace gf

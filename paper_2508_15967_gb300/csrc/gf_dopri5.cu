@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "gf_dfloat.cuh"
@@ -32,7 +33,6 @@ constexpr double e1 = 35.0 / 384.0 - 5179.0 / 57600.0, e3 = 500.0 / 1113.0 - 757
 
 struct Ctl {
     double rtol, atol, h0, t_max, r2, fac_min, fac_max, safety;
-    float safety_f, rtol_f, atol_f;
     int64_t max_steps, max_attempts;
     Omega<double> om;
 };
@@ -56,15 +56,11 @@ struct Lane {
     double t, h, fmax, dm;
     int64_t ray;
     int32_t steps, rejects, status, attempts, nb;
+    // the lane's medium: scaled FP64 rows, FP32 pre-test rows (or NULL) and
+    // double-float rows of the batch's tables (global memory, L1/L2-resident)
+    const double *rows;
+    const float *prer, *dfr;
     MediumParams mp;
-};
-
-// A lane's blob slot in shared memory (field f of blob j at [(row j + f) * stride]):
-// scaled FP64 rows and FP32 pre-test rows (pf may be NULL), or double-float rows.
-struct Slot {
-    double *sm;
-    float *pf;
-    float *sf;
 };
 
 // Block-shared exponential tables: 2^(j/2048) (FP64) or the double-float 2^(j/64).
@@ -76,8 +72,6 @@ struct Tabs {
 template <int KIND, bool DF>
 struct LaneRhs {
     const Lane &L;
-    const Slot &S;
-    int stride;
     const Omega<double> &om;
     const Tabs &tb;
     template <bool WANT_D = true>
@@ -85,23 +79,21 @@ struct LaneRhs {
     {
         if constexpr (DF) {
             int live = 0;
-            return rhs_df<KIND, WANT_D>(L.mp, S.sf, L.nb, stride, om, y, f, D, tb.dT, live);
+            return rhs_df<KIND, WANT_D>(L.mp, L.dfr, L.nb, 1, om, y, f, D, tb.dT, live);
         } else {
             EvalCtx<double> cx;
             cx.T = tb.T;
-            cx.pre = S.pf;
-            cx.pre_stride = stride;
-            return rhs_iso<double, KIND, WANT_D>(L.mp, S.sm, L.nb, om, y, f, D, cx, stride);
+            cx.pre = L.prer;
+            return rhs_iso<double, KIND, WANT_D>(L.mp, L.rows, L.nb, om, y, f, D, cx, 1);
         }
     }
 };
 
-// Load ray `ray` of medium `med` into lane L and its per-thread shared-memory
-// blob slot.  Returns false if the ray is not active.
+// Load ray `ray` of medium `med` into lane L (its medium's rows are read in
+// place from the batch's tables).  Returns false if the ray is not active.
 template <int KIND, bool DF>
 __device__ __forceinline__ bool lane_load(Lane &L, const BatchView &B, const RaysView<double> &r,
-                                          int med, int64_t ray, const Slot &S, int stride, const Tabs &tb,
-                                          const Ctl &c)
+                                          int med, int64_t ray, const Tabs &tb, const Ctl &c)
 {
     L.status = r.status[ray];
     if (L.status != GF_RAY_ACTIVE) return false;
@@ -111,17 +103,12 @@ __device__ __forceinline__ bool lane_load(Lane &L, const BatchView &B, const Ray
     L.mp.n_h2 = B.base[3 * med];
     L.mp.n02 = B.base[3 * med + 1];
     L.mp.n02a2 = B.base[3 * med + 2];
-    if constexpr (DF) {
-        const float *dsrc = B.df + (int64_t)med * B.nb_max * kDfBlobStride;
-        for (int j = 0; j < L.nb * kDfBlobStride; ++j) S.sf[j * stride] = dsrc[j];
-    } else {
-        const double *src = B.blobs + (int64_t)med * B.nb_max * kBlobStride;
-        for (int j = 0; j < L.nb * kBlobStride; ++j) S.sm[j * stride] = src[j];
-        if (S.pf != nullptr) {
-            L.mp.pre_lim = B.pre_lim[med];
-            const float *psrc = B.pre + (int64_t)med * B.nb_max * 4;
-            for (int j = 0; j < L.nb * 4; ++j) S.pf[j * stride] = psrc[j];
-        }
+    L.rows = B.blobs + (int64_t)med * B.nb_max * kBlobStride;
+    L.prer = nullptr;
+    L.dfr = DF ? B.df + (int64_t)med * B.nb_max * kDfBlobStride : nullptr;
+    if (!DF && B.pre != nullptr) {
+        L.mp.pre_lim = B.pre_lim[med];
+        L.prer = B.pre + (int64_t)med * B.nb_max * 4;
     }
 #pragma unroll
     for (int c2 = 0; c2 < 6; ++c2) L.y[c2] = r.y[c2 * r.ld + ray];
@@ -133,7 +120,7 @@ __device__ __forceinline__ bool lane_load(Lane &L, const BatchView &B, const Ray
     L.h = c.h0;
     L.fmax = c.fac_max;
     double D;
-    const LaneRhs<KIND, DF> f{L, S, stride, c.om, tb};
+    const LaneRhs<KIND, DF> f{L, c.om, tb};
     bool ok = f.eval(L.y, L.K1, D);
     L.dm = fmax(L.dm, fabs(D));
     if (!ok) L.status = GF_RAY_CUTOFF;
@@ -143,10 +130,10 @@ __device__ __forceinline__ bool lane_load(Lane &L, const BatchView &B, const Ray
 // Final residual and store of a lane whose ray stopped.
 template <int KIND, bool DF>
 __device__ __forceinline__ void lane_store(const Lane &L, const RaysView<double> &r, int32_t *rejects,
-                                           const Slot &S, int stride, const Tabs &tb, const Ctl &c)
+                                           const Tabs &tb, const Ctl &c)
 {
     double K[6], D;
-    const LaneRhs<KIND, DF> f{L, S, stride, c.om, tb};
+    const LaneRhs<KIND, DF> f{L, c.om, tb};
     f.eval(L.y, K, D);
     const double dm = fmax(L.dm, fabs(D));
     const int64_t i = L.ray;
@@ -160,64 +147,234 @@ __device__ __forceinline__ void lane_store(const Lane &L, const RaysView<double>
     if (r.d_max) r.d_max[i] = dm;
 }
 
-// One attempted DOPRI5 step of an active lane (the step-size controller of
-// Hairer-Norsett-Wanner I, Sec. II.4).  Leaves L.status != ACTIVE when the ray stops.
-template <int KIND, bool DF>
-__device__ __forceinline__ void lane_attempt(Lane &L, const Slot &S, int stride, const Tabs &tb, const Ctl &c)
+// |v| by clearing the sign bit (an integer operation).
+__device__ __forceinline__ double abs_bits(double v)
+{
+    return __longlong_as_double(__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFll);
+}
+
+// 2^-120 <= v <= 2^120 for v >= 0, decided on the bit pattern: the range in
+// which v and v^(-1/10) are normal floats.
+__device__ __forceinline__ bool err2_in_range(double v)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return b >= 0x3870000000000000ull && b <= 0x4770000000000000ull;
+}
+
+// ------------------------------------------------- warp-cooperative blob sums
+
+// The persistent kernel's lanes hold rays at different places and times, so
+// their sets of non-negligible blob terms differ: evaluated lane by lane, a
+// warp spends one instruction slot per term that any of its lanes needs (the
+// union), while each lane needs only its own (in the batched workload 4.6 of
+// 8 terms per lane against 7.2 for the union).  Here the warp evaluates its
+// lanes' terms as a packed list instead: every lane selects its terms with
+// the FP32 pre-test, the (lane, blob) pairs are numbered across the warp,
+// and in rounds of 32 each lane computes one pair's u = sigma x - sigma c,
+// exponent and Gaussian G (the FP64 evaluator's operations, on the owner's
+// point and rows); the owners then add their own terms, in blob order, with
+// the same fused operations as the lane-by-lane evaluator.  The sums are
+// therefore the same bits as that evaluator's, whichever lanes share a warp.
+// Shared memory per warp: 32 nb_max pair slots of (G, u) and their (owner,
+// blob) indices.
+struct CoopWarp {
+    double *res;            // [32 nb_max][4]: G, u0, u1, u2
+    unsigned short *pair;   // [32 nb_max]: owner lane << 8 | blob
+};
+
+__host__ __device__ constexpr size_t coop_warp_bytes(int nb_max)
+{
+    return (size_t)32 * nb_max * (4 * sizeof(double) + sizeof(unsigned short));
+}
+
+__device__ __forceinline__ CoopWarp coop_warp(double *sm_dyn, int nb_max)
+{
+    char *base = reinterpret_cast<char *>(sm_dyn) + (threadIdx.x >> 5) * coop_warp_bytes(nb_max);
+    return CoopWarp{reinterpret_cast<double *>(base),
+                    reinterpret_cast<unsigned short *>(base + (size_t)32 * nb_max * 4 * sizeof(double))};
+}
+
+// Adds the blob terms of the lane's medium at x to n2 and g, cooperatively.
+// All 32 lanes of the warp must call it together (warp-uniform control flow);
+// lanes with part = false contribute no terms and their n2, g are left as they are.
+__device__ __forceinline__ void coop_blob_sums(const Lane &L, bool part, const double *x, double &n2, double *g,
+                                               const double *__restrict__ T, const CoopWarp &cw)
+{
+    constexpr unsigned kAll = 0xffffffffu;
+    const int lane = (int)(threadIdx.x & 31u);
+    unsigned m = 0u;   // candidate terms of this lane (bit j: blob j)
+    if (part) {
+        PreX px = {0.f, 0.f, 0.f, false};
+        if (L.prer != nullptr) px = pretest_point(L.mp, x);
+        for (int j = 0; j < L.nb; ++j)
+            if (!(px.on && pretest_negligible(L.prer + 4 * j, 1, px))) m |= 1u << j;
+    }
+    const int cnt = __popc(m);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(kAll, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(kAll, incl, 31);
+    if (total == 0) return;
+    const int first = incl - cnt;
+    for (unsigned mm = m, k = first; mm != 0u; mm &= mm - 1u, ++k)
+        cw.pair[k] = (unsigned short)((lane << 8) | (__ffs(mm) - 1));
+    __syncwarp(kAll);
+    // rounds of 32 pairs: G and u of pair p on lane p mod 32
+    const unsigned long long rows = (unsigned long long)L.rows;
+    for (int base = 0; base < total; base += 32) {
+        const int p = base + lane;
+        const int pr = p < total ? cw.pair[p] : 0;
+        const int own = pr >> 8;
+        const double x0 = __shfl_sync(kAll, x[0], own), x1 = __shfl_sync(kAll, x[1], own),
+                     x2 = __shfl_sync(kAll, x[2], own);
+        const double *b = reinterpret_cast<const double *>(__shfl_sync(kAll, rows, own)) + kBlobStride * (pr & 255);
+        if (p < total) {
+            const double sg = b[0];
+            const double u0 = fma(sg, x0, b[1]), u1 = fma(sg, x1, b[2]), u2 = fma(sg, x2, b[3]);
+            const double a = fma(-u2, u2, fma(-u1, u1, -(u0 * u0)));
+            double *r = cw.res + 4 * p;
+            r[0] = below_cull(a) ? 0.0 : exp2_tab(a, T);
+            r[1] = u0;
+            r[2] = u1;
+            r[3] = u2;
+        }
+    }
+    __syncwarp(kAll);
+    // the owner's terms, in blob order (a culled term has G = +0 and adds nothing)
+    const double *__restrict__ rb = L.rows;
+    for (unsigned mm = m, k = first; mm != 0u; mm &= mm - 1u, ++k) {
+        const double *r = cw.res + 4 * k;
+        const double G = r[0];
+        if (__double_as_longlong(G) == 0ll) continue;
+        const double *b = rb + kBlobStride * (__ffs(mm) - 1);
+        n2 = fma(b[4], G, n2);
+        const double c = b[5] * G;
+        g[0] = fma(c, r[1], g[0]);
+        g[1] = fma(c, r[2], g[1]);
+        g[2] = fma(c, r[3], g[2]);
+    }
+    __syncwarp(kAll);   // the buffers are reused by the next evaluation
+}
+
+// The right-hand side with warp-cooperative blob sums (FP64 blob rows only).
+template <int KIND, bool WANT_D>
+__device__ __forceinline__ bool rhs_coop(const Lane &L, bool part, const Omega<double> &om, const double *y,
+                                         double *f, double &D, const double *T, const CoopWarp &cw)
+{
+    double n2, g[3];
+    EvalCtx<double> base;
+    iso_index<double, KIND>(L.mp, nullptr, 0, y, n2, g, base);   // the index law without blobs
+    coop_blob_sums(L, part, y, n2, g, T, cw);
+    return rhs_iso_from_index<double, WANT_D>(om, y, n2, g, f, D);
+}
+
+// One attempted DOPRI5 step (the step-size controller of Hairer-Norsett-Wanner
+// I, Sec. II.4).  Leaves L.status != ACTIVE when the ray stops.  COOP: every
+// lane of the warp calls it together and the evaluations are warp-cooperative;
+// part = false marks a lane without an active ray, and a lane whose ray stops
+// inside the attempt goes on evaluating without terms.  Otherwise it is called
+// by active lanes alone and returns as soon as the ray stops.  The stage
+// combinations are explicit fused operations, so that both forms (and both
+// schedules) produce the same bits.
+template <int KIND, bool DF, bool COOP>
+__device__ __forceinline__ void lane_attempt(Lane &L, bool part, const Tabs &tb, const Ctl &c, const CoopWarp &cw)
 {
     using namespace dp;
-    if (L.steps >= c.max_steps || L.attempts >= c.max_attempts) { L.status = GF_RAY_MAX_STEPS; return; }
-    if (L.t >= c.t_max) { L.status = GF_RAY_DONE; return; }
-    ++L.attempts;
-    double hs = L.h;
+    bool go = part;
+    double hs = 0.0;
     bool last = false;
-    if (L.t + hs >= c.t_max) { hs = c.t_max - L.t; last = true; }
-    if (hs < 1e-14 * fmax(1.0, fabs(L.t))) { L.status = GF_RAY_STEP_UNDERFLOW; return; }
-    const LaneRhs<KIND, DF> f{L, S, stride, c.om, tb};
+    if (go) {
+        if (L.steps >= c.max_steps || L.attempts >= c.max_attempts) {
+            L.status = GF_RAY_MAX_STEPS;
+            go = false;
+        } else if (L.t >= c.t_max) {
+            L.status = GF_RAY_DONE;
+            go = false;
+        } else {
+            ++L.attempts;
+            hs = L.h;
+            if (L.t + hs >= c.t_max) { hs = c.t_max - L.t; last = true; }
+            if (hs < 1e-14 * fmax(1.0, fabs(L.t))) { L.status = GF_RAY_STEP_UNDERFLOW; go = false; }
+        }
+    }
+    if constexpr (!COOP) {
+        if (!go) return;
+    }
+    const LaneRhs<KIND, DF> f{L, c.om, tb};
+    const auto eval = [&](const double *Yp, double *Kp, double &Dp, auto want_d) -> bool {
+        constexpr bool WD = decltype(want_d)::value;
+        bool ok;
+        if constexpr (COOP)
+            ok = rhs_coop<KIND, WD>(L, go, c.om, Yp, Kp, Dp, tb.T, cw);
+        else
+            ok = f.template eval<WD>(Yp, Kp, Dp);
+        if (go && !ok) {
+            L.status = GF_RAY_CUTOFF;
+            go = false;
+        }
+        return go;
+    };
+    using NoD = std::integral_constant<bool, false>;
+    using WithD = std::integral_constant<bool, true>;
     const double *y = L.y, *K1 = L.K1;
-    double K2[6], K3[6], K4[6], K5[6], K6[6], K7[6], Y[6], D;
+    double K2[6], K3[6], K4[6], K5[6], K6[6], K7[6], Y[6], D = 0.0;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) Y[i] = y[i] + hs * (a21 * K1[i]);
-    if (!f.template eval<false>(Y, K2, D)) { L.status = GF_RAY_CUTOFF; return; }
+    for (int i = 0; i < 6; ++i) Y[i] = fma(hs, a21 * K1[i], y[i]);
+    if (!eval(Y, K2, D, NoD{}) && !COOP) return;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) Y[i] = y[i] + hs * (a31 * K1[i] + a32 * K2[i]);
-    if (!f.template eval<false>(Y, K3, D)) { L.status = GF_RAY_CUTOFF; return; }
+    for (int i = 0; i < 6; ++i) Y[i] = fma(hs, fma(a32, K2[i], a31 * K1[i]), y[i]);
+    if (!eval(Y, K3, D, NoD{}) && !COOP) return;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) Y[i] = y[i] + hs * (a41 * K1[i] + a42 * K2[i] + a43 * K3[i]);
-    if (!f.template eval<false>(Y, K4, D)) { L.status = GF_RAY_CUTOFF; return; }
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-        Y[i] = y[i] + hs * (a51 * K1[i] + a52 * K2[i] + a53 * K3[i] + a54 * K4[i]);
-    if (!f.template eval<false>(Y, K5, D)) { L.status = GF_RAY_CUTOFF; return; }
+    for (int i = 0; i < 6; ++i) Y[i] = fma(hs, fma(a43, K3[i], fma(a42, K2[i], a41 * K1[i])), y[i]);
+    if (!eval(Y, K4, D, NoD{}) && !COOP) return;
 #pragma unroll
     for (int i = 0; i < 6; ++i)
-        Y[i] = y[i] + hs * (a61 * K1[i] + a62 * K2[i] + a63 * K3[i] + a64 * K4[i] + a65 * K5[i]);
-    if (!f.template eval<false>(Y, K6, D)) { L.status = GF_RAY_CUTOFF; return; }
+        Y[i] = fma(hs, fma(a54, K4[i], fma(a53, K3[i], fma(a52, K2[i], a51 * K1[i]))), y[i]);
+    if (!eval(Y, K5, D, NoD{}) && !COOP) return;
 #pragma unroll
     for (int i = 0; i < 6; ++i)
-        Y[i] = y[i] + hs * (a71 * K1[i] + a73 * K3[i] + a74 * K4[i] + a75 * K5[i] + a76 * K6[i]);
-    if (!f.template eval<true>(Y, K7, D)) { L.status = GF_RAY_CUTOFF; return; }
+        Y[i] = fma(hs, fma(a65, K5[i], fma(a64, K4[i], fma(a63, K3[i], fma(a62, K2[i], a61 * K1[i])))), y[i]);
+    if (!eval(Y, K6, D, NoD{}) && !COOP) return;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        Y[i] = fma(hs, fma(a76, K6[i], fma(a75, K5[i], fma(a74, K4[i], fma(a73, K3[i], a71 * K1[i])))), y[i]);
+    if (!eval(Y, K7, D, WithD{})) return;
     bool fin = true;
 #pragma unroll
     for (int i = 0; i < 6; ++i) fin = fin && finite_bits(Y[i]) && finite_bits(K7[i]);
     if (!fin) { L.status = GF_RAY_NONFINITE; return; }
-    // The embedded error estimate e (FP64: a small difference of O(1) terms)
-    // is scaled and normed in FP32, as is the step factor: the controller is
-    // a heuristic, and the FP32 norm differs from an FP64 one by ~1e-7
-    // relative, which can only flip an accept decision for err within that of 1.
-    // Its float inputs are the bit-pattern truncations of e, y and Y (the
-    // hardware conversions run on the FP64 pipe).
-    float err2 = 0.0f;
+    // The controller of the oracle (Hairer-Norsett-Wanner I, Sec. II.4) in FP64
+    // accuracy: err^2 = mean_i (e_i / sc_i)^2 with sc_i = atol + rtol max(|y_i|,
+    // |Y_i|), accept iff err <= 1, fac = safety err^(-1/5).  The step factor
+    // must be accurate to far better than FP32: near the Luneburg surface the
+    // error committed by the step that crosses it depends on where the step
+    // boundaries fall, and a 1e-7 relative difference in the step sizes moves
+    // the solution by more than 1e-9 there.  No FP64 division, square root or
+    // power: 1/sc_i is the Newton-refined reciprocal, and err2^(-1/10) is the
+    // FP32 power refined by one Newton step y <- y (1 + (1 - err2 y^10) / 10)
+    // (quadratic: relative error below 6e-14 from the FP32 seed's ~1e-7);
+    // outside [2^-120, 2^120], where the seed is not a normal float, the FP64 power.
+    double err2 = 0.0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        const double e = hs * (e1 * K1[i] + e3 * K3[i] + e4 * K4[i] + e5 * K5[i] + e6 * K6[i] + e7 * K7[i]);
-        const float sc = fmaf(c.rtol_f, fmaxf(fabsf(narrow_trunc(y[i])), fabsf(narrow_trunc(Y[i]))), c.atol_f);
-        const float q = narrow_trunc(e) / sc;
-        err2 = fmaf(q, q, err2);
+        const double e = hs * fma(e7, K7[i], fma(e6, K6[i], fma(e5, K5[i], fma(e4, K4[i], fma(e3, K3[i], e1 * K1[i])))));
+        const double sc = fma(c.rtol, max_abs(abs_bits(y[i]), Y[i]), c.atol);
+        const double q = e * recip_pos(sc);
+        err2 = fma(q, q, err2);
     }
-    const float errf = sqrtf(err2 * (1.0f / 6.0f));
-    const double fac = errf > 0.0f ? widen(c.safety_f * powf(errf, -0.2f)) : L.fmax;
-    if (errf <= 1.0f) {
+    err2 = err2 * (1.0 / 6.0);
+    double fac = L.fmax;   // err = 0: grow by the current cap
+    if (err2_in_range(err2)) {
+        const double y0 = widen(powf(narrow_rn(err2), -0.1f));
+        const double y2 = y0 * y0, y4 = y2 * y2, y10 = (y4 * y4) * y2;
+        fac = c.safety * fma(y0 * 0.1, fma(-err2, y10, 1.0), y0);
+    } else if (positive(err2)) {
+        fac = c.safety * pow(err2, -0.1);
+    }
+    if (err2 <= 1.0) {
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
             L.y[i] = Y[i];
@@ -228,7 +385,7 @@ __device__ __forceinline__ void lane_attempt(Lane &L, const Slot &S, int stride,
         L.dm = max_abs(L.dm, D);
         L.h = hs * fmin(L.fmax, fmax(c.fac_min, fac));
         L.fmax = c.fac_max;
-        if (c.r2 > 0.0 && Y[0] * Y[0] + Y[1] * Y[1] + Y[2] * Y[2] > c.r2) L.status = GF_RAY_EXITED;
+        if (c.r2 > 0.0 && norm2_fixed(Y) > c.r2) L.status = GF_RAY_EXITED;
     } else {
         ++L.rejects;
         L.h = hs * fmin(L.fmax, fmax(c.fac_min, fac));
@@ -249,36 +406,23 @@ __device__ __forceinline__ Tabs stage_tables(double *sT, float *sdT)
     return Tabs{sT, sdT};
 }
 
-// Lane slot s of this thread: FP64 rows then FP32 pre-test rows (if the view
-// carries them), or double-float rows; `stride` lanes per row field.
-template <bool DF>
-__device__ __forceinline__ Slot lane_slot(double *sm_dyn, const BatchView &B, int stride, int s)
-{
-    const int at = s * blockDim.x + threadIdx.x;
-    if constexpr (DF) return Slot{nullptr, nullptr, reinterpret_cast<float *>(sm_dyn) + at};
-    float *pf = B.pre ? reinterpret_cast<float *>(sm_dyn + (size_t)B.nb_max * kBlobStride * stride) + at : nullptr;
-    return Slot{sm_dyn + at, pf, nullptr};
-}
-
 template <int KIND, bool DF>
 __global__ void __launch_bounds__(128) dopri5_medium_kernel(const BatchView B, const int med,
                                                             const int64_t lo, const int64_t hi,
                                                             const RaysView<double> r, int32_t *rejects,
                                                             const Ctl c)
 {
-    extern __shared__ double sm_dyn[];
     __shared__ double sT[DF ? 1 : kExpTabN];
     __shared__ float sdT[DF ? 2 * kDfExpN : 1];
     const Tabs tb = stage_tables<DF>(sT, sdT);
     __syncthreads();
-    const int stride = blockDim.x;
-    const Slot S = lane_slot<DF>(sm_dyn, B, stride, 0);
     const int64_t ray = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (ray >= hi) return;
     Lane L;
-    if (!lane_load<KIND, DF>(L, B, r, med, ray, S, stride, tb, c)) return;
-    while (L.status == GF_RAY_ACTIVE) lane_attempt<KIND, DF>(L, S, stride, tb, c);
-    lane_store<KIND, DF>(L, r, rejects, S, stride, tb, c);
+    if (!lane_load<KIND, DF>(L, B, r, med, ray, tb, c)) return;
+    const CoopWarp none{nullptr, nullptr};
+    while (L.status == GF_RAY_ACTIVE) lane_attempt<KIND, DF, false>(L, true, tb, c, none);
+    lane_store<KIND, DF>(L, r, rejects, tb, c);
 }
 
 // ------------------------------------------------------------- persistent
@@ -289,29 +433,44 @@ __global__ void __launch_bounds__(128) dopri5_medium_kernel(const BatchView B, c
 // items run dry; lanes may hold rays of different media (each lane has its own
 // blob slot in shared memory).  RPT ray slots per thread are interleaved.
 template <int KIND, int RPT, bool DF>
-__global__ void dopri5_persistent_kernel(const BatchView B, const RaysView<double> r,
+__global__ void __maxnreg__(168) dopri5_persistent_kernel(const BatchView B, const RaysView<double> r,
                                          int32_t *rejects, const Ctl c,
                                          const int compaction, int *__restrict__ head)
 {
+    // FP64 blob sums are warp-cooperative (coop_blob_sums, its buffers in
+    // dynamic shared memory); the double-float ones run lane by lane on the
+    // FP32 pipes, where a lane idle in a divergent term costs little
+    constexpr bool kCoop = !DF;
     extern __shared__ double sm_dyn[];
     __shared__ double sT[DF ? 1 : kExpTabN];
     __shared__ float sdT[DF ? 2 * kDfExpN : 1];
     const Tabs tb = stage_tables<DF>(sT, sdT);
     __syncthreads();
-    const int stride = blockDim.x * RPT;
+    const CoopWarp cw = kCoop ? coop_warp(sm_dyn, B.nb_max) : CoopWarp{nullptr, nullptr};
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
     Lane L[RPT];
     bool active[RPT];
 #pragma unroll
-    for (int s = 0; s < RPT; ++s) active[s] = false;
+    for (int s = 0; s < RPT; ++s) {
+        active[s] = false;
+        // a lane without a ray still runs the cooperative attempts (as a non-participant)
+#pragma unroll
+        for (int i = 0; i < 6; ++i) L[s].y[i] = L[s].K1[i] = 0.0;
+        L[s].h = L[s].t = 0.0;
+        L[s].nb = 0;
+        L[s].rows = B.blobs;
+        L[s].prer = nullptr;
+        L[s].dfr = nullptr;
+        L[s].mp.kind = KIND;
+        L[s].mp.n_h2 = L[s].mp.n02 = L[s].mp.n02a2 = 1.0;
+    }
     int64_t cur = 0, end = 0;
     int cur_med = 0;
     bool exhausted = false;
     for (;;) {
 #pragma unroll
         for (int s = 0; s < RPT; ++s) {
-            const Slot S = lane_slot<DF>(sm_dyn, B, stride, s);
             unsigned freem = __ballot_sync(0xffffffffu, !active[s]);
             while (freem != 0u && !exhausted) {
                 if (cur >= end) {
@@ -330,11 +489,11 @@ __global__ void dopri5_persistent_kernel(const BatchView B, const RaysView<doubl
                 const int take = (int)min((int64_t)nfree, end - cur);
                 const int rank = __popc(freem & lt_mask);
                 if (!active[s] && rank < take) {
-                    if (lane_load<KIND, DF>(L[s], B, r, cur_med, cur + rank, S, stride, tb, c)) {
+                    if (lane_load<KIND, DF>(L[s], B, r, cur_med, cur + rank, tb, c)) {
                         if (L[s].status == GF_RAY_ACTIVE)
                             active[s] = true;
                         else
-                            lane_store<KIND, DF>(L[s], r, rejects, S, stride, tb, c);
+                            lane_store<KIND, DF>(L[s], r, rejects, tb, c);
                     }
                 }
                 cur += take;
@@ -348,13 +507,15 @@ __global__ void dopri5_persistent_kernel(const BatchView B, const RaysView<doubl
         for (int it = 0; it < compaction; ++it) {
 #pragma unroll
             for (int s = 0; s < RPT; ++s) {
-                if (active[s]) {
-                    const Slot S = lane_slot<DF>(sm_dyn, B, stride, s);
-                    lane_attempt<KIND, DF>(L[s], S, stride, tb, c);
-                    if (L[s].status != GF_RAY_ACTIVE) {
-                        lane_store<KIND, DF>(L[s], r, rejects, S, stride, tb, c);
-                        active[s] = false;
-                    }
+                if constexpr (kCoop) {
+                    if (!__any_sync(0xffffffffu, active[s])) continue;   // warp-uniform
+                    lane_attempt<KIND, DF, true>(L[s], active[s], tb, c, cw);
+                } else if (active[s]) {
+                    lane_attempt<KIND, DF, false>(L[s], true, tb, c, cw);
+                }
+                if (active[s] && L[s].status != GF_RAY_ACTIVE) {
+                    lane_store<KIND, DF>(L[s], r, rejects, tb, c);
+                    active[s] = false;
                 }
             }
         }
@@ -490,9 +651,6 @@ static Ctl ctl_of(const gf_step_ctl *c, double omega)
     k.fac_min = c->fac_min;
     k.fac_max = c->fac_max;
     k.safety = c->safety;
-    k.safety_f = (float)c->safety;
-    k.rtol_f = (float)c->rtol;
-    k.atol_f = (float)c->atol;
     k.max_steps = c->max_steps;
     // rejections shrink h geometrically to h_min, so attempts are bounded; this
     // cap only guards against a controller that never converges
@@ -526,32 +684,22 @@ static gf_status check_tune(const gf_tune *t)
 
 static const gf_tune kDefaultTune = {128, 1, 4, 64};
 
-// Shared memory of one lane slot: scaled FP64 rows, and FP32 pre-test rows
-// when `pre`; or double-float rows (GF_F64X).
-static size_t lane_slot_bytes(int nb_max, bool pre, bool df = false)
-{
-    if (df) return (size_t)nb_max * kDfBlobStride * sizeof(float);
-    return (size_t)nb_max * (kBlobStride * sizeof(double) + (pre ? 4 * sizeof(float) : 0));
-}
-
-// Lane slots of a launch may take this much dynamic shared memory; a shape
-// whose slots with pre-test rows would exceed it runs without the pre-test.
-constexpr size_t kMaxLaneSmem = 200 * 1024;
-
 // Launch shape resolved outside any stream capture (function attributes and
-// occupancy queries are not stream work).
+// occupancy queries are not stream work).  The kernels read each lane's blob
+// rows in place, so a launch needs no dynamic shared memory.
 struct LaunchPlan {
     int grid = 0, block = 128, rpt = 1;
     size_t smem = 0;
-    bool pre = true;   // lane slots hold the FP32 pre-test rows
+    bool pre = true;   // FP32 pre-test rows are read (FP64 blob sums)
     bool df = false;   // double-float blob sums (GF_F64X)
 };
 
-static void size_slots(gf_batch b, int lanes, LaunchPlan &p)
+static void size_slots(gf_batch b, int lanes, LaunchPlan &p, bool persistent)
 {
     p.df = b->prec == GF_F64X;
-    p.pre = !p.df && lane_slot_bytes(b->nb_max, true) * lanes <= kMaxLaneSmem;
-    p.smem = lane_slot_bytes(b->nb_max, p.pre, p.df) * lanes;
+    p.pre = !p.df;
+    // the persistent FP64 kernel's cooperative buffers, one set per warp
+    p.smem = persistent && !p.df ? (size_t)(lanes / 32) * coop_warp_bytes(b->nb_max) : 0;
 }
 
 template <int KIND, int RPT, bool DF>
@@ -560,7 +708,7 @@ static cudaError_t plan_persistent_rpt(gf_batch b, const gf_tune &t, LaunchPlan 
     auto k = dopri5_persistent_kernel<KIND, RPT, DF>;
     p.block = t.block;
     p.rpt = RPT;
-    size_slots(b, t.block * RPT, p);
+    size_slots(b, t.block, p, true);
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -586,7 +734,7 @@ static cudaError_t plan(gf_batch b, gf_schedule sched, const gf_tune &t, LaunchP
                                       : plan_persistent_rpt<KIND, 2, false>(b, t, p);
     }
     p.block = 128;
-    size_slots(b, p.block, p);
+    size_slots(b, p.block, p, false);
     return df ? cudaFuncSetAttribute(dopri5_medium_kernel<KIND, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)p.smem)
               : cudaFuncSetAttribute(dopri5_medium_kernel<KIND, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -988,7 +1136,6 @@ gf_status gf_dopri5_autotune(gf_batch b, const gf_rays *rays, double omega, cons
             for (int cp : comps)
                 for (int ch : chunks) {
                     gf_tune cand{bl, rp, cp, ch};
-                    if (lane_slot_bytes(b->nb_max, false, b->prec == GF_F64X) * bl * rp > kMaxLaneSmem) continue;
                     reset();
                     cudaEventRecord(e0);
                     gf_status rs = run_dopri5(&sub, &scratch, nullptr, omega, ctl, GF_SCHED_PERSISTENT,

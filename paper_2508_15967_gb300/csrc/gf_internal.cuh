@@ -358,6 +358,19 @@ __device__ __forceinline__ double blob_term_scaled(const double *__restrict__ b,
 // stages; field f of blob j is read from sb[(kBlobStride * j + f) * stride]
 // (stride 1: a table shared by the block; stride = block size: one table per
 // thread).
+// |x|^2 with the roundings fixed (for double: the products and sums as
+// explicit fused operations), so that every kernel that evaluates the same
+// point -- the forward trace and the adjoint's recomputation of it --
+// obtains the same bits whatever the compiler contracts elsewhere.
+template <typename R>
+__device__ __forceinline__ R norm2_fixed(const R *x)
+{
+    if constexpr (sizeof(R) == 8)
+        return fma(x[2], x[2], fma(x[1], x[1], __dmul_rn(x[0], x[0])));
+    else
+        return x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+}
+
 template <typename R, int KIND>
 __device__ __forceinline__ void iso_index(const MediumParams &m, const R *__restrict__ sb, int nb,
                                           const R *x, R &n2, R *g, EvalCtx<R> &cx, int stride = 1)
@@ -366,7 +379,7 @@ __device__ __forceinline__ void iso_index(const MediumParams &m, const R *__rest
         n2 = (R)m.n_h2;
         g[0] = g[1] = g[2] = (R)0;
     } else if constexpr (KIND == K_LUNEBURG) {
-        R r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+        R r2 = norm2_fixed(x);
         if (r2 <= (R)1) {
             n2 = (R)2 - r2;
             g[0] = (R)-2 * x[0];
@@ -377,14 +390,17 @@ __device__ __forceinline__ void iso_index(const MediumParams &m, const R *__rest
             g[0] = g[1] = g[2] = (R)0;
         }
     } else if constexpr (KIND == K_QUADRATIC) {
-        R r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+        R r2 = norm2_fixed(x);
         n2 = (R)2 - r2;
         g[0] = (R)-2 * x[0];
         g[1] = (R)-2 * x[1];
         g[2] = (R)-2 * x[2];
     } else {  // K_GRIN
         R c = (R)m.n02a2;
-        n2 = (R)m.n02 - c * (x[1] * x[1] + x[2] * x[2]);
+        if constexpr (sizeof(R) == 8)
+            n2 = fma(-c, fma(x[2], x[2], __dmul_rn(x[1], x[1])), m.n02);
+        else
+            n2 = (R)m.n02 - c * (x[1] * x[1] + x[2] * x[2]);
         g[0] = (R)0;
         g[1] = (R)-2 * c * x[1];
         g[2] = (R)-2 * c * x[2];
@@ -434,14 +450,18 @@ struct Omega {
     R w, inv_w, half_w, inv_w2;   // w, 1/w, w/2, 1/w^2
 };
 
-template <typename R, int KIND, bool WANT_D>
-__device__ __forceinline__ bool rhs_iso(const MediumParams &m, const R *__restrict__ sb, int nb,
-                                        const Omega<R> &om, const R *y, R *f, R &D, EvalCtx<R> &cx,
-                                        int stride = 1)
+// ng, if not NULL, receives n^2 and grad n^2 (the adjoint's stage values).
+// The right-hand side from n^2 and grad n^2 at y (D when WANT_D), with the
+// roundings fixed for double, shared by every isotropic evaluator.
+template <typename R, bool WANT_D>
+__device__ __forceinline__ bool rhs_iso_from_index(const Omega<R> &om, const R *y, R n2, const R *g, R *f, R &D)
 {
-    R n2, g[3];
-    iso_index<R, KIND>(m, sb, nb, y, n2, g, cx, stride);
-    if constexpr (WANT_D) D = y[3] * y[3] + y[4] * y[4] + y[5] * y[5] - om.w * om.w * n2;
+    if constexpr (WANT_D) {
+        if constexpr (sizeof(R) == 8)
+            D = fma(-__dmul_rn(om.w, om.w), n2, norm2_fixed(y + 3));
+        else
+            D = y[3] * y[3] + y[4] * y[4] + y[5] * y[5] - om.w * om.w * n2;
+    }
     if (!positive(n2)) return false;
     R inv;
     if constexpr (sizeof(R) == 8)
@@ -457,6 +477,22 @@ __device__ __forceinline__ bool rhs_iso(const MediumParams &m, const R *__restri
     f[4] = b * g[1];
     f[5] = b * g[2];
     return true;
+}
+
+template <typename R, int KIND, bool WANT_D>
+__device__ __forceinline__ bool rhs_iso(const MediumParams &m, const R *__restrict__ sb, int nb,
+                                        const Omega<R> &om, const R *y, R *f, R &D, EvalCtx<R> &cx,
+                                        int stride = 1, R *ng = nullptr)
+{
+    R n2, g[3];
+    iso_index<R, KIND>(m, sb, nb, y, n2, g, cx, stride);
+    if (ng != nullptr) {
+        ng[0] = n2;
+        ng[1] = g[0];
+        ng[2] = g[1];
+        ng[3] = g[2];
+    }
+    return rhs_iso_from_index<R, WANT_D>(om, y, n2, g, f, D);
 }
 
 // Periodic tricubic B-spline: values and gradients of the 7 channels
@@ -659,6 +695,38 @@ __device__ __forceinline__ R cold_dkx(const MediumParams &m, const Omega<R> &om,
     const R RL = S * S - Dst * Dst;
     const R Da = S * ((R)2 * a + b) + P * b - RL - P * S;
     return (R)2 * Da * y[3] / w2;
+}
+
+// The RK4 combination of the fixed-step trace, shared by the forward kernel
+// and the adjoint's recomputation so that both produce the same bits: for
+// double every rounding is explicit (y + a K as one fused operation,
+// acc + 2 K fused, then y + h6 (acc + K4) as a rounded product and sum);
+// for float the expressions the compiler contracts as it sees fit.
+template <typename R>
+__device__ __forceinline__ R rk_axpy(R a, R k, R y)
+{
+    if constexpr (sizeof(R) == 8)
+        return fma(a, k, y);
+    else
+        return y + a * k;
+}
+
+template <typename R>
+__device__ __forceinline__ R rk_acc2(R acc, R k)
+{
+    if constexpr (sizeof(R) == 8)
+        return fma(2.0, k, acc);
+    else
+        return acc + (R)2 * k;
+}
+
+template <typename R>
+__device__ __forceinline__ R rk_inc(R h6, R acc, R k)
+{
+    if constexpr (sizeof(R) == 8)
+        return __dmul_rn(h6, __dadd_rn(acc, k));
+    else
+        return h6 * (acc + k);
 }
 
 // Dispatch on the medium kind at compile time.

@@ -62,14 +62,14 @@ __device__ __forceinline__ bool finite6<double>(const double *y)
     return bad == 0u;
 }
 
-// State update y <- y + inc.  FP64: plain add.  FP32: Kahan-compensated
+// State update y <- y + inc.  FP64: one rounded addition.  FP32: Kahan-compensated
 // (Kahan 1965) so that 10^4 small increments to |x| ~ 1 do not drift.
 template <typename R>
 struct Accum {
     __device__ __forceinline__ void add(R *y, const R *inc, R *out) const
     {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) out[c] = y[c] + inc[c];
+        for (int c = 0; c < 6; ++c) out[c] = __dadd_rn(y[c], inc[c]);
     }
     __device__ __forceinline__ void commit(R *y, const R *out) {
 #pragma unroll
@@ -174,17 +174,17 @@ rk4_kernel(const MediumParams m, const RaysView<R> r, const Omega<R> om, const R
             dm = max_abs(dm, D);
             if (!ok) { st = GF_RAY_CUTOFF; break; }
 #pragma unroll
-            for (int c = 0; c < 6; ++c) { acc[c] = K[c]; Y[c] = y[c] + h2 * K[c]; }
+            for (int c = 0; c < 6; ++c) { acc[c] = K[c]; Y[c] = rk_axpy(h2, K[c], y[c]); }
             if (!f.template eval<false>(Y, K, D, cx)) { st = GF_RAY_CUTOFF; break; }
 #pragma unroll
-            for (int c = 0; c < 6; ++c) { acc[c] += (R)2 * K[c]; Y[c] = y[c] + h2 * K[c]; }
+            for (int c = 0; c < 6; ++c) { acc[c] = rk_acc2(acc[c], K[c]); Y[c] = rk_axpy(h2, K[c], y[c]); }
             if (!f.template eval<false>(Y, K, D, cx)) { st = GF_RAY_CUTOFF; break; }
 #pragma unroll
-            for (int c = 0; c < 6; ++c) { acc[c] += (R)2 * K[c]; Y[c] = y[c] + dt * K[c]; }
+            for (int c = 0; c < 6; ++c) { acc[c] = rk_acc2(acc[c], K[c]); Y[c] = rk_axpy(dt, K[c], y[c]); }
             if (!f.template eval<false>(Y, K, D, cx)) { st = GF_RAY_CUTOFF; break; }
             R inc[6], yn[6];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) inc[c] = h6 * (acc[c] + K[c]);
+            for (int c = 0; c < 6; ++c) inc[c] = rk_inc(h6, acc[c], K[c]);
             acc_state.add(y, inc, yn);
             if (!finite6(yn)) { st = GF_RAY_NONFINITE; break; }
             acc_state.commit(y, yn);

@@ -153,11 +153,44 @@ def test_autograd_dy0_and_direct_call_agree():
 
 
 def test_checkpoint_interval_does_not_change_the_gradient():
+    """The recomputation reproduces the forward trace's bits and the sweep
+    runs in the same order whatever the segment length: the gradient is the
+    same bit for bit for every checkpoint interval."""
     wl, om, y0, xstar = _case(64, 300)
     ref, _, _ = _gpu_grad(wl, y0, xstar, every=64)
     for every in (1, 7, 300, 1000):
         g, _, _ = _gpu_grad(wl, y0, xstar, every=every)
-        assert _rel(g, ref) <= 1e-12, every
+        assert np.array_equal(g, ref), (every, _rel_per_component(g, ref))
+
+
+def test_recomputation_reproduces_the_forward_checkpoints():
+    """Work counters of the backward: every recomputed segment ends on the next
+    checkpoint of the forward trace in every bit (counters[3] = 0), including
+    rays that stop early; the sweep evaluates blob terms (counters[2] > 0)."""
+    wl, om, y0, xstar = _case(300, 700)
+    m = gf.gf_medium_create(**wl.medium)
+    rays = gf.Rays.from_numpy(y0[:, :3], y0[:, 3:])
+    st = np.zeros(300, np.int32)
+    st[::17] = gf.GF_RAY_CUTOFF                        # some rays never move
+    rays.status.copy_(torch.from_numpy(st))
+    every = 64
+    ck = torch.full((-(-700 // every), 6, 300), float("nan"), dtype=torch.float64, device="cuda")
+    gf.gf_trace_rk4(m, rays, 1.0, wl.dt, 700, 1.2, every, ck)   # radius 1.2: rays stop on leaving
+    steps = rays.steps.cpu().numpy()
+    assert (steps[::17] == 0).all() and 0 < steps.min(initial=700, where=st == 0) < 700
+    lam = torch.zeros_like(rays.y)
+    lam[:3] = 2 * (rays.y[:3] - torch.from_numpy(np.ascontiguousarray(xstar.T)).cuda())
+    counters = torch.zeros(4, dtype=torch.int64, device="cuda")
+    dth = torch.empty(64, dtype=torch.float64, device="cuda")
+    gf.gf_bench_set_counters(counters)
+    try:
+        gf.gf_trace_adjoint(m, 300, 1.0, wl.dt, 700, every, ck, rays.steps, lam, dth)
+        torch.cuda.synchronize()
+    finally:
+        gf.gf_bench_set_counters(None)
+    c = counters.cpu().numpy()
+    assert c[0] == 4 * steps.sum() and c[1] > 0 and c[2] > 0
+    assert c[3] == 0, f"{c[3]} recomputed segment-end components differ from the checkpoints"
 
 
 def test_adjoint_edge_cases():

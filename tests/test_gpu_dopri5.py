@@ -1,18 +1,28 @@
 """GPU batched adaptive DOPRI5 (persistent work-stealing and one launch per
 medium) against the FP64 oracle, through the C ABI.
 
-An embedded error estimate is a ~tol-sized difference of O(1) stage values,
-so its relative rounding is ~1e-16 / tol ~ 1e-7 at tol = 1e-9; any two
-implementations choose step sizes that differ at ~1e-8, their step sequences
-drift apart, and each solution carries its own global error (the oracle's at
-tol = 1e-9 on these media: median 1e-7, max 1.4e-6 against tol = 1e-13).  A
-1e-9 endpoint gate is therefore not attainable by any second implementation;
-the gate is that the GPU solution is as accurate as the oracle's:
-  per-ray error against the oracle at rtol = atol = 1e-13, at the same time,
-  has median, 99th percentile and maximum within 2x those of the oracle's own
-  tol = 1e-9 solution (+1e-9).
-Exiting rays (no event location) are compared at each ray's own stopping time.
-Both schedules and every launch shape return bit-identical buffers.
+Smooth media (the quadratic law n^2 = 2 - |x|^2 plus Gaussian blobs) are
+the strict gate: every ray within 1e-9 relative of the oracle at equal times,
+the oracle's accepted and rejected step counts on at least 99% of rays.
+
+The Luneburg medium has a kink: grad n^2 jumps at |x| = 1, and the error the
+crossing step commits depends on where the step boundaries fall relative to
+the surface.  An adaptive trace is therefore ill-conditioned there with
+respect to the rounding of its step sizes, in the oracle itself: changing the
+tolerance by one part in a million (which moves every step size by 2e-7, the
+size of the step-size differences between two FP64 implementations of the
+same controller, whose error estimates differ by up to ~1e-6 relative on
+steps where the estimate is small and cancellation-dominated) moves ~10% of
+the oracle's endpoints by more than 1e-9.  The Luneburg gate measures that
+conditioning on the same rays and requires the GPU to be no farther from the
+oracle than the oracle is from itself under that perturbation: at the
+median, 90th and 99th percentile and the maximum (within 2x + 1e-12), and
+with the oracle's step sequence on at least as many rays (within 2%).
+Equal times: a common t_max, or, for rays that stop on leaving r = 1.5 (no
+event location), the oracle re-traced to the stopping time.  As a second
+check the GPU solution is as accurate as the oracle's against a tight (1e-13)
+reference.  Both schedules and every launch shape return bit-identical
+buffers.
 """
 from __future__ import annotations
 
@@ -30,17 +40,17 @@ from tests._parity import rel_err
 pytestmark = pytest.mark.gpu
 
 
-def _setup(n_media=48, scale=1.0 / 64, nb=8):
+def _setup(n_media=48, scale=1.0 / 64, nb=8, kind="luneburg"):
     wl = W.batched(n_media=n_media, n_blobs=nb, scale_counts=scale)
     blobs, off = wl.extra["blobs"], wl.extra["offsets"]
-    om = [O.medium(kind="luneburg", blobs=blobs[j]) for j in range(n_media)]
+    om = [O.medium(kind=kind, blobs=blobs[j]) for j in range(n_media)]
     k0 = np.empty_like(wl.x0)
     for j in range(n_media):
         lo, hi = off[j], off[j + 1]
         if hi > lo:
             k0[lo:hi], st = O.onshell(om[j], wl.x0[lo:hi], wl.d[lo:hi])
             assert (st == 0).all()
-    media = [gf.gf_medium_create("luneburg", blobs=blobs[j]) for j in range(n_media)]
+    media = [gf.gf_medium_create(kind, blobs=blobs[j]) for j in range(n_media)]
     batch = gf.gf_batch_create(media, off)
     return wl, om, media, batch, k0
 
@@ -76,6 +86,10 @@ def _oracle(om, off, x0, k0, ctl, status=None):
 
 
 TIGHT = dict(rtol=1e-13, atol=1e-13)
+STRICT_TOL = 1e-9     # smooth media: every ray
+MIN_SAME = 0.99       # smooth media: share of rays with the oracle's step counts
+COND_DELTA = 1e-6     # kinked medium: relative change of rtol that probes the conditioning
+QUANTILES = (0.5, 0.9, 0.99, 1.0)
 
 
 def _as_accurate(e_g, e_o):
@@ -84,45 +98,128 @@ def _as_accurate(e_g, e_o):
         assert a <= 2 * b + 1e-9, (q, a, b)
 
 
-def _compare_fixed_time(g, o, om, off, x0, k0, ctl, t_end):
+def _same_sequence(g, o):
+    """Rays whose GPU accepted and rejected step counts both equal the oracle's."""
+    steps = g["steps"] if isinstance(g, dict) else g.steps
+    rej = g["rej"] if isinstance(g, dict) else g.rejects
+    return (steps == o.steps) & (rej == o.rejects)
+
+
+def _strict_gate(e, same, what):
+    assert same.mean() >= MIN_SAME, f"{what}: {(~same).sum()} of {len(same)} rays changed step counts"
+    assert e.max() <= STRICT_TOL, f"{what}: max rel err {e.max():.3e}"
+
+
+def _conditioned_gate(e, same, e_ref, same_ref, what):
+    """GPU-vs-oracle errors e no larger than the oracle-vs-perturbed-oracle
+    errors e_ref at every quantile (2x + 1e-12), and the oracle's step counts
+    kept on at least as many rays as the perturbed oracle keeps them (- 2%)."""
+    for q in QUANTILES:
+        a, b = np.quantile(e, q), np.quantile(e_ref, q)
+        assert a <= 2 * b + 1e-12, f"{what}: quantile {q}: {a:.3e} against the oracle's own {b:.3e}"
+    assert same.mean() >= same_ref.mean() - 0.02, (what, same.mean(), same_ref.mean())
+
+
+def _rejections_match(g, o, min_share, total=True):
+    """Rejections per ray equal the oracle's on min_share of rays (and, if
+    total, in sum within 0.1%)."""
+    assert (g["rej"] == o.rejects).mean() >= min_share, ((g["rej"] == o.rejects).mean(), min_share)
+    if total:
+        tg, to = int(g["rej"].sum()), int(o.rejects.sum())
+        assert abs(tg - to) <= 1e-3 * max(to, 1), (tg, to)
+
+
+def _perturbed(ctl):
+    return dict(ctl, rtol=ctl["rtol"] * (1 + COND_DELTA))
+
+
+def _compare_fixed_time(g, o, om, off, x0, k0, ctl, t_end, smooth=False):
     assert (g["status"] == gf.GF_RAY_DONE).all() and (o.status == gf.GF_RAY_DONE).all()
     assert (g["t"] == t_end).all()
+    same = _same_sequence(g, o)
+    e = rel_err(g["y"], o.y)
+    if smooth:
+        _strict_gate(e, same, f"t = {t_end}")
+        _rejections_match(g, o, MIN_SAME)
+        # |D| = | |k|^2 - n^2 |, a difference of O(1) terms: states that agree to
+        # ~1e-13 give residuals that agree to ~1e-12 absolute
+        np.testing.assert_allclose(g["dres"], o.dres, rtol=0, atol=1e-12)
+        np.testing.assert_allclose(g["dmax"], o.dmax, rtol=0, atol=1e-12)
+    else:
+        p = _oracle(om, off, x0, k0, _perturbed(ctl))
+        _conditioned_gate(e, same, rel_err(p.y, o.y), _same_sequence(p, o), f"t = {t_end}")
+        _rejections_match(g, o, (p.rejects == o.rejects).mean() - 0.02, total=False)
+        # |D| is set by the kink-crossing step, as sensitive as the state: same distribution
+        _as_accurate(g["dres"], o.dres)
+        _as_accurate(g["dmax"], o.dmax)
     ref = _oracle(om, off, x0, k0, dict(ctl, **TIGHT))
     _as_accurate(rel_err(g["y"], ref.y), rel_err(o.y, ref.y))
-    # max |D| along an adaptive trace measures that trace's own integration
-    # error: same magnitude on both sides, not the same value
-    _as_accurate(g["dmax"], o.dmax)
-
-
-def _err_at_own_time(y, t, rows, om, off, x0, k0, ctl):
-    med = np.searchsorted(off, rows, side="right") - 1
-    e = np.empty(len(rows))
-    for i, (r, j) in enumerate(zip(rows, med)):
-        one = O.make_rays(x0[r:r + 1], k0[r:r + 1])
-        O.trace_dopri5([om[j]], [0, 1], one, 1.0, **dict(ctl, radius=0.0, t_max=float(t[i]), **TIGHT))
-        e[i] = rel_err(y[i:i + 1], one.y)[0]
     return e
 
 
+def _retrace(om, off, x0, k0, ctl, rows, t_end, **kw):
+    """The oracle re-traced, ray by ray, to the given end times (no exit test)."""
+    med = np.searchsorted(off, rows, side="right") - 1
+    y = np.empty((len(rows), 6))
+    for i, (r, j) in enumerate(zip(rows, med)):
+        one = O.make_rays(x0[r:r + 1], k0[r:r + 1])
+        O.trace_dopri5([om[j]], [0, 1], one, 1.0, **dict(ctl, radius=0.0, t_max=float(t_end[i]), **kw))
+        y[i] = one.y[0]
+    return y
+
+
+def _oracle_rows(om, off, x0, k0, ctl, rows):
+    """The oracle's own traces of the given rays (each in its medium)."""
+    o = O.make_rays(x0[rows], k0[rows])
+    med = np.searchsorted(off, rows, side="right") - 1
+    for i, j in enumerate(med):
+        one = O.make_rays(x0[rows[i]:rows[i] + 1], k0[rows[i]:rows[i] + 1])
+        O.trace_dopri5([om[j]], [0, 1], one, 1.0, **ctl)
+        for name in ("y", "t", "status", "steps", "dres", "dmax", "rejects"):
+            getattr(o, name)[i] = getattr(one, name)[0]
+    return o
+
+
 def _compare_exit(g, om, off, x0, k0, ctl, o=None, rows=None):
-    """EXITED rays: GPU and oracle states each against a tight re-trace to their own stopping time."""
+    """EXITED rays (Luneburg): the GPU state against the oracle re-traced to
+    the GPU's stopping time at the same tolerance, gated by the oracle's own
+    conditioning (the perturbed oracle's exit states against the oracle
+    re-traced to their stopping times); then both solutions against a tight
+    re-trace to their own stopping times."""
     rows = np.arange(len(g["t"])) if rows is None else rows
     assert (g["status"] == gf.GF_RAY_EXITED).all()
     assert (np.linalg.norm(g["y"][:, :3], axis=1) > ctl["radius"]).all()
     if o is None:
-        o = O.make_rays(x0[rows], k0[rows])
-        med = np.searchsorted(off, rows, side="right") - 1
-        for i, j in enumerate(med):
-            one = O.make_rays(x0[rows[i]:rows[i] + 1], k0[rows[i]:rows[i] + 1])
-            O.trace_dopri5([om[j]], [0, 1], one, 1.0, **ctl)
-            for name in ("y", "t", "status", "steps", "dres", "dmax", "rejects"):
-                getattr(o, name)[i] = getattr(one, name)[0]
+        o = _oracle_rows(om, off, x0, k0, ctl, rows)
     assert (o.status == gf.GF_RAY_EXITED).all()
-    assert np.abs(g["steps"] - o.steps).max() <= 15
-    e_g = _err_at_own_time(g["y"], g["t"], rows, om, off, x0, k0, ctl)
-    e_o = _err_at_own_time(o.y, o.t, rows, om, off, x0, k0, ctl)
+    p = _oracle_rows(om, off, x0, k0, _perturbed(ctl), rows)
+    e = rel_err(g["y"], _retrace(om, off, x0, k0, ctl, rows, g["t"]))
+    e_ref = rel_err(p.y, _retrace(om, off, x0, k0, ctl, rows, p.t))
+    _conditioned_gate(e, _same_sequence(g, o), e_ref, _same_sequence(p, o), "exit")
+    _rejections_match(g, o, (p.rejects == o.rejects).mean() - 0.02, total=False)
+    e_g = rel_err(g["y"], _retrace(om, off, x0, k0, ctl, rows, g["t"], **TIGHT))
+    e_o = rel_err(o.y, _retrace(om, off, x0, k0, ctl, rows, o.t, **TIGHT))
     _as_accurate(e_g, e_o)
-    return e_g
+    return e
+
+
+def test_smooth_medium_strict_parity():
+    """Quadratic law + 8 blobs (no kink), 48 media, to t = 3 (about a third of
+    an orbit past the far side): every ray within 1e-9 of the oracle, the
+    oracle's step counts on >= 99% of rays; the same in GF_F64X; the
+    per-medium schedule bit-identical."""
+    wl, om, media, batch, k0 = _setup(kind="quadratic")
+    off = wl.extra["offsets"]
+    ctl = _ctl(wl, t_max=3.0, radius=0.0)
+    o = _oracle(om, off, wl.x0, k0, ctl)
+    g = _host(*_gpu(batch, wl.x0, k0, ctl))
+    _compare_fixed_time(g, o, om, off, wl.x0, k0, ctl, 3.0, smooth=True)
+    pm = _host(*_gpu(batch, wl.x0, k0, ctl, gf.GF_SCHED_PER_MEDIUM))
+    for k in g:
+        assert np.array_equal(g[k], pm[k]), k
+    gf.gf_batch_set_precision(batch, gf.GF_F64X)
+    gx = _host(*_gpu(batch, wl.x0, k0, ctl))
+    _compare_fixed_time(gx, o, om, off, wl.x0, k0, ctl, 3.0, smooth=True)
 
 
 def test_persistent_matches_oracle():
@@ -136,7 +233,7 @@ def test_persistent_matches_oracle():
 
 def test_fixed_end_time_parity():
     """Every ray integrated to t = 2.5 (through the lens surface, before the
-    exit), the tight equal-time gate."""
+    exit), gated by the oracle's own conditioning at that time."""
     wl, om, media, batch, k0 = _setup()
     ctl = _ctl(wl, t_max=2.5, radius=0.0)
     g = _host(*_gpu(batch, wl.x0, k0, ctl))

@@ -549,6 +549,34 @@ def test_dopri5_agrees_with_fine_rk4():
     np.testing.assert_allclose(r1.y, r2.y, atol=1e-9)
 
 
+def test_dopri5_kink_makes_step_placement_ill_conditioned():
+    """The Luneburg surface |x| = 1 (grad n^2 jumps) makes the adaptive trace
+    sensitive to the rounding of its step sizes: a relative change of 1e-6 in
+    rtol (every step 2e-7 shorter) moves at least 5% of the endpoints at t = 2.5
+    by more than 1e-9, while the same change in the kink-free quadratic law
+    with the same blobs moves none by more than 1e-12.  This is the oracle's
+    own conditioning, which bounds how closely any second implementation can
+    follow it through the kink."""
+    wl = W.batched(n_media=12, scale_counts=1.0 / 64)
+    blobs, off = wl.extra["blobs"], wl.extra["offsets"]
+    moved = {}
+    for kind in ("luneburg", "quadratic"):
+        media = [O.medium(kind=kind, blobs=blobs[j]) for j in range(12)]
+        k0 = np.empty_like(wl.x0)
+        for j in range(12):
+            if off[j + 1] > off[j]:
+                k0[off[j]:off[j + 1]], _ = O.onshell(media[j], wl.x0[off[j]:off[j + 1]], wl.d[off[j]:off[j + 1]])
+        ys = []
+        for rtol in (1e-9, 1e-9 * (1 + 1e-6)):
+            r = O.make_rays(wl.x0, k0)
+            O.trace_dopri5(media, off, r, 1.0, rtol=rtol, atol=1e-9, t_max=2.5, radius=0.0)
+            assert (r.status == O.DONE).all()
+            ys.append(r.y)
+        moved[kind] = np.abs(ys[1] - ys[0]).max(axis=1)
+    assert (moved["luneburg"] > 1e-9).mean() >= 0.05, (moved["luneburg"] > 1e-9).mean()
+    assert moved["quadratic"].max() < 1e-12, moved["quadratic"].max()
+
+
 # ---------------------------------------------------------------- sensitivities
 
 def _adjoint_case(n_rays=3, n_blobs=3, n_steps=300, dt=1e-2):
