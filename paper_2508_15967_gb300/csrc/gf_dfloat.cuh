@@ -129,7 +129,20 @@ __device__ __forceinline__ double df_to_double(dfl x) { return widen(x.hi) + wid
 // float pair, summed with error-free transformations and renormalised, times
 // 2^(k >> 11).  Relative error about 2^-47 max(1, |a|) (a.lo enters through
 // one float product), median ~2^-50.  sT: the (hi, lo) table in shared memory.
-__device__ __forceinline__ dfl df_exp2(dfl a, const float *__restrict__ sT)
+// Table entries 2^(j/2048) as float pairs: from the double-float table, or
+// split from the FP64 table (hi = RN_float(T_j), lo = RN_float(T_j - hi):
+// one FP64 subtraction, 48 of its 53 bits).
+struct DfTabPairs {
+    const float *__restrict__ sT;
+    __device__ __forceinline__ dfl operator()(int j) const { return {sT[2 * j], sT[2 * j + 1]}; }
+};
+struct DfTabFromDouble {
+    const double *__restrict__ T;
+    __device__ __forceinline__ dfl operator()(int j) const { return df_from_double(T[j]); }
+};
+
+template <typename Tab>
+__device__ __forceinline__ dfl df_exp2_tab(dfl a, const Tab &tab)
 {
     const float tf = __fmaf_rn(a.hi, 2048.0f, 12582912.0f);           // 1.5 * 2^23 + k
     const int k = __float_as_int(tf) - 0x4B400000;                      // bits of 1.5 * 2^23
@@ -140,7 +153,7 @@ __device__ __forceinline__ dfl df_exp2(dfl a, const float *__restrict__ sT)
     const float small = __fmaf_rn(__fmul_rn(rs, rs), __fmaf_rn(rs, kDfC3, kDfC2), __fmul_rn(kDfC1Hi, a.lo));
     const float plo = __fadd_rn(P1.lo, small);                          // p = P1.hi + plo
     const int j = k & (kDfExpN - 1);
-    const dfl T = {sT[2 * j], sT[2 * j + 1]};
+    const dfl T = tab(j);
     // T (1 + p) = T.hi + T.hi P1.hi + [T.lo + (T.lo P1.hi + T.hi plo + error of T.hi P1.hi)]
     const dfl ph = two_prod(T.hi, P1.hi);
     const float tl = __fmaf_rn(T.lo, P1.hi, __fmaf_rn(T.hi, plo, ph.lo));
@@ -150,6 +163,11 @@ __device__ __forceinline__ dfl df_exp2(dfl a, const float *__restrict__ sT)
     const dfl G = fast_two_sum(v.hi, __fadd_rn(v.lo, __fadd_rn(tl, u.lo)));
     const float sc = __int_as_float((127 + (k >> 11)) << 23);           // 2^(k >> 11), k >> 11 >= -64
     return {__fmul_rn(G.hi, sc), __fmul_rn(G.lo, sc)};
+}
+
+__device__ __forceinline__ dfl df_exp2(dfl a, const float *__restrict__ sT)
+{
+    return df_exp2_tab(a, DfTabPairs{sT});
 }
 
 static __constant__ float c_dfexp2_tab[2 * kDfExpN] = {GF_DFEXP2_TAB_VALUES};

@@ -63,7 +63,7 @@ struct Lane {
     MediumParams mp;
 };
 
-// Block-shared exponential tables: 2^(j/2048) (FP64) or the double-float 2^(j/64).
+// Block-shared exponential tables: 2^(j/2048) in FP64 or as double-float pairs.
 struct Tabs {
     const double *T;
     const float *dT;
@@ -259,26 +259,43 @@ __device__ __forceinline__ void coop_blob_sums(const Lane &L, bool part, const d
     __syncwarp(kAll);   // the buffers are reused by the next evaluation
 }
 
-// The right-hand side with warp-cooperative blob sums (FP64 blob rows only).
-template <int KIND, bool WANT_D>
+// The right-hand side with warp-cooperative blob sums (FP64 blob rows only);
+// D is formed when want_d.
+template <int KIND>
 __device__ __forceinline__ bool rhs_coop(const Lane &L, bool part, const Omega<double> &om, const double *y,
-                                         double *f, double &D, const double *T, const CoopWarp &cw)
+                                         double *f, double &D, bool want_d, const double *T, const CoopWarp &cw)
 {
     double n2, g[3];
     EvalCtx<double> base;
     iso_index<double, KIND>(L.mp, nullptr, 0, y, n2, g, base);   // the index law without blobs
     coop_blob_sums(L, part, y, n2, g, T, cw);
-    return rhs_iso_from_index<double, WANT_D>(om, y, n2, g, f, D);
+    return want_d ? rhs_iso_from_index<double, true>(om, y, n2, g, f, D)
+                  : rhs_iso_from_index<double, false>(om, y, n2, g, f, D);
 }
+
+// Stage coefficients as a queue: after stage j (2..7) is evaluated, its K_j
+// enters the accumulators of stages j+1 .. j+5 with a_{j+k, j} (zero beyond
+// stage 7), and the error accumulator with e_j.  The accumulator of stage j
+// is a_{j1} K_1 + ... + a_{j,j-1} K_{j-1}, summed in that order with fused
+// operations, exactly as an unrolled combination would.
+__constant__ double c_dp_queue[6][5] = {
+    {dp::a32, dp::a42, dp::a52, dp::a62, 0.0},            // K2 into stages 3..7
+    {dp::a43, dp::a53, dp::a63, dp::a73, 0.0},            // K3 into stages 4..7
+    {dp::a54, dp::a64, dp::a74, 0.0, 0.0},                // K4
+    {dp::a65, dp::a75, 0.0, 0.0, 0.0},                    // K5
+    {dp::a76, 0.0, 0.0, 0.0, 0.0},                        // K6
+    {0.0, 0.0, 0.0, 0.0, 0.0}};                           // K7 (the new state's slope)
+__constant__ double c_dp_err[6] = {0.0, dp::e3, dp::e4, dp::e5, dp::e6, dp::e7};   // e_2 .. e_7
 
 // One attempted DOPRI5 step (the step-size controller of Hairer-Norsett-Wanner
 // I, Sec. II.4).  Leaves L.status != ACTIVE when the ray stops.  COOP: every
 // lane of the warp calls it together and the evaluations are warp-cooperative;
 // part = false marks a lane without an active ray, and a lane whose ray stops
 // inside the attempt goes on evaluating without terms.  Otherwise it is called
-// by active lanes alone and returns as soon as the ray stops.  The stage
-// combinations are explicit fused operations, so that both forms (and both
-// schedules) produce the same bits.
+// by active lanes alone and returns as soon as the ray stops.  The six stages
+// run as one loop (a single copy of the evaluator in the code) over a queue
+// of stage accumulators; the combinations are explicit fused operations, so
+// both forms (and both schedules) produce the same bits.
 template <int KIND, bool DF, bool COOP>
 __device__ __forceinline__ void lane_attempt(Lane &L, bool part, const Tabs &tb, const Ctl &c, const CoopWarp &cw)
 {
@@ -304,44 +321,69 @@ __device__ __forceinline__ void lane_attempt(Lane &L, bool part, const Tabs &tb,
         if (!go) return;
     }
     const LaneRhs<KIND, DF> f{L, c.om, tb};
-    const auto eval = [&](const double *Yp, double *Kp, double &Dp, auto want_d) -> bool {
-        constexpr bool WD = decltype(want_d)::value;
+    const double *y = L.y, *K1 = L.K1;
+    // Q[k]: accumulator of stage j + k (k = 0: the stage evaluated next); E: error sum
+    double Q[5][6], E[6], K[6], Y[6], D = 0.0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        Q[0][i] = a21 * K1[i];
+        Q[1][i] = a31 * K1[i];
+        Q[2][i] = a41 * K1[i];
+        Q[3][i] = a51 * K1[i];
+        Q[4][i] = a61 * K1[i];
+        E[i] = e1 * K1[i];
+    }
+#pragma unroll 1
+    for (int j = 0; j < 6; ++j) {   // stage j + 2
+#pragma unroll
+        for (int i = 0; i < 6; ++i) Y[i] = fma(hs, Q[0][i], y[i]);
+        const bool want_d = j == 5;
         bool ok;
         if constexpr (COOP)
-            ok = rhs_coop<KIND, WD>(L, go, c.om, Yp, Kp, Dp, tb.T, cw);
+            ok = rhs_coop<KIND>(L, go, c.om, Y, K, D, want_d, tb.T, cw);
         else
-            ok = f.template eval<WD>(Yp, Kp, Dp);
+            ok = want_d ? f.template eval<true>(Y, K, D) : f.template eval<false>(Y, K, D);
         if (go && !ok) {
             L.status = GF_RAY_CUTOFF;
             go = false;
         }
-        return go;
-    };
-    using NoD = std::integral_constant<bool, false>;
-    using WithD = std::integral_constant<bool, true>;
-    const double *y = L.y, *K1 = L.K1;
-    double K2[6], K3[6], K4[6], K5[6], K6[6], K7[6], Y[6], D = 0.0;
+        if constexpr (!COOP) {
+            if (!go) return;
+        }
+        if (j == 5) break;   // K = K7 at Y = Y7, the 5th-order solution
+        // K_{j+2} into the accumulators of stages j+3 .. 7, advancing the queue
+        // (Q[k] becomes stage j+3+k's); the zero coefficients (e_2, a_72 and the
+        // stages beyond 7) are skipped, which changes no bit of the sums
+        if (j > 0) {
 #pragma unroll
-    for (int i = 0; i < 6; ++i) Y[i] = fma(hs, a21 * K1[i], y[i]);
-    if (!eval(Y, K2, D, NoD{}) && !COOP) return;
+            for (int i = 0; i < 6; ++i) E[i] = fma(c_dp_err[j], K[i], E[i]);
+        }
 #pragma unroll
-    for (int i = 0; i < 6; ++i) Y[i] = fma(hs, fma(a32, K2[i], a31 * K1[i]), y[i]);
-    if (!eval(Y, K3, D, NoD{}) && !COOP) return;
+        for (int i = 0; i < 6; ++i) Q[0][i] = fma(c_dp_queue[j][0], K[i], Q[1][i]);
+        if (j <= 3) {
 #pragma unroll
-    for (int i = 0; i < 6; ++i) Y[i] = fma(hs, fma(a43, K3[i], fma(a42, K2[i], a41 * K1[i])), y[i]);
-    if (!eval(Y, K4, D, NoD{}) && !COOP) return;
+            for (int i = 0; i < 6; ++i) Q[1][i] = fma(c_dp_queue[j][1], K[i], Q[2][i]);
+        }
+        if (j <= 2) {
 #pragma unroll
-    for (int i = 0; i < 6; ++i)
-        Y[i] = fma(hs, fma(a54, K4[i], fma(a53, K3[i], fma(a52, K2[i], a51 * K1[i]))), y[i]);
-    if (!eval(Y, K5, D, NoD{}) && !COOP) return;
+            for (int i = 0; i < 6; ++i) Q[2][i] = fma(c_dp_queue[j][2], K[i], Q[3][i]);
+        }
+        if (j <= 1) {
 #pragma unroll
-    for (int i = 0; i < 6; ++i)
-        Y[i] = fma(hs, fma(a65, K5[i], fma(a64, K4[i], fma(a63, K3[i], fma(a62, K2[i], a61 * K1[i])))), y[i]);
-    if (!eval(Y, K6, D, NoD{}) && !COOP) return;
+            for (int i = 0; i < 6; ++i) Q[3][i] = fma(c_dp_queue[j][3], K[i], Q[4][i]);
+        }
+        if (j == 0) {
 #pragma unroll
-    for (int i = 0; i < 6; ++i)
-        Y[i] = fma(hs, fma(a76, K6[i], fma(a75, K5[i], fma(a74, K4[i], fma(a73, K3[i], a71 * K1[i])))), y[i]);
-    if (!eval(Y, K7, D, WithD{})) return;
+            for (int i = 0; i < 6; ++i) Q[4][i] = a71 * K1[i];   // stage 7 enters: a_71 K_1 (a_72 = 0)
+        }
+    }
+    if (!go) return;
+    double K7[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        K7[i] = K[i];
+        E[i] = fma(c_dp_err[5], K[i], E[i]);
+    }
     bool fin = true;
 #pragma unroll
     for (int i = 0; i < 6; ++i) fin = fin && finite_bits(Y[i]) && finite_bits(K7[i]);
@@ -360,7 +402,7 @@ __device__ __forceinline__ void lane_attempt(Lane &L, bool part, const Tabs &tb,
     double err2 = 0.0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        const double e = hs * fma(e7, K7[i], fma(e6, K6[i], fma(e5, K5[i], fma(e4, K4[i], fma(e3, K3[i], e1 * K1[i])))));
+        const double e = hs * E[i];
         const double sc = fma(c.rtol, max_abs(abs_bits(y[i]), Y[i]), c.atol);
         const double q = e * recip_pos(sc);
         err2 = fma(q, q, err2);
@@ -395,7 +437,7 @@ __device__ __forceinline__ void lane_attempt(Lane &L, bool part, const Tabs &tb,
 
 // ------------------------------------------------------- one launch per medium
 
-// The exponential table of the evaluator (DF: double-float 2^(j/64), else 2^(j/2048)).
+// The exponential table of the evaluator: 2^(j/2048) as float pairs (DF) or in FP64.
 template <bool DF>
 __device__ __forceinline__ Tabs stage_tables(double *sT, float *sdT)
 {
