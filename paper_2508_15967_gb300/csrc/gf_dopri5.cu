@@ -456,12 +456,33 @@ __global__ void __launch_bounds__(128) dopri5_medium_kernel(const BatchView B, c
 {
     __shared__ double sT[DF ? 1 : kExpTabN];
     __shared__ float sdT[DF ? 2 * kDfExpN : 1];
+    // every ray of the launch is in medium `med`: its rows are staged once per block
+    __shared__ double srows[DF ? 1 : GF_MAX_BATCH_BLOBS * kBlobStride];
+    __shared__ float sprer[DF ? 1 : GF_MAX_BATCH_BLOBS * 4];
+    __shared__ float sdfr[DF ? GF_MAX_BATCH_BLOBS * kDfBlobStride : 1];
     const Tabs tb = stage_tables<DF>(sT, sdT);
+    const int nbm = B.nb[med];
+    if constexpr (DF) {
+        for (int j = threadIdx.x; j < nbm * kDfBlobStride; j += blockDim.x)
+            sdfr[j] = B.df[(int64_t)med * B.nb_max * kDfBlobStride + j];
+    } else {
+        for (int j = threadIdx.x; j < nbm * kBlobStride; j += blockDim.x)
+            srows[j] = B.blobs[(int64_t)med * B.nb_max * kBlobStride + j];
+        if (B.pre != nullptr)
+            for (int j = threadIdx.x; j < nbm * 4; j += blockDim.x) sprer[j] = B.pre[(int64_t)med * B.nb_max * 4 + j];
+    }
     __syncthreads();
     const int64_t ray = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (ray >= hi) return;
     Lane L;
     if (!lane_load<KIND, DF>(L, B, r, med, ray, tb, c)) return;
+    // the same values, read from shared memory
+    if constexpr (DF) {
+        L.dfr = sdfr;
+    } else {
+        L.rows = srows;
+        if (L.prer != nullptr) L.prer = sprer;
+    }
     const CoopWarp none{nullptr, nullptr};
     while (L.status == GF_RAY_ACTIVE) lane_attempt<KIND, DF, false>(L, true, tb, c, none);
     lane_store<KIND, DF>(L, r, rejects, tb, c);
