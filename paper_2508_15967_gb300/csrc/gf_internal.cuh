@@ -259,12 +259,47 @@ template <>
 __device__ __forceinline__ const float *blob_table<float>(const MediumParams &m) { return m.blobs32; }
 
 // Stage the scaled blob rows the evaluator of precision R reads into shared
-// memory (all threads of the block call it).
+// memory (all threads of the block call it).  FP64: row after row.  FP32:
+// pairs of blobs interleaved field by field, (f_2p, f_2p+1) as one float2 per
+// field, for the packed FP32x2 evaluator; an odd count is padded with a zero
+// row (zero amplitude: it adds exactly nothing).
 template <typename R>
 __device__ __forceinline__ void stage_blobs(const MediumParams &m, R *sb)
 {
     const R *src = blob_table<R>(m);
-    for (int j = threadIdx.x; j < m.n_blobs * kBlobStride; j += blockDim.x) sb[j] = src[j];
+    if constexpr (sizeof(R) == 8) {
+        for (int j = threadIdx.x; j < m.n_blobs * kBlobStride; j += blockDim.x) sb[j] = src[j];
+    } else {
+        const int np = (m.n_blobs + 1) / 2;
+        for (int e = threadIdx.x; e < np * 2 * kBlobStride; e += blockDim.x) {
+            const int p = e / (2 * kBlobStride), f = (e / 2) % kBlobStride, h = e & 1;
+            const int j = 2 * p + h;
+            sb[e] = j < m.n_blobs ? src[kBlobStride * j + f] : (R)0;
+        }
+    }
+}
+
+// Packed FP32x2 arithmetic (two lanes of float per instruction on sm_100 and
+// later): d = a b + c, a b, and a + b, each half correctly rounded.
+__device__ __forceinline__ unsigned long long pk2(float2 v)
+{
+    return ((unsigned long long)__float_as_uint(v.y) << 32) | __float_as_uint(v.x);
+}
+__device__ __forceinline__ float2 upk2(unsigned long long v)
+{
+    return make_float2(__uint_as_float((unsigned)v), __uint_as_float((unsigned)(v >> 32)));
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)), "l"(pk2(c)));
+    return upk2(d);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b)
+{
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+    return upk2(d);
 }
 
 // Blob terms whose exponent is below this are skipped.  The FP64, FP32 and
@@ -417,28 +452,36 @@ __device__ __forceinline__ void iso_index(const MediumParams &m, const R *__rest
         }
     } else {
         // the same scaled form in FP32 with the hardware base-2 exponential
-        // (relative error ~2^-22; the FP32 rounding of |u|^2 adds up to
-        // 58.5 ln2 2^-24 ~ 2.4e-6 near the culling threshold).  Near a
-        // blob centre u = sigma x - sigma c loses ~ulp(sigma x) to cancellation,
-        // a relative error of ~4e-6 in G there: below one float ulp of n^2 for
-        // the amplitudes in use, far inside the FP32 gate.
-#pragma unroll 2
-        for (int j = 0; j < nb; ++j) {
-            const float *b = sb + kBlobStride * j * stride;
-            const float sg = b[0];
-            const float u0 = fmaf(sg, x[0], b[stride]), u1 = fmaf(sg, x[1], b[2 * stride]),
-                        u2 = fmaf(sg, x[2], b[3 * stride]);
-            const float a = fmaf(-u2, u2, fmaf(-u1, u1, -(u0 * u0)));
-            if (a >= (float)kBlobCull2) {
-                const float G = exp2_fast(a);
-                n2 = fmaf(b[4 * stride], G, n2);
-                const float c = b[5 * stride] * G;
-                g[0] = fmaf(c, u0, g[0]);
-                g[1] = fmaf(c, u1, g[1]);
-                g[2] = fmaf(c, u2, g[2]);
-                ++cx.live;
-            }
+        // (relative error ~2^-22), two blobs per packed FP32x2 instruction
+        // over the pair-interleaved rows of stage_blobs<float> (stride 1).
+        // Every term is evaluated: a term below 2^-58.5 (the FP64 evaluator's
+        // cut) is ~2^-34 of an FP32 ulp of n^2, and ex2 of a very negative
+        // exponent flushes to zero, so no lane waits on another's terms.
+        // Near a blob centre u = sigma x - sigma c loses ~ulp(sigma x) to
+        // cancellation, a relative error of ~4e-6 in G there: below one float
+        // ulp of n^2 for the amplitudes in use, far inside the FP32 gate.
+        const float2 X0 = make_float2(x[0], x[0]), X1 = make_float2(x[1], x[1]), X2 = make_float2(x[2], x[2]);
+        float2 N = make_float2(0.f, 0.f), H0 = N, H1 = N, H2 = N;
+        const float2 *rp = reinterpret_cast<const float2 *>(sb);
+        const int np = (nb + 1) / 2;
+#pragma unroll 1
+        for (int p = 0; p < np; ++p) {
+            const float2 *b = rp + kBlobStride * p;
+            const float2 sg = b[0];
+            const float2 u0 = fma2(sg, X0, b[1]), u1 = fma2(sg, X1, b[2]), u2 = fma2(sg, X2, b[3]);
+            const float2 q = fma2(u2, u2, fma2(u1, u1, mul2(u0, u0)));   // |u|^2
+            const float2 G = make_float2(exp2_fast(-q.x), exp2_fast(-q.y));
+            N = fma2(b[4], G, N);
+            const float2 c = mul2(b[5], G);
+            H0 = fma2(c, u0, H0);
+            H1 = fma2(c, u1, H1);
+            H2 = fma2(c, u2, H2);
         }
+        n2 += N.x + N.y;
+        g[0] += H0.x + H0.y;
+        g[1] += H1.x + H1.y;
+        g[2] += H2.x + H2.y;
+        cx.live += nb;
     }
 }
 

@@ -124,7 +124,7 @@ rk4_kernel(const MediumParams m, const RaysView<R> r, const Omega<R> om, const R
 {
     // FP64 blob terms: scaled rows, the FP32 pre-test rows and the exp table
     constexpr bool kBlobs64 = sizeof(R) == 8 && KIND != K_SPLINE && KIND != K_COLD && !DF;
-    __shared__ R sb[kBlobStride * GF_MAX_BLOBS];
+    __shared__ __align__(16) R sb[kBlobStride * GF_MAX_BLOBS];
     __shared__ double sT[kBlobs64 ? kExpTabN : 1];
     __shared__ float sp[kBlobs64 ? 4 * GF_MAX_BLOBS : 1];
     __shared__ float sdf[DF ? kDfBlobStride * GF_MAX_BLOBS : 1];
@@ -215,7 +215,7 @@ template <typename R, int KIND>
 __global__ void __launch_bounds__(kRk4Block) onshell_kernel(const MediumParams m, const RaysView<R> r,
                                                             const R *__restrict__ dir, const R omega)
 {
-    __shared__ R sb[kBlobStride * GF_MAX_BLOBS];
+    __shared__ __align__(16) R sb[kBlobStride * GF_MAX_BLOBS];
     __shared__ double sT[sizeof(R) == 8 ? kExpTabN : 1];
     if constexpr (KIND != K_SPLINE) stage_blobs<R>(m, sb);
     if constexpr (sizeof(R) == 8) stage_exp_table(sT);
@@ -258,7 +258,7 @@ template <typename R, int KIND>
 __global__ void __launch_bounds__(kRk4Block) newton_kx_kernel(const MediumParams m, const RaysView<R> r,
                                                               const R omega, const R tol, const int max_iter)
 {
-    __shared__ R sb[kBlobStride * GF_MAX_BLOBS];
+    __shared__ __align__(16) R sb[kBlobStride * GF_MAX_BLOBS];
     __shared__ double sT[sizeof(R) == 8 ? kExpTabN : 1];
     if constexpr (KIND != K_SPLINE) stage_blobs<R>(m, sb);
     if constexpr (sizeof(R) == 8) stage_exp_table(sT);
