@@ -675,7 +675,7 @@ __device__ __forceinline__ bool rhs_spline(const MediumParams &m, const Omega<R>
 // D_k through a = (k_x^2 + k_y^2)/w^2 and b = k_z^2/w^2, D_x through
 // S, Dst, P (f, g depend on x_0), D_w through a, b, S, Dst, P.  The ray
 // equations need only D_k, D_x and D_w; D_w = 0 is the cut-off test.
-template <typename R>
+template <typename R, bool WANT_D = true>
 __device__ __forceinline__ bool rhs_cold(const MediumParams &m, const Omega<R> &om, const R *y, R *f, R &D)
 {
     const R w = om.w, w2 = w * w, iw2 = om.inv_w2;
@@ -701,7 +701,7 @@ __device__ __forceinline__ bool rhs_cold(const MediumParams &m, const Omega<R> &
     }
     const R a = (y[3] * y[3] + y[4] * y[4]) * iw2, b = y[5] * y[5] * iw2;
     const R RL = S * S - Dst * Dst;
-    D = S * a * (a + b) + P * b * (a + b) - RL * a - P * S * (a + (R)2 * b) + P * RL;
+    if constexpr (WANT_D) D = S * a * (a + b) + P * b * (a + b) - RL * a - P * S * (a + (R)2 * b) + P * RL;
     const R DS = a * (a + b) - (R)2 * S * a - P * (a + (R)2 * b) + (R)2 * P * S;
     const R DD = (R)2 * Dst * a - (R)2 * P * Dst;
     const R DP = b * (a + b) - S * (a + (R)2 * b) + RL;
@@ -785,7 +785,7 @@ struct Rhs {
         if constexpr (KIND == K_SPLINE)
             return rhs_spline<R>(m, om, y, f, D);
         else if constexpr (KIND == K_COLD)
-            return rhs_cold<R>(m, om, y, f, D);
+            return rhs_cold<R, WANT_D>(m, om, y, f, D);
         else
             return rhs_iso<R, KIND, WANT_D>(m, sb, nb, om, y, f, D, cx);
     }

@@ -222,6 +222,32 @@ def test_smooth_medium_strict_parity():
     _compare_fixed_time(gx, o, om, off, wl.x0, k0, ctl, 3.0, smooth=True)
 
 
+def test_smooth_grin_batch_strict_parity():
+    """A batch of parabolic GRIN fibres (n0 = 1.5, a = 2) with 8 blobs each, the
+    batched kernels' GRIN index law: rays from the plane x = -1 within 0.9 of
+    the axis bend back towards it; strict gate at t = 1.5."""
+    wl = W.batched(n_media=24, scale_counts=1.0 / 64)
+    blobs, off = wl.extra["blobs"], wl.extra["offsets"]
+    x0 = wl.x0.copy()
+    x0[:, 1:] *= 0.3                                          # inside the fibre (n^2 > 0)
+    om = [O.medium(kind="grin", n0=1.5, a=2.0, blobs=blobs[j]) for j in range(24)]
+    k0 = np.empty_like(x0)
+    for j in range(24):
+        lo, hi = off[j], off[j + 1]
+        if hi > lo:
+            k0[lo:hi], st = O.onshell(om[j], x0[lo:hi], wl.d[lo:hi])
+            assert (st == 0).all()
+    media = [gf.gf_medium_create("grin", n0=1.5, a=2.0, blobs=blobs[j]) for j in range(24)]
+    batch = gf.gf_batch_create(media, off)
+    ctl = _ctl(wl, t_max=1.5, radius=0.0)
+    o = _oracle(om, off, x0, k0, ctl)
+    g = _host(*_gpu(batch, x0, k0, ctl))
+    _compare_fixed_time(g, o, om, off, x0, k0, ctl, 1.5, smooth=True)
+    pm = _host(*_gpu(batch, x0, k0, ctl, gf.GF_SCHED_PER_MEDIUM))
+    for k in g:
+        assert np.array_equal(g[k], pm[k]), k
+
+
 def test_persistent_matches_oracle():
     wl, om, media, batch, k0 = _setup()
     ctl = _ctl(wl)

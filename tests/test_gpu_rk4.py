@@ -82,6 +82,26 @@ def test_grin_f32_parity():
     assert_parity(g, o, 1e-4, diag_atol=1e-5)
 
 
+@pytest.mark.parametrize("n_blobs", [1, 7, 64])
+def test_f32_odd_and_full_blob_counts(n_blobs):
+    """The FP32 evaluator takes blobs in pairs (packed FP32x2 instructions); an
+    odd count is padded with a zero row.  GRIN with 1, 7 and 64 blobs, 300 rays
+    x 2000 steps, set on shell by the FP32 kernel, against the FP64 oracle on
+    the same FP32-rounded states."""
+    wl = W.grin(n=300, n_steps=2000, n_blobs=n_blobs)
+    x0f = _f32(wl.x0)
+    m = gf.gf_medium_create(**wl.medium)
+    rays = gf.Rays.from_numpy(x0f, None, torch.float32)
+    gf.gf_rays_onshell(m, rays, torch.from_numpy(np.ascontiguousarray(wl.d.T)).to("cuda", torch.float32), 1.0)
+    k0f = rays.state()[:, 3:].copy()
+    k_or, st = O.onshell(O.medium(**wl.medium), x0f, _f32(wl.d))
+    assert (st == 0).all()
+    np.testing.assert_allclose(k0f, k_or, rtol=1e-6, atol=1e-6)
+    g = gpu_rk4(wl.medium, x0f, k0f, 1.0, wl.dt, wl.n_steps, dtype=torch.float32)
+    o, _ = oracle_rk4(wl.medium, x0f, k0f, 1.0, wl.dt, wl.n_steps)
+    assert_parity(g, o, 1e-4, diag_atol=1e-5)
+
+
 def test_spline_parity_f64():
     """Anisotropic 128^3 tricubic medium, 257 rays (2 blocks + 1), 4000 steps.
     Rays whose oracle endpoint moves by > 1e-10 under a one-ulp launch
