@@ -2,8 +2,8 @@
  * gf_bench.h -- measurement helpers of libgf.so (no counterpart in the paper).
  *
  * The ray kernels are bound by the FP64 (or FP32) non-tensor pipes, whose
- * peaks are not in the measured peak table; these helpers measure
- * them on the current device with independent FMA chains.
+ * peaks a copy-bandwidth or tensor-GEMM measurement does not give; these
+ * helpers measure them on the current device with independent FMA chains.
  */
 #ifndef GF_BENCH_H
 #define GF_BENCH_H

@@ -653,7 +653,7 @@ static gf_status build_items(gf_batch b, int chunk)
     dev_free(b->d_item_end);
     b->d_item_medium = nullptr;
     b->d_item_begin = b->d_item_end = nullptr;
-    b->chunk = 0;   // no valid item list until this build completes
+    b->chunk = 0;   // no valid item list until the rebuild below completes
     b->n_items = 0;
     size_t n = std::max<size_t>(med.size(), 1);
     gf_status s;
