@@ -474,12 +474,15 @@ def measure_luneburg(gf, torch) -> dict:
             "ms": t, "ray_steps_per_s": wl.n * wl.n_steps / (t / 1e3), "us_per_step": 1e3 * t / wl.n_steps}
 
 
-def measure_cold(gf, torch, peak: float | None = None) -> dict:
+def measure_cold(gf, torch, peak: float | None = None, n: int | None = None, n_steps: int | None = None) -> dict:
     """Cold-plasma workload (1,048,576 rays in the magnetised slab of Sec. 4.1
     with the Eq. 4 density gradient, O branch, RK4 dt = 1e-2 x 1500, FP64),
     the counterpart of the paper's own benchmark (1e6 cold-plasma rays, timed
-    without setup): Newton on k_x, then one warm-up and one timed trace."""
-    wl = W.cold()
+    without setup): Newton on k_x, then one warm-up and one timed trace.
+    n and n_steps shorten it (profiling captures)."""
+    d = inspect.signature(W.cold).parameters
+    wl = W.cold(n=min(n or d["n"].default, d["n"].default),
+                n_steps=min(n_steps or d["n_steps"].default, d["n_steps"].default))
     m = gf.gf_medium_create(**wl.medium)
     init = gf.Rays.from_numpy(wl.x0, wl.extra["k_start"])
     gf.gf_rays_newton_kx(m, init, wl.omega)
@@ -916,7 +919,7 @@ def run_workload(a):
     elif a.workload == "luneburg":
         res = measure_luneburg(gf, torch)
     elif a.workload == "cold":
-        res = measure_cold(gf, torch, peak)
+        res = measure_cold(gf, torch, peak, a.rays, a.nsteps)
     elif a.workload == "aniso":
         full = inspect.signature(W.aniso).parameters["n_steps"].default
         res = measure_aniso(gf, torch, peak, min(a.nsteps, full))

@@ -320,6 +320,14 @@ gf_status gf_medium_create(const gf_medium_desc *d, gf_medium *out)
     p.n_species = d->kind == GF_MED_COLD ? d->n_species : 0;
     for (int i = 0; i < 2 * GF_MAX_SPECIES; ++i) p.species[i] = i < 2 * p.n_species ? d->species[i] : 0.0;
     for (int i = 0; i < 4; ++i) p.prof[i] = d->kind == GF_MED_COLD ? d->profile[i] : 0.0;
+    p.wp_sum = 0.0;
+    for (int sp = 0; sp < GF_MAX_SPECIES; ++sp) {
+        const bool on = sp < p.n_species;
+        p.cold_x[3 * sp] = on ? p.species[2 * sp] * p.prof[1] : 0.0;
+        p.cold_x[3 * sp + 1] = on ? p.species[2 * sp + 1] * p.prof[3] : 0.0;
+        p.cold_x[3 * sp + 2] = 2.0 * p.cold_x[3 * sp + 1];
+        p.wp_sum += on ? p.species[2 * sp] : 0.0;
+    }
     gf_status s = GF_OK;
     const size_t n64 = std::max<size_t>(t64.size(), 1), n32 = std::max<size_t>(t32.size(), 1);
     if ((s = cuda_status(dev_alloc(&m->d_blobs64, n64 * sizeof(double)), "cudaMalloc(blobs)")) != GF_OK ||

@@ -153,6 +153,16 @@ __device__ __forceinline__ double abs_bits(double v)
     return __longlong_as_double(__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFll);
 }
 
+// min and max of two positive doubles (neither NaN) on their bit patterns.
+__device__ __forceinline__ double min_pos(double a, double b)
+{
+    return __double_as_longlong(a) < __double_as_longlong(b) ? a : b;
+}
+__device__ __forceinline__ double max_pos(double a, double b)
+{
+    return __double_as_longlong(a) > __double_as_longlong(b) ? a : b;
+}
+
 // 2^-120 <= v <= 2^120 for v >= 0, decided on the bit pattern: the range in
 // which v and v^(-1/10) are normal floats.
 __device__ __forceinline__ bool err2_in_range(double v)
@@ -395,19 +405,19 @@ __device__ __forceinline__ void lane_attempt(Lane &L, bool part, const Tabs &tb,
     // error committed by the step that crosses it depends on where the step
     // boundaries fall, and a 1e-7 relative difference in the step sizes moves
     // the solution by more than 1e-9 there.  No FP64 division, square root or
-    // power: 1/sc_i is the Newton-refined reciprocal, and err2^(-1/10) is the
+    // power: 1/sc_i is the Newton-refined reciprocal (relative error below
+    // 2^-44), the factor h^2 / 6 is applied to the sum, and err2^(-1/10) is the
     // FP32 power refined by one Newton step y <- y (1 + (1 - err2 y^10) / 10)
     // (quadratic: relative error below 6e-14 from the FP32 seed's ~1e-7);
     // outside [2^-120, 2^120], where the seed is not a normal float, the FP64 power.
     double err2 = 0.0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        const double e = hs * E[i];
         const double sc = fma(c.rtol, max_abs(abs_bits(y[i]), Y[i]), c.atol);
-        const double q = e * recip_pos(sc);
+        const double q = E[i] * recip_pos_q(sc);
         err2 = fma(q, q, err2);
     }
-    err2 = err2 * (1.0 / 6.0);
+    err2 = err2 * ((hs * hs) * (1.0 / 6.0));
     double fac = L.fmax;   // err = 0: grow by the current cap
     if (err2_in_range(err2)) {
         const double y0 = widen(powf(narrow_rn(err2), -0.1f));
@@ -416,7 +426,9 @@ __device__ __forceinline__ void lane_attempt(Lane &L, bool part, const Tabs &tb,
     } else if (positive(err2)) {
         fac = c.safety * pow(err2, -0.1);
     }
-    if (err2 <= 1.0) {
+    // err2 <= 1 and |Y|^2 > r^2, both sides >= +0 (or err2 NaN: rejected):
+    // compared on the bit patterns
+    if ((unsigned long long)__double_as_longlong(err2) <= 0x3FF0000000000000ull) {
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
             L.y[i] = Y[i];
@@ -425,12 +437,12 @@ __device__ __forceinline__ void lane_attempt(Lane &L, bool part, const Tabs &tb,
         L.t = last ? c.t_max : L.t + hs;
         ++L.steps;
         L.dm = max_abs(L.dm, D);
-        L.h = hs * fmin(L.fmax, fmax(c.fac_min, fac));
+        L.h = hs * min_pos(L.fmax, max_pos(c.fac_min, fac));
         L.fmax = c.fac_max;
-        if (c.r2 > 0.0 && norm2_fixed(Y) > c.r2) L.status = GF_RAY_EXITED;
+        if (c.r2 > 0.0 && __double_as_longlong(norm2_fixed(Y)) > __double_as_longlong(c.r2)) L.status = GF_RAY_EXITED;
     } else {
         ++L.rejects;
-        L.h = hs * fmin(L.fmax, fmax(c.fac_min, fac));
+        L.h = hs * min_pos(L.fmax, max_pos(c.fac_min, fac));
         L.fmax = 1.0;
     }
 }

@@ -39,8 +39,10 @@ struct MediumParams {
     const float *dfrows;         // n_blobs double-float rows (GF_F64X; layout in gf_dfloat.cuh)
     const float4 *grid;          // grid_n^3 nodes x 2 float4
     int32_t n_species, pad2;     // cold plasma
-    double species[2 * GF_MAX_SPECIES];
-    double prof[4];
+    double species[2 * GF_MAX_SPECIES];   // (w_p^2, Omega) per species
+    double prof[4];                       // f = prof0 + prof1 x_0, g = prof2 + prof3 x_0
+    double cold_x[3 * GF_MAX_SPECIES];    // per species w_p^2 f', Omega g', 2 Omega g'
+    double wp_sum;                        // sum of the species' w_p^2
 };
 
 // Ray buffers with a typed state pointer.
@@ -156,6 +158,20 @@ __device__ __forceinline__ double recip_pos(double v)
     const double r = __hiloint2double((int)((rb >> 3) + ((1023u - 127u) << 20)), (int)(rb << 29));
     const double e = fma(-v, r, 1.0);
     return fma(r, fma(e, e, e), r);
+}
+
+// 1/v for v > 0 to a relative error below 2^-44: the same FP32 seed refined by
+// one Newton step of quadratic order, r (1 + e), in 2 FP64 operations (for
+// error measures, where a few ulps do not matter).  Outside 2^-120 <= v < 2^120
+// the IEEE division.
+__device__ __forceinline__ double recip_pos_q(double v)
+{
+    const unsigned hi = (unsigned)__double2hiint(v);
+    if (hi - ((1023u - 120u) << 20) >= (240u << 20)) return 1.0 / v;
+    const float vf = __uint_as_float(((hi - ((1023u - 127u) << 20)) << 3) | ((unsigned)__double2loint(v) >> 29));
+    const unsigned rb = __float_as_uint(__frcp_rn(vf));
+    const double r = __hiloint2double((int)((rb >> 3) + ((1023u - 127u) << 20)), (int)(rb << 29));
+    return fma(r, fma(-v, r, 1.0), r);
 }
 
 // 2^a for a <= 0 (finite or -inf; a <= -1021 returns 0, below four times the
@@ -415,7 +431,13 @@ __device__ __forceinline__ void iso_index(const MediumParams &m, const R *__rest
         g[0] = g[1] = g[2] = (R)0;
     } else if constexpr (KIND == K_LUNEBURG) {
         R r2 = norm2_fixed(x);
-        if (r2 <= (R)1) {
+        // r2 <= 1; for a double (r2 >= +0 or NaN) decided on the bit pattern
+        bool inside;
+        if constexpr (sizeof(R) == 8)
+            inside = (unsigned long long)__double_as_longlong(r2) <= 0x3FF0000000000000ull;
+        else
+            inside = r2 <= (R)1;
+        if (inside) {
             n2 = (R)2 - r2;
             g[0] = (R)-2 * x[0];
             g[1] = (R)-2 * x[1];
@@ -675,46 +697,58 @@ __device__ __forceinline__ bool rhs_spline(const MediumParams &m, const Omega<R>
 // D_k through a = (k_x^2 + k_y^2)/w^2 and b = k_z^2/w^2, D_x through
 // S, Dst, P (f, g depend on x_0), D_w through a, b, S, Dst, P.  The ray
 // equations need only D_k, D_x and D_w; D_w = 0 is the cut-off test.
+// Per species t = wp2 / (w^2 - W^2) (wp2 = w_p^2 f, W = Omega g) enters
+// S = 1 - sum t and Dst = sum W t / w; its derivatives are
+// t_x = (wp2_x + 2 W t W_x) / den and t_w = -2 w t / den, so
+//   S_x = -sum t_x,  Dst_x = sum (W_x t + W t_x) / w,
+//   S_w = 2 w sum t / den,  Dst_w = -(sum W t / w^2 + 2 sum W t / den),
+// and P = 1 - f sum(w_p^2) / w^2 is linear in f: P_x, P_w follow from the one
+// sum.  The factors 1/w, 2w common to the species are applied once, after the
+// loop; wp2_x = w_p^2 f', W_x = Omega g' and 2 W_x are the host's constants.
 template <typename R, bool WANT_D = true>
 __device__ __forceinline__ bool rhs_cold(const MediumParams &m, const Omega<R> &om, const R *y, R *f, R &D)
 {
     const R w = om.w, w2 = w * w, iw2 = om.inv_w2;
-    const R fx = (R)m.prof[1], gx = (R)m.prof[3];
-    const R fv = (R)m.prof[0] + fx * y[0], gv = (R)m.prof[2] + gx * y[0];
-    R S = 1, Dst = 0, P = 1, Sx = 0, Dx = 0, Px = 0, Sw = 0, Dw = 0, Pw = 0;
+    const R fx = (R)m.prof[1];
+    const R fv = fma(fx, y[0], (R)m.prof[0]), gv = fma((R)m.prof[3], y[0], (R)m.prof[2]);
+    R S = 1, Sx = 0, sWt = 0, sDx = 0, sT2 = 0, sWT2 = 0;
     for (int sp = 0; sp < m.n_species; ++sp) {
-        const R wp = (R)m.species[2 * sp], Om = (R)m.species[2 * sp + 1];
-        const R wp2 = wp * fv, wp2x = wp * fx;
-        const R W = Om * gv, Wx = Om * gx;
-        const R den = w2 - W * W;
+        const R wp2 = (R)m.species[2 * sp] * fv, W = (R)m.species[2 * sp + 1] * gv;
+        const R wp2x = (R)m.cold_x[3 * sp], Wx = (R)m.cold_x[3 * sp + 1], Wx2 = (R)m.cold_x[3 * sp + 2];
+        const R den = fma(-W, W, w2);
         const R iden = recip<R>(den);   // either sign: below or above the cyclotron resonance
-        const R t = wp2 * iden;
+        const R t = wp2 * iden, Wt = W * t;
+        const R tx = fma(wp2x, iden, (Wt * Wx2) * iden);
         S -= t;
-        Dst += W * t * om.inv_w;
-        P -= wp2 * iw2;
-        Sx -= (wp2x + (R)2 * t * W * Wx) * iden;
-        Dx += ((Wx * wp2 + W * wp2x) + (R)2 * W * W * t * Wx) * iden * om.inv_w;
-        Px -= wp2x * iw2;
-        Sw += (R)2 * w * t * iden;
-        Dw -= W * t * ((R)3 * w2 - W * W) * iden * om.inv_w * om.inv_w;
-        Pw += (R)2 * wp2 * iw2 * om.inv_w;
+        Sx -= tx;
+        sWt += Wt;
+        sDx = fma(Wx, t, fma(W, tx, sDx));
+        sT2 = fma(t, iden, sT2);
+        sWT2 = fma(Wt, iden, sWT2);
     }
-    const R a = (y[3] * y[3] + y[4] * y[4]) * iw2, b = y[5] * y[5] * iw2;
-    const R RL = S * S - Dst * Dst;
-    if constexpr (WANT_D) D = S * a * (a + b) + P * b * (a + b) - RL * a - P * S * (a + (R)2 * b) + P * RL;
-    const R DS = a * (a + b) - (R)2 * S * a - P * (a + (R)2 * b) + (R)2 * P * S;
-    const R DD = (R)2 * Dst * a - (R)2 * P * Dst;
-    const R DP = b * (a + b) - S * (a + (R)2 * b) + RL;
-    const R Da = S * ((R)2 * a + b) + P * b - RL - P * S;
-    const R Db = S * a + P * (a + (R)2 * b) - (R)2 * P * S;
-    const R Dom = -(R)2 * (Da * a + Db * b) * om.inv_w + DS * Sw + DD * Dw + DP * Pw;
+    const R Dst = sWt * om.inv_w, Dx = sDx * om.inv_w;
+    const R Sw = (R)2 * w * sT2;
+    const R Dw = -fma(sWt, iw2, (R)2 * sWT2);
+    const R Pc = (R)m.wp_sum * iw2;
+    const R P = fma(-Pc, fv, (R)1), Px = -Pc * fx, Pw = ((R)2 * om.inv_w * Pc) * fv;
+    const R a = fma(y[4], y[4], y[3] * y[3]) * iw2, b = (y[5] * y[5]) * iw2;
+    const R ab = a + b, a2b = ab + b, PmA = P - a;
+    const R RL = fma(S, S, -(Dst * Dst));
+    // D = S a (a+b) + P b (a+b) - RL a - P S (a+2b) + P RL
+    if constexpr (WANT_D) D = fma(fma(S, a, P * b), ab, fma(RL, PmA, -(P * S) * a2b));
+    const R DS = fma(a, ab, fma(-P, a2b, (R)2 * S * PmA));
+    const R DD = (R)-2 * Dst * PmA;
+    const R DP = fma(b, ab, fma(-S, a2b, RL));
+    const R Da = fma(S, a + ab, fma(P, b - S, -RL));
+    const R Db = fma(P, fma((R)-2, S, a2b), S * a);
+    const R Dom = fma(DP, Pw, fma(DD, Dw, fma(DS, Sw, fma(Db, b, Da * a) * ((R)-2 * om.inv_w))));
     if (!(Dom != (R)0) || !isfinite(Dom)) return false;
     const R inv = recip<R>(Dom);
-    const R ka = (R)2 * Da * iw2, kb = (R)2 * Db * iw2;
-    f[0] = -ka * y[3] * inv;
-    f[1] = -ka * y[4] * inv;
-    f[2] = -kb * y[5] * inv;
-    f[3] = (DS * Sx + DD * Dx + DP * Px) * inv;
+    const R cA = (Da * inv) * ((R)-2 * iw2), cB = (Db * inv) * ((R)-2 * iw2);
+    f[0] = cA * y[3];
+    f[1] = cA * y[4];
+    f[2] = cB * y[5];
+    f[3] = fma(DP, Px, fma(DD, Dx, DS * Sx)) * inv;
     f[4] = (R)0;
     f[5] = (R)0;
     return true;

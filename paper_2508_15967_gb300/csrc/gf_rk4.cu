@@ -64,12 +64,14 @@ __device__ __forceinline__ bool finite6<double>(const double *y)
 
 // State update y <- y + inc.  FP64: one rounded addition.  FP32: Kahan-compensated
 // (Kahan 1965) so that 10^4 small increments to |x| ~ 1 do not drift.
+// Components NC..5 have a zero right-hand side and are carried unchanged.
 template <typename R>
 struct Accum {
+    template <int NC>
     __device__ __forceinline__ void add(R *y, const R *inc, R *out) const
     {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) out[c] = __dadd_rn(y[c], inc[c]);
+        for (int c = 0; c < 6; ++c) out[c] = c < NC ? __dadd_rn(y[c], inc[c]) : y[c];
     }
     __device__ __forceinline__ void commit(R *y, const R *out) {
 #pragma unroll
@@ -81,10 +83,16 @@ template <>
 struct Accum<float> {
     float comp[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float pend[6];
+    template <int NC>
     __device__ __forceinline__ void add(float *y, const float *inc, float *out)
     {
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
+            if (c >= NC) {
+                pend[c] = comp[c];
+                out[c] = y[c];
+                continue;
+            }
             float yk = __fsub_rn(inc[c], comp[c]);
             float s = __fadd_rn(y[c], yk);
             pend[c] = __fsub_rn(__fsub_rn(s, y[c]), yk);
@@ -161,6 +169,9 @@ rk4_kernel(const MediumParams m, const RaysView<R> r, const Omega<R> om, const R
         for (int c = 0; c < 6; ++c) y[c] = r.y[c * r.ld + i];
         dm = r.d_max ? (R)r.d_max[i] : (R)0;
         const R h2 = dt * (R)0.5, h6 = dt / (R)6;
+        // the cold plasma's k_y, k_z are constants of motion (f_4 = f_5 = 0):
+        // only the first NC components are combined
+        constexpr int NC = KIND == K_COLD ? 4 : 6;
         Accum<R> acc_state;
         for (; s < n_steps; ++s) {
             if (ckpt != nullptr && s % every == 0) {
@@ -174,18 +185,18 @@ rk4_kernel(const MediumParams m, const RaysView<R> r, const Omega<R> om, const R
             dm = max_abs(dm, D);
             if (!ok) { st = GF_RAY_CUTOFF; break; }
 #pragma unroll
-            for (int c = 0; c < 6; ++c) { acc[c] = K[c]; Y[c] = rk_axpy(h2, K[c], y[c]); }
+            for (int c = 0; c < 6; ++c) { acc[c] = K[c]; Y[c] = c < NC ? rk_axpy(h2, K[c], y[c]) : y[c]; }
             if (!f.template eval<false>(Y, K, D, cx)) { st = GF_RAY_CUTOFF; break; }
 #pragma unroll
-            for (int c = 0; c < 6; ++c) { acc[c] = rk_acc2(acc[c], K[c]); Y[c] = rk_axpy(h2, K[c], y[c]); }
+            for (int c = 0; c < NC; ++c) { acc[c] = rk_acc2(acc[c], K[c]); Y[c] = rk_axpy(h2, K[c], y[c]); }
             if (!f.template eval<false>(Y, K, D, cx)) { st = GF_RAY_CUTOFF; break; }
 #pragma unroll
-            for (int c = 0; c < 6; ++c) { acc[c] = rk_acc2(acc[c], K[c]); Y[c] = rk_axpy(dt, K[c], y[c]); }
+            for (int c = 0; c < NC; ++c) { acc[c] = rk_acc2(acc[c], K[c]); Y[c] = rk_axpy(dt, K[c], y[c]); }
             if (!f.template eval<false>(Y, K, D, cx)) { st = GF_RAY_CUTOFF; break; }
             R inc[6], yn[6];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) inc[c] = rk_inc(h6, acc[c], K[c]);
-            acc_state.add(y, inc, yn);
+            for (int c = 0; c < NC; ++c) inc[c] = rk_inc(h6, acc[c], K[c]);
+            acc_state.template add<NC>(y, inc, yn);
             if (!finite6(yn)) { st = GF_RAY_NONFINITE; break; }
             acc_state.commit(y, yn);
             if (radius2 > (R)0 && y[0] * y[0] + y[1] * y[1] + y[2] * y[2] > radius2) {

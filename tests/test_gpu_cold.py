@@ -18,6 +18,9 @@ COLD2 = dict(kind="cold", species=((0.45, -0.6), (0.03, 0.08)), profile=(1.0, 0.
 # the launch points, and Newton from k_x = 1.2 / 0.5 lands on the O / X root
 COLDXO = dict(kind="cold", species=((0.3, -0.5), (0.02, 0.05)), profile=(1.0, 0.1, 1.0, 0.05))
 COLD_E = dict(kind="cold", species=((0.3, -0.5),), profile=(1.0, 0.1, 1.0, 0.0))
+# the most species a medium holds (GF_MAX_SPECIES = 4): electrons and three ion species
+COLD4 = dict(kind="cold", species=((0.3, -0.5), (0.012, 0.06), (0.006, 0.03), (0.003, 0.02)),
+             profile=(1.0, 0.1, 1.0, 0.05))
 
 
 def _launch(n, seed, oblique):
@@ -67,6 +70,20 @@ def test_cold_rk4_parity_f64(spec, oblique):
     g = GpuResult(rays)
     o, _ = oracle_rk4(spec, x0, k0, 1.0, 0.01, 3000, status=st)
     assert_parity(g, o, 1e-9, diag_atol=1e-11)
+
+
+@pytest.mark.parametrize("guess", [1.2, 0.5])
+def test_cold_rk4_parity_four_species(guess):
+    """300 rays (2 blocks + a tail) in a four-species plasma, O (1.2) or X (0.5)
+    branch, 2000 steps of 0.01."""
+    x0, ky, kz = _launch(300, 4, True)
+    k0, st = _roots(COLD4, x0, ky, kz, guess)
+    assert (st == 0).all()
+    m = gf.gf_medium_create(**COLD4)
+    rays = gf.Rays.from_numpy(x0, k0)
+    gf.gf_trace_rk4(m, rays, 1.0, 0.01, 2000)
+    o, _ = oracle_rk4(COLD4, x0, k0, 1.0, 0.01, 2000, status=st)
+    assert_parity(GpuResult(rays), o, 1e-9, diag_atol=1e-11)
 
 
 def test_cold_rk4_parity_f32():
