@@ -531,8 +531,8 @@ __device__ __forceinline__ bool rhs_iso_from_index(const Omega<R> &om, const R *
     R inv;
     if constexpr (sizeof(R) == 8)
         inv = recip_pos(n2);
-    else
-        inv = __frcp_rn(n2);   // correctly rounded, as (R)1 / n2
+    else   // the hardware reciprocal (within one ulp; n^2 is far from the subnormals)
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(n2));
     const R a = inv * om.inv_w;
     const R b = om.half_w * inv;
     f[0] = a * y[3];

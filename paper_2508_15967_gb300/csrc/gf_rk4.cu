@@ -125,7 +125,7 @@ __device__ __forceinline__ void add_work(unsigned long long *counters, long long
 }
 
 template <typename R, int KIND, bool DF>
-__global__ void __launch_bounds__(kRk4Block, (KIND == K_SPLINE || KIND == K_COLD || sizeof(R) == 4) ? 1 : 5)
+__global__ void __launch_bounds__(kRk4Block, (KIND == K_SPLINE || KIND == K_COLD) ? 1 : sizeof(R) == 4 ? 6 : 5)
 rk4_kernel(const MediumParams m, const RaysView<R> r, const Omega<R> om, const R dt, const double dt64,
            const int64_t n_steps, const R radius2, const int64_t every, double *__restrict__ ckpt,
            unsigned long long *counters)
