@@ -199,7 +199,7 @@ rk4_kernel(const MediumParams m, const RaysView<R> r, const Omega<R> om, const R
             acc_state.template add<NC>(y, inc, yn);
             if (!finite6(yn)) { st = GF_RAY_NONFINITE; break; }
             acc_state.commit(y, yn);
-            if (radius2 > (R)0 && y[0] * y[0] + y[1] * y[1] + y[2] * y[2] > radius2) {
+            if (radius2 > (R)0 && norm2_fixed(y) > radius2) {
                 st = GF_RAY_EXITED;
                 ++s;
                 break;
@@ -219,6 +219,188 @@ rk4_kernel(const MediumParams m, const RaysView<R> r, const Omega<R> om, const R
         r.status[i] = st;
     }
     add_work(counters, evals, cx.live);
+}
+
+// ------------------------------------------- small traces: components split
+
+// A trace with few rays leaves most SM sub-partitions idle, and one warp's
+// FP64 instruction occupies its sub-partition for ~64 cycles whatever the
+// number of its active lanes, so such a trace takes (FP64 instructions of a
+// step per warp) x 64 cycles a step, however its rays are spread over warps.
+// Here kSplitWarps warps share 32 rays: warp w advances the components c with
+// c mod kSplitWarps = w (the stage points, the slope sums and the update of
+// those), and every warp evaluates what all components need (index law, blob
+// sums, reciprocal of n^2) at the full stage point, which the warps exchange
+// through shared memory once per stage.  Each value is formed by the same
+// operations as in rk4_kernel, so both kernels return the same bits.  Every
+// thread of a block passes the same barriers: the stops are decided from the
+// exchanged (identical) values, and the loop ends by a block-wide vote.
+// (measured on the 1024-ray Luneburg trace: 1, 2, 3 and 6 warps per 32 rays
+// take 9.1, 8.0, 7.0 and 7.5 ms; a 1000-ray GRIN trace with 16 blobs 77.8,
+// 72.6, 68.8 and 83.8 ms)
+constexpr int kSplitWarps = 3;
+static_assert(6 % kSplitWarps == 0, "each warp owns 6 / kSplitWarps components");
+
+template <int KIND, int W>
+__device__ __forceinline__ void rk4_split_warp(const MediumParams &m, const RaysView<double> &r,
+                                               const Omega<double> &om, const double dt, const double dt64,
+                                               const int64_t n_steps, const double radius2, const int64_t every,
+                                               double *__restrict__ ckpt, unsigned long long *counters,
+                                               const double *sb, EvalCtx<double> &cx, double (*xb)[6][32])
+{
+    constexpr int NO = 6 / kSplitWarps;   // this warp's components: W + kSplitWarps j, j < NO
+    const int lane = (int)(threadIdx.x & 31u);
+    const int64_t i = (int64_t)blockIdx.x * 32 + lane;
+    int st = GF_RAY_DONE;
+    if (i < r.n) st = r.status[i];
+    const bool started = st == GF_RAY_ACTIVE;
+    bool act = started;
+    double y[6], dm = 0.0;
+    if (started) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) y[c] = r.y[c * r.ld + i];
+        dm = r.d_max ? r.d_max[i] : 0.0;
+    }
+    const Rhs<double, KIND> f{m, sb, m.n_blobs, om};
+    const double h2 = dt * 0.5, h6 = dt / 6.0;
+    long long evals = 0;
+    int64_t s = 0;
+    int b = 0;
+    // the stage point Y: own components computed, the others read from the exchange
+    auto exchange = [&](double *Y, bool live) {
+        if (live) {
+#pragma unroll
+            for (int j = 0; j < NO; ++j) xb[b][W + kSplitWarps * j][lane] = Y[W + kSplitWarps * j];
+        }
+        __syncthreads();
+        if (live) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c)
+                if (c % kSplitWarps != W) Y[c] = xb[b][c][lane];
+        }
+        b ^= 1;
+    };
+    for (int64_t it = 0; it < n_steps; ++it) {
+        // a block-wide decision, so that every thread of the block passes the same barriers
+        if (!__syncthreads_or(act)) break;
+        double K[6], Y[6], D, acc[NO];
+        if (act) {
+            if (ckpt != nullptr && s % every == 0) {
+                double *slot = ckpt + (s / every) * 6 * r.n;
+#pragma unroll
+                for (int j = 0; j < NO; ++j) slot[(W + kSplitWarps * j) * r.n + i] = y[W + kSplitWarps * j];
+            }
+            evals += 4;
+            const bool ok = f.template eval<true>(y, K, D, cx);
+            dm = max_abs(dm, D);
+            if (!ok) { st = GF_RAY_CUTOFF; act = false; }
+        }
+        if (act) {
+#pragma unroll
+            for (int j = 0; j < NO; ++j) {
+                const int c = W + kSplitWarps * j;
+                acc[j] = K[c];
+                Y[c] = rk_axpy(h2, K[c], y[c]);
+            }
+        }
+        exchange(Y, act);
+        if (act && !f.template eval<false>(Y, K, D, cx)) { st = GF_RAY_CUTOFF; act = false; }
+        if (act) {
+#pragma unroll
+            for (int j = 0; j < NO; ++j) {
+                const int c = W + kSplitWarps * j;
+                acc[j] = rk_acc2(acc[j], K[c]);
+                Y[c] = rk_axpy(h2, K[c], y[c]);
+            }
+        }
+        exchange(Y, act);
+        if (act && !f.template eval<false>(Y, K, D, cx)) { st = GF_RAY_CUTOFF; act = false; }
+        if (act) {
+#pragma unroll
+            for (int j = 0; j < NO; ++j) {
+                const int c = W + kSplitWarps * j;
+                acc[j] = rk_acc2(acc[j], K[c]);
+                Y[c] = rk_axpy(dt, K[c], y[c]);
+            }
+        }
+        exchange(Y, act);
+        if (act && !f.template eval<false>(Y, K, D, cx)) { st = GF_RAY_CUTOFF; act = false; }
+        double yn[6];
+        if (act) {
+#pragma unroll
+            for (int j = 0; j < NO; ++j) {
+                const int c = W + kSplitWarps * j;
+                yn[c] = __dadd_rn(y[c], rk_inc(h6, acc[j], K[c]));
+            }
+        }
+        exchange(yn, act);
+        if (act) {
+            if (!finite6(yn)) {
+                st = GF_RAY_NONFINITE;
+                act = false;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) y[c] = yn[c];
+                ++s;
+                if (radius2 > 0.0 && norm2_fixed(y) > radius2) {
+                    st = GF_RAY_EXITED;
+                    act = false;
+                }
+            }
+        }
+    }
+    if (started) {
+#pragma unroll
+        for (int j = 0; j < NO; ++j) r.y[(W + kSplitWarps * j) * r.ld + i] = y[W + kSplitWarps * j];
+        if constexpr (W == 0) {
+            double K[6], D;
+            f.template eval<true>(y, K, D, cx);
+            ++evals;
+            dm = max_abs(dm, D);
+            if (r.d_res) r.d_res[i] = fabs(D);
+            if (r.d_max) r.d_max[i] = dm;
+            if (s > 0) r.t[i] = __dadd_rn(r.t[i], __dmul_rn((double)s, dt64));
+            r.steps[i] += (int32_t)s;
+            r.status[i] = st;
+        }
+    }
+    if constexpr (W == 0) add_work(counters, evals, cx.live);
+}
+
+template <int KIND, int W = 0>
+__device__ __forceinline__ void rk4_split_dispatch(int w, const MediumParams &m, const RaysView<double> &r,
+                                                   const Omega<double> &om, const double dt, const int64_t n_steps,
+                                                   const double radius2, const int64_t every, double *ckpt,
+                                                   unsigned long long *counters, const double *sb,
+                                                   EvalCtx<double> &cx, double (*xb)[6][32])
+{
+    if constexpr (W < kSplitWarps) {
+        if (w == W)
+            rk4_split_warp<KIND, W>(m, r, om, dt, dt, n_steps, radius2, every, ckpt, counters, sb, cx, xb);
+        else
+            rk4_split_dispatch<KIND, W + 1>(w, m, r, om, dt, n_steps, radius2, every, ckpt, counters, sb, cx, xb);
+    }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(32 * kSplitWarps, 1)
+rk4_split_kernel(const MediumParams m, const RaysView<double> r, const Omega<double> om, const double dt,
+                 const int64_t n_steps, const double radius2, const int64_t every, double *__restrict__ ckpt,
+                 unsigned long long *counters)
+{
+    __shared__ __align__(16) double sb[kBlobStride * GF_MAX_BLOBS];
+    __shared__ double sT[kExpTabN];
+    __shared__ float sp[4 * GF_MAX_BLOBS];
+    __shared__ double xb[2][6][32];
+    stage_blobs<double>(m, sb);
+    stage_pretest(m, sp);
+    stage_exp_table(sT);
+    __syncthreads();
+    EvalCtx<double> cx;
+    cx.T = sT;
+    cx.pre = sp;
+    rk4_split_dispatch<KIND>((int)(threadIdx.x >> 5), m, r, om, dt, n_steps, radius2, every, ckpt, counters, sb,
+                             cx, xb);
 }
 
 // k = s d with D(x, s d, w) = 0, s = w sqrt(eps / q).
@@ -402,9 +584,20 @@ static cudaError_t rk4_launch(const MediumParams &m, const gf_rays &r, double om
                               int64_t n_steps, double radius, int64_t every, double *ckpt,
                               cudaStream_t s)
 {
+    const R r2 = radius > 0 ? (R)(radius * radius) : (R)0;
+    if constexpr (sizeof(R) == 8 && !DF && KIND != K_SPLINE && KIND != K_COLD) {
+        // few rays: three warps per 32 rays while they fit one per SM sub-partition
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            kSplitWarps * ((r.n + 31) / 32) <= 4 * (int64_t)sms) {
+            rk4_split_kernel<KIND><<<(unsigned)((r.n + 31) / 32), 32 * kSplitWarps, 0, s>>>(
+                m, view<R>(r), make_omega<R>(omega), dt, n_steps, r2, every, ckpt, work_counters());
+            return cudaGetLastError();
+        }
+    }
     const int block = rk4_block(rk4_kernel<R, KIND, DF>, r.n);
     const int64_t blocks = (r.n + block - 1) / block;
-    const R r2 = radius > 0 ? (R)(radius * radius) : (R)0;
     rk4_kernel<R, KIND, DF><<<(unsigned)blocks, block, 0, s>>>(m, view<R>(r), make_omega<R>(omega), (R)dt,
                                                                dt, n_steps, r2, every, ckpt, work_counters());
     return cudaGetLastError();

@@ -61,6 +61,43 @@ def test_luneburg_focus_on_gpu():
     np.testing.assert_allclose(np.linalg.norm(g.y[:, 3:], axis=1), 1.0, atol=5e-3)
 
 
+def _split_threshold_rays():
+    """Largest ray count the component-split kernel takes: three warps per 32
+    rays while they fit one warp per SM sub-partition (4 per SM)."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    return (4 * sms // 3) * 32
+
+
+@pytest.mark.parametrize("kind", ["luneburg", "grin", "homog"])
+def test_few_rays_split_kernel_matches_per_ray_kernel_bitwise(kind):
+    """A trace of few rays runs three warps per 32 rays (each warp advances two
+    components, the stage points exchanged through shared memory); a trace of
+    many rays runs one thread per ray.  Both must return the same bits: the
+    first n rays of an 8n-ray trace against the same n rays alone, including
+    checkpoints, d_res/d_max, statuses and step counts, with exits at r = 1.2
+    (Luneburg), blobs and the pre-test (GRIN) and a ragged tail."""
+    if kind == "luneburg":
+        wl = W.luneburg(n=1000)
+        spec, n_steps, dt, radius = wl.medium, 3000, 1e-3, 1.2
+    elif kind == "grin":
+        wl = W.grin(n=1000)
+        spec, n_steps, dt, radius = wl.medium, 1500, wl.dt, 0.0
+    else:
+        wl = W.luneburg(n=1000)
+        spec, n_steps, dt, radius = dict(kind="homog", n_h=1.3), 2000, 2e-3, 1.5
+    k0 = _onshell(spec, wl.x0, wl.d)
+    n = wl.x0.shape[0]
+    assert n <= _split_threshold_rays() < 8 * n
+    few = gpu_rk4(spec, wl.x0, k0, 1.0, dt, n_steps, radius=radius, ckpt_every=64)
+    many = gpu_rk4(spec, np.tile(wl.x0, (8, 1)), np.tile(k0, (8, 1)), 1.0, dt, n_steps, radius=radius,
+                   ckpt_every=64)
+    for name in ("y", "t", "status", "steps", "dres", "dmax"):
+        assert np.array_equal(getattr(few, name), getattr(many, name)[:n], equal_nan=True), name
+    assert np.array_equal(few.ckpt, many.ckpt[:, :, :n], equal_nan=True)
+    if kind != "grin":
+        assert (few.status == 1).sum() > 0    # GF_RAY_EXITED: rays left the sphere of radius r
+
+
 def test_grin_f64_parity_ragged():
     """GRIN + 16 blobs, 1000 rays (7 full blocks + a tail of 104), 10,000 steps."""
     wl = W.grin(n=1000)
