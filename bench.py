@@ -261,16 +261,17 @@ def run_reference(a):
 
 # Algorithmic FP64 flops (add/mul 1, fma 2) of the fused RK4 kernel, per unit
 # of work; units are counted exactly by an untimed pass with work counters.
-#   live blob term  26: x - c (3), |x - c|^2 (5), exponent (1), table exp (8: a
-#                       base-2 table exp at FP64 accuracy -- exact reduction 1,
-#                       degree-3 polynomial 5, table fma 2), A e, n^2 +=,
+#   live blob term  21: x - c (3), |x - c|^2 (5), exponent (1), table exp (3:
+#                       the FP64 part of the base-2 table exp at FP64 accuracy,
+#                       one addition and the table fma; its reduction and
+#                       polynomial run on the FP32 pipes), A e, n^2 +=,
 #                       2 s A e (3), grad += (6)
 #   culled term      9: x - c, |x - c|^2 and the exponent, then skipped
 #   evaluation      51: GRIN base n^2 and gradient (8), 1/n^2 as 8, the two
 #                       prefactors (2), f (6), stage update and RK4 accumulate (24),
 #                       D at one evaluation in four (5/4 rounded up to 3)
 #   ray-step        18: final y + dt/6 (...) update
-FLOPS_LIVE_TERM, FLOPS_CULLED_TERM, FLOPS_EVAL, FLOPS_STEP = 26, 9, 51, 18
+FLOPS_LIVE_TERM, FLOPS_CULLED_TERM, FLOPS_EVAL, FLOPS_STEP = 21, 9, 51, 18
 
 # DRAM bytes (read + write) of one rk4_kernel<double, GRIN> launch over
 # 1,048,576 rays, from an ncu capture of the same launch shape (the kernel
@@ -845,7 +846,7 @@ def run_gpu(a):
                      "kernel": kname, "kernel_ms": 1e3 * k_sec,
                      "counted_work": {"achieved": achieved_counted, "frac": achieved_counted / peak,
                                       "flops_per_launch": flops,
-                                      "model": "live blob term 26 (8-flop table exponential), culled term 9, "
+                                      "model": "live blob term 21 (3 FP64 flops of the table exponential), culled term 9, "
                                                "evaluation 51, ray-step 18, from the kernel's work counters"},
                      "evaluations": evals, "blob_terms_live": live,
                      "blob_terms_total": evals * n_blobs,

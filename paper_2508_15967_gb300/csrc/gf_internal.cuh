@@ -174,33 +174,74 @@ __device__ __forceinline__ double recip_pos_q(double v)
     return fma(r, fma(-v, r, 1.0), r);
 }
 
+// The bits of a double a below the 24 that narrow_trunc(a) keeps, as two
+// floats with a's sign: a = narrow_trunc(a) + t1 + t2 exactly, t1 holding the
+// next 23 significand bits and t2 the last 6, for 2^-74 <= |a| < 2^11.
+// Smaller |a| give t1 = t2 = 0 (the bits dropped are below 2^-97).  Each part
+// is a small integer turned into a float by the 2^23 bias trick and scaled by a
+// power of two built on its bit pattern: integer and FP32 operations only.
+__device__ __forceinline__ void tail_floats(double a, float &t1, float &t2)
+{
+    const unsigned hi = (unsigned)__double2hiint(a), lo = (unsigned)__double2loint(a);
+    const unsigned eb = (hi >> 20) & 0x7FFu;                 // biased exponent E + 1023
+    const unsigned sgn = hi & 0x80000000u;
+    const float m1 = __fsub_rn(__uint_as_float(0x4B000000u | ((lo >> 6) & 0x7FFFFFu)), 8388608.0f);
+    const float m2 = __fsub_rn(__uint_as_float(0x4B000000u | (lo & 0x3Fu)), 8388608.0f);
+    const bool ok = eb - 949u < 85u;                          // 949 <= eb <= 1033
+    const float s1 = __uint_as_float(sgn | ((eb - 942u) << 23));   // +-2^(E - 46)
+    const float s2 = __uint_as_float(sgn | ((eb - 948u) << 23));   // +-2^(E - 52)
+    t1 = ok ? __fmul_rn(m1, s1) : 0.0f;
+    t2 = ok ? __fmul_rn(m2, s2) : 0.0f;
+}
+
 // 2^a for a <= 0 (finite or -inf; a <= -1021 returns 0, below four times the
-// smallest normal double), table-driven after Tang (ACM TOMS 1989) in base 2,
-// where the argument reduction is exact: with k = round(2048 a) and
-// r = a - k/2048, 2^a = 2^(k >> 11) * 2^((k & 2047)/2048) * 2^r and
-// 2^r - 1 = r (c1 + r (c2 + r c3)), c_n = ln2^n / n! (truncation below
-// (r ln2)^4 / 24).  k is found in FP32 from a truncated to float (2048 |a| <
-// 2^22, so adding 1.5 * 2^23 rounds it to an integer); it may then be one off
-// the nearest integer, which leaves |r| <= 2^-12 + 2^-23 |a| (2.52e-4 for
-// |a| <= 64, 3.7e-4 up to 1021).  -k/2048 is exact in float and widened
-// to double on its bit pattern (zero widens to 2^-127, which moves r by far
-// less than an ulp of 2^a), and r = a + (-k/2048) is exact.  Five FP64
-// operations (r, the polynomial's three, the table product); the rest runs
-// on the FP32 and integer pipes, which the FP64-bound evaluator leaves idle.
-// Error against 2^a: table and final rounding 0.5 ulp each, truncation
-// below 3.9e-17 relative for |a| <= 64 (1.8e-16 up to 1021), i.e. under
-// 1.35 ulp (2.6 ulp); the blob terms only use -58.5 <= a <= 0.
+// smallest normal double), table-driven after Tang (ACM TOMS 1989) in base 2:
+// with k = round(2048 a) and r = a - k/2048, 2^a = 2^(k >> 11) *
+// 2^((k & 2047)/2048) * 2^r.  Only the table product and one addition run on
+// the FP64 pipe; the reduction and 2^r - 1 are carried on the FP32 and
+// integer pipes, which the FP64-bound evaluators leave idle:
+//  - a is split exactly into three floats, a0 = a truncated to 24 bits
+//    (narrow_trunc) and the tail a1 + a2 (tail_floats);
+//  - k is found from a0 (2048 |a0| < 2^22, so adding 1.5 * 2^23 rounds it to
+//    an integer); -k/2048 is exact in float, and so is s = a0 - k/2048 (both
+//    are multiples of a0's ulp and |s| <= 2^-12 + 2^-23 |a|);
+//  - r = s + a1 + a2 as a float pair (rh, rl) by Knuth's two-sum, exact up
+//    to the rounding of rl (below 2^-60 absolute);
+//  - t = r ln2 as a float pair from ln2 = hi + lo (Dekker's product with an
+//    FMA), and e^t - 1 = t + t^2/2 + t^3/6 + t^4/24 as a float pair (Ph, Pl):
+//    t^2/2 with its exact product error, the t^3 and t^4 terms in float;
+//    |t| <= 2.6e-4 ln2 for |a| <= 1021, so the omitted t^5/120 is below 2e-21
+//    and the pair is within ~2^-59 of 2^r - 1;
+//  - P = Ph + Pl in FP64, then v = T_j + T_j P (one FMA).
+// Error against 2^a: table and final rounding 0.5 ulp each plus ~0.03 ulp,
+// under 1.05 ulp over the whole range; the blob terms use -58.5 <= a <= 0.
 __device__ __forceinline__ double exp2_tab(double a, const double *__restrict__ T)
 {
-    const float af = narrow_trunc(a);
-    const float tf = fmaf(af, 2048.0f, 12582912.0f);            // 1.5 * 2^23 + k
+    const float a0 = narrow_trunc(a);
+    float a1, a2;
+    tail_floats(a, a1, a2);
+    const float tf = fmaf(a0, 2048.0f, 12582912.0f);            // 1.5 * 2^23 + k
     const int k = __float_as_int(tf) - 0x4B400000;               // bits of 1.5 * 2^23
-    const unsigned wb = __float_as_uint(fmaf(tf, -0x1p-11f, 6144.0f));   // -k/2048 >= 0, exact
-    const double w = __hiloint2double((int)((wb >> 3) + ((1023u - 127u) << 20)), (int)(wb << 29));
-    const double r = a + w;
-    const double p = r * fma(r, fma(r, kExp2C3, kExp2C2), kExp2C1);     // 2^r - 1
+    const float w = fmaf(tf, -0x1p-11f, 6144.0f);                // -k/2048, exact
+    const float s = __fadd_rn(a0, w);                             // a0 - k/2048, exact
+    // r = s + a1 + a2: two-sum of s and a1, then the small a2
+    const float rh = __fadd_rn(s, a1);
+    const float bb = __fsub_rn(rh, s);
+    const float rl = __fadd_rn(__fadd_rn(__fsub_rn(s, __fsub_rn(rh, bb)), __fsub_rn(a1, bb)), a2);
+    // t = r ln2 = th + tl
+    const float th = __fmul_rn(rh, kLn2FHi);
+    const float tl = fmaf(rl, kLn2FHi, fmaf(rh, kLn2FLo, fmaf(rh, kLn2FHi, -th)));
+    // e^t - 1 = Ph + Pl
+    const float p2 = __fmul_rn(th, th);
+    const float e2 = fmaf(th, th, -p2);                           // th^2 = p2 + e2 exactly
+    const float h = __fmul_rn(0.5f, p2);
+    const float Ph = __fadd_rn(th, h);
+    const float l0 = __fsub_rn(h, __fsub_rn(Ph, th));             // fast two-sum, |th| >= |h|
+    const float c34 = __fmul_rn(p2, fmaf(th, kInv6F, __fmul_rn(p2, kInv24F)));   // t^3/6 + t^4/24
+    const float Pl = __fadd_rn(l0, __fadd_rn(tl, fmaf(0.5f, e2, fmaf(th, tl, c34))));
+    const double P = __dadd_rn(widen(Ph), widen(Pl));
     const double Tj = T[k & (kExpTabN - 1)];
-    const double v = fma(Tj, p, Tj);
+    const double v = fma(Tj, P, Tj);
     const int hi = __double2hiint(v) + ((k >> 11) << 20);
     const unsigned ahi = (unsigned)__double2hiint(a);
     // a <= -1021 (sign set, |a| >= 1021: hi word >= that of -1021.0), -inf and

@@ -113,11 +113,18 @@ def _strict_gate(e, same, what):
 def _conditioned_gate(e, same, e_ref, same_ref, what):
     """GPU-vs-oracle errors e no larger than the oracle-vs-perturbed-oracle
     errors e_ref at every quantile (2x + 1e-12), and the oracle's step counts
-    kept on at least as many rays as the perturbed oracle keeps them (- 2%)."""
+    kept on at least as many rays as the perturbed oracle keeps them (- 2%).
+    Among the rays that keep the oracle's step counts, at least as large a
+    share lies within 1e-9 of the oracle as for the perturbed oracle (- 2%):
+    the same step sequence does not fix the step sizes, whose rounding moves
+    the kink-crossing error, so 1e-9 on every such ray is not a property
+    even of the oracle against itself."""
     for q in QUANTILES:
         a, b = np.quantile(e, q), np.quantile(e_ref, q)
         assert a <= 2 * b + 1e-12, f"{what}: quantile {q}: {a:.3e} against the oracle's own {b:.3e}"
     assert same.mean() >= same_ref.mean() - 0.02, (what, same.mean(), same_ref.mean())
+    within, within_ref = (e[same] <= STRICT_TOL).mean(), (e_ref[same_ref] <= STRICT_TOL).mean()
+    assert within >= within_ref - 0.02, f"{what}: same-sequence rays within 1e-9: {within:.3f} < {within_ref:.3f}"
 
 
 def _rejections_match(g, o, min_share, total=True):

@@ -2,7 +2,7 @@
 against their mathematical definitions: the 2^(j/2048) table of the FP64 blob
 exponential (correctly rounded doubles), its float-pair copy for the
 double-float mode (hi = RN_float(v), lo = RN_float(v - hi)), the polynomial
-and reduction constants, and that the committed include files are exactly
+and reduction constants (floats of the FP64 exponential's reduced argument), and that the committed include files are exactly
 what their generator scripts print."""
 from __future__ import annotations
 
@@ -62,9 +62,13 @@ def test_fp64_exponential_table_and_constants():
     for j, v in enumerate(values):
         exact = (Decimal(j) / 2048 * ln2).exp()
         assert v == float(exact), j                  # correctly rounded 2^(j/2048)
-    assert _const(text, "kExp2C1") == float(ln2)
-    assert _const(text, "kExp2C2") == float(ln2 ** 2 / 2)
-    assert _const(text, "kExp2C3") == float(ln2 ** 3 / 6)
+    # t = r ln2 is formed as a float pair: ln2 = hi + lo to within 2^-48 ln2;
+    # the Taylor coefficients of e^t - 1 beyond t^2/2 are floats
+    l2h, l2l = _const(text, "kLn2FHi"), _const(text, "kLn2FLo")
+    assert l2h == _f32(ln2) and l2l == _f32(ln2 - Decimal(l2h))
+    assert abs(Decimal(l2h) + Decimal(l2l) - ln2) <= Decimal(2) ** -48 * ln2
+    assert _const(text, "kInv6F") == _f32(Decimal(1) / 6)
+    assert _const(text, "kInv24F") == _f32(Decimal(1) / 24)
     # natural-base reduction of the generated-medium exponential: the high part
     # of ln2/2048 has few enough bits that k * hi is exact for |k| < 2^22, and
     # hi + lo is ln2/2048 to within the rounding of lo
