@@ -261,17 +261,17 @@ def run_reference(a):
 
 # Algorithmic FP64 flops (add/mul 1, fma 2) of the fused RK4 kernel, per unit
 # of work; units are counted exactly by an untimed pass with work counters.
-#   live blob term  21: x - c (3), |x - c|^2 (5), exponent (1), table exp (3:
-#                       the FP64 part of the base-2 table exp at FP64 accuracy,
-#                       one addition and the table fma; its reduction and
-#                       polynomial run on the FP32 pipes), A e, n^2 +=,
-#                       2 s A e (3), grad += (6)
+#   live blob term  18: x - c (3), |x - c|^2 (5), exponent (1), A e, n^2 +=,
+#                       2 s A e (3), grad += (6); the base-2 table exp at FP64
+#                       accuracy takes no FP64 operation in this kernel (its
+#                       reduction and polynomial run on the FP32 pipes, the
+#                       table product in integer arithmetic)
 #   culled term      9: x - c, |x - c|^2 and the exponent, then skipped
 #   evaluation      51: GRIN base n^2 and gradient (8), 1/n^2 as 8, the two
 #                       prefactors (2), f (6), stage update and RK4 accumulate (24),
 #                       D at one evaluation in four (5/4 rounded up to 3)
 #   ray-step        18: final y + dt/6 (...) update
-FLOPS_LIVE_TERM, FLOPS_CULLED_TERM, FLOPS_EVAL, FLOPS_STEP = 21, 9, 51, 18
+FLOPS_LIVE_TERM, FLOPS_CULLED_TERM, FLOPS_EVAL, FLOPS_STEP = 18, 9, 51, 18
 
 # DRAM bytes (read + write) of one rk4_kernel<double, GRIN> launch over
 # 1,048,576 rays, from an ncu capture of the same launch shape (the kernel
@@ -309,7 +309,8 @@ MODEL_COLD_RAY_STEP = 4 * (2 * 49 + 83 + 24) + 18
 MODEL_ADJ_BWD_RAY_STEP = MODEL_ADJ_FWD_RAY_STEP + 4 * (64 * 27 + 50) + 6
 MODEL_TEXT = {
     "grin": f"{MODEL_GRIN_RAY_STEP} flops per ray-step: 4 evaluations x (16 blob terms x 18 + index law 6 + "
-            "right-hand side 8) + RK4 combination 84; exponentials and divisions not counted",
+            "right-hand side 8) + RK4 combination 84; every blob term charged, also those the kernel skips as "
+            "negligible (exponent below -58.5 in base 2), exponentials and divisions not counted",
     "dopri5": f"{MODEL_DOPRI5_ATTEMPT} flops per attempted step: 6 evaluations x (8 blob terms x 18 + 13) "
               "+ stage combination and error norm 150; exponentials and divisions not counted",
     "adj_fwd": f"{MODEL_ADJ_FWD_RAY_STEP} flops per ray-step: 4 evaluations x (64 blob terms x 18 + 14) + 84",
@@ -846,7 +847,7 @@ def run_gpu(a):
                      "kernel": kname, "kernel_ms": 1e3 * k_sec,
                      "counted_work": {"achieved": achieved_counted, "frac": achieved_counted / peak,
                                       "flops_per_launch": flops,
-                                      "model": "live blob term 21 (3 FP64 flops of the table exponential), culled term 9, "
+                                      "model": "live blob term 18 (the table exponential takes no FP64 flop), culled term 9, "
                                                "evaluation 51, ray-step 18, from the kernel's work counters"},
                      "evaluations": evals, "blob_terms_live": live,
                      "blob_terms_total": evals * n_blobs,

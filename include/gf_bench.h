@@ -46,12 +46,21 @@ gf_status gf_bench_set_counters(unsigned long long *counters);
 /*
  * gf_bench_exp -- evaluate the library's table-driven base-2 exponential 2^a
  * (used for every Gaussian-blob term of the FP64 evaluator, whose rows carry
- * the exponent in base 2; defined for a <= 0, returning 0 for a <= -1021)
- * and CUDA's exp2 on n device doubles `in`, writing out_lib and out_cuda
- * (device, n each), so that tests can bound its error.  Stream-ordered on
- * `stream`.  Errors: GF_ERR_INVALID_ARG (n < 0, non-device pointers), GF_ERR_CUDA.
+ * the exponent in base 2; defined for a <= 0, returning 0 for a <= -1021),
+ * in the form that uses no FP64 operation, and CUDA's exp2 on n device
+ * doubles `in`, writing out_lib and out_cuda (device, n each), so that tests
+ * can bound its error.  Stream-ordered on `stream`.
+ * Errors: GF_ERR_INVALID_ARG (n < 0, non-device pointers), GF_ERR_CUDA.
  */
 gf_status gf_bench_exp(const double *in, double *out_lib, double *out_cuda, int64_t n, void *stream);
+
+/*
+ * gf_bench_exp_fp -- the same exponential in its other form (the table
+ * product as one FP64 fused multiply-add, for kernels whose FP32 and integer
+ * pipes are busy), on n device doubles `in`, writing `out` (device); it must
+ * return gf_bench_exp's bits exactly.  Errors: GF_ERR_INVALID_ARG, GF_ERR_CUDA.
+ */
+gf_status gf_bench_exp_fp(const double *in, double *out, int64_t n, void *stream);
 
 /*
  * gf_bench_exp_df -- evaluate the double-float base-2 exponential 2^a of the

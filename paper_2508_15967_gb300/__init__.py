@@ -88,6 +88,7 @@ def lib() -> C.CDLL:
             "gf_bench_set_counters": ([P], I32),
             "gf_bench_exp": ([P, P, P, I64, P], I32),
             "gf_bench_exp_df": ([P, P, I64, P], I32),
+            "gf_bench_exp_fp": ([P, P, I64, P], I32),
             "gf_bench_recip": ([P, P, P, I64, P], I32),
             "gf_fault_inject": ([I64], I32),
             "gf_bench_live_allocations": ([P], I64),
@@ -470,6 +471,14 @@ def gf_bench_exp(a: torch.Tensor):
     o1, o2 = torch.empty_like(a), torch.empty_like(a)
     _check("gf_bench_exp", lib().gf_bench_exp(_ptr(a), _ptr(o1), _ptr(o2), a.numel(), _stream(None)))
     return o1, o2
+
+
+def gf_bench_exp_fp(a: torch.Tensor) -> torch.Tensor:
+    """The library's 2^a in its FP64-FMA form, of a float64 device tensor."""
+    a = a.contiguous()
+    o = torch.empty_like(a)
+    _check("gf_bench_exp_fp", lib().gf_bench_exp_fp(_ptr(a), _ptr(o), a.numel(), _stream(None)))
+    return o
 
 
 def gf_bench_exp_df(a: torch.Tensor) -> torch.Tensor:

@@ -122,6 +122,7 @@ __global__ void __launch_bounds__(kAdjBlock, 8) adjoint_kernel(
     EvalCtx<double> cx;
     cx.T = sT;
     cx.pre = sp;
+    cx.exp_fp = true;   // the sweep keeps the FP32 pipes busy: the FP64-pipe form (same bits)
     long long work[4] = {0, 0, 0, 0};   // recomputed evaluations, their blob terms, swept blob terms,
                                         // segment ends that differ from the next checkpoint
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -68,8 +68,18 @@ __global__ void exp_check_kernel(const double *in, double *out_lib, double *out_
     __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    out_lib[i] = exp2_tab(in[i], sT);
+    out_lib[i] = exp2_tab_int(in[i], sT);
     out_cuda[i] = exp2(in[i]);
+}
+
+__global__ void exp_fp_check_kernel(const double *in, double *out, int64_t n)
+{
+    __shared__ double sT[kExpTabN];
+    stage_exp_table(sT);
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = exp2_tab_fp(in[i], sT);
 }
 
 __global__ void recip_check_kernel(const double *in, double *out_recip, float *out_narrow, int64_t n)
@@ -115,6 +125,19 @@ extern "C" gf_status gf_bench_exp(const double *in, double *out_lib, double *out
         return s;
     gf::exp_check_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(in, out_lib, out_cuda, n);
     return gf::cuda_status(cudaGetLastError(), "gf_bench_exp launch");
+}
+
+extern "C" gf_status gf_bench_exp_fp(const double *in, double *out, int64_t n, void *stream)
+{
+    if (n < 0) {
+        gf::set_error("gf_bench_exp_fp: n < 0");
+        return GF_ERR_INVALID_ARG;
+    }
+    if (n == 0) return GF_OK;
+    gf_status s;
+    if ((s = gf::check_device_ptr(in, "in")) != GF_OK || (s = gf::check_device_ptr(out, "out")) != GF_OK) return s;
+    gf::exp_fp_check_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(in, out, n);
+    return gf::cuda_status(cudaGetLastError(), "gf_bench_exp_fp launch");
 }
 
 extern "C" gf_status gf_bench_exp_df(const double *in, double *out, int64_t n, void *stream)

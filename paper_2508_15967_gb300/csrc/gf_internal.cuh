@@ -194,28 +194,38 @@ __device__ __forceinline__ void tail_floats(double a, float &t1, float &t2)
     t2 = ok ? __fmul_rn(m2, s2) : 0.0f;
 }
 
-// 2^a for a <= 0 (finite or -inf; a <= -1021 returns 0, below four times the
-// smallest normal double), table-driven after Tang (ACM TOMS 1989) in base 2:
-// with k = round(2048 a) and r = a - k/2048, 2^a = 2^(k >> 11) *
-// 2^((k & 2047)/2048) * 2^r.  Only the table product and one addition run on
-// the FP64 pipe; the reduction and 2^r - 1 are carried on the FP32 and
-// integer pipes, which the FP64-bound evaluators leave idle:
-//  - a is split exactly into three floats, a0 = a truncated to 24 bits
-//    (narrow_trunc) and the tail a1 + a2 (tail_floats);
-//  - k is found from a0 (2048 |a0| < 2^22, so adding 1.5 * 2^23 rounds it to
-//    an integer); -k/2048 is exact in float, and so is s = a0 - k/2048 (both
-//    are multiples of a0's ulp and |s| <= 2^-12 + 2^-23 |a|);
-//  - r = s + a1 + a2 as a float pair (rh, rl) by Knuth's two-sum, exact up
-//    to the rounding of rl (below 2^-60 absolute);
-//  - t = r ln2 as a float pair from ln2 = hi + lo (Dekker's product with an
-//    FMA), and e^t - 1 = t + t^2/2 + t^3/6 + t^4/24 as a float pair (Ph, Pl):
-//    t^2/2 with its exact product error, the t^3 and t^4 terms in float;
-//    |t| <= 2.6e-4 ln2 for |a| <= 1021, so the omitted t^5/120 is below 2e-21
-//    and the pair is within ~2^-59 of 2^r - 1;
-//  - P = Ph + Pl in FP64, then v = T_j + T_j P (one FMA).
-// Error against 2^a: table and final rounding 0.5 ulp each plus ~0.03 ulp,
-// under 1.05 ulp over the whole range; the blob terms use -58.5 <= a <= 0.
-__device__ __forceinline__ double exp2_tab(double a, const double *__restrict__ T)
+// x 2^63 truncated toward zero, as a signed 64-bit integer, for a float
+// |x| < 2^-11 (its significand shifted into place; zero and subnormals give 0).
+__device__ __forceinline__ long long fix63(float x)
+{
+    const unsigned b = __float_as_uint(x);
+    const unsigned e = (b >> 23) & 0xFFu;
+    const unsigned long long m = (b & 0x7FFFFFu) | 0x800000u;
+    const int sh = (int)e - 87;                                   // x = m 2^(e - 150)
+    unsigned long long v = sh >= 0 ? m << min(sh, 63) : m >> min(-sh, 63);   // shifts kept below 64
+    v = e == 0u ? 0ull : v;
+    return (b >> 31) ? -(long long)v : (long long)v;
+}
+
+// x truncated toward zero to a multiple of 2^-63 (fix63(x) 2^-63 as a float:
+// the fraction bits below 2^-63 cleared; zero and subnormals give 0).
+__device__ __forceinline__ float trunc63(float x)
+{
+    const unsigned b = __float_as_uint(x);
+    const int nclr = 87 - (int)((b >> 23) & 0xFFu);              // fraction bits below 2^-63
+    const unsigned keep = nclr <= 0 ? 0xFFFFFFFFu : (nclr >= 24 ? 0u : ~((1u << nclr) - 1u));
+    return __uint_as_float(b & keep);
+}
+
+// The reduction and polynomial of the blob exponential (exp2_tab_int,
+// exp2_tab_fp), on the FP32 and integer pipes: k = round(2048 a) and
+// e^t - 1 = ph + pl with t = (a - k/2048) ln2.
+struct Exp2Red {
+    int k;
+    float ph, pl;
+};
+
+__device__ __forceinline__ Exp2Red exp2_reduce(double a)
 {
     const float a0 = narrow_trunc(a);
     float a1, a2;
@@ -231,22 +241,76 @@ __device__ __forceinline__ double exp2_tab(double a, const double *__restrict__ 
     // t = r ln2 = th + tl
     const float th = __fmul_rn(rh, kLn2FHi);
     const float tl = fmaf(rl, kLn2FHi, fmaf(rh, kLn2FLo, fmaf(rh, kLn2FHi, -th)));
-    // e^t - 1 = Ph + Pl
+    // e^t - 1 = ph + pl
     const float p2 = __fmul_rn(th, th);
     const float e2 = fmaf(th, th, -p2);                           // th^2 = p2 + e2 exactly
     const float h = __fmul_rn(0.5f, p2);
-    const float Ph = __fadd_rn(th, h);
-    const float l0 = __fsub_rn(h, __fsub_rn(Ph, th));             // fast two-sum, |th| >= |h|
+    const float ph = __fadd_rn(th, h);
+    const float l0 = __fsub_rn(h, __fsub_rn(ph, th));             // fast two-sum, |th| >= |h|
     const float c34 = __fmul_rn(p2, fmaf(th, kInv6F, __fmul_rn(p2, kInv24F)));   // t^3/6 + t^4/24
-    const float Pl = __fadd_rn(l0, __fadd_rn(tl, fmaf(0.5f, e2, fmaf(th, tl, c34))));
-    const double P = __dadd_rn(widen(Ph), widen(Pl));
-    const double Tj = T[k & (kExpTabN - 1)];
-    const double v = fma(Tj, P, Tj);
-    const int hi = __double2hiint(v) + ((k >> 11) << 20);
+    const float pl = __fadd_rn(l0, __fadd_rn(tl, fmaf(0.5f, e2, fmaf(th, tl, c34))));
+    return Exp2Red{k, ph, pl};
+}
+
+// 2^a for a <= 0 (finite or -inf; a <= -1021 returns 0, below four times the
+// smallest normal double), table-driven after Tang (ACM TOMS 1989) in base 2:
+// with k = round(2048 a) and r = a - k/2048, 2^a = 2^(k >> 11) *
+// 2^((k & 2047)/2048) * 2^r, in two forms that return the same bits:
+// exp2_tab_int uses no FP64 operation (for kernels bound by the FP64 pipe),
+// exp2_tab_fp uses two (for kernels whose FP32 and integer pipes are busy).
+// Both carry the reduction and 2^r - 1 in float pairs (exp2_reduce):
+//  - a is split exactly into three floats, a0 = a truncated to 24 bits
+//    (narrow_trunc) and the tail a1 + a2 (tail_floats);
+//  - k is found from a0 (2048 |a0| < 2^22, so adding 1.5 * 2^23 rounds it to
+//    an integer); -k/2048 is exact in float, and so is s = a0 - k/2048 (both
+//    are multiples of a0's ulp and |s| <= 2^-12 + 2^-23 |a|);
+//  - r = s + a1 + a2 as a float pair (rh, rl) by Knuth's two-sum, exact up
+//    to the rounding of rl (below 2^-60 absolute);
+//  - t = r ln2 as a float pair from ln2 = hi + lo (Dekker's product with an
+//    FMA), and e^t - 1 = t + t^2/2 + t^3/6 + t^4/24 as a float pair (ph, pl):
+//    t^2/2 with its exact product error, the t^3 and t^4 terms in float;
+//    |t| <= 2.6e-4 for |a| <= 1021, so the omitted t^5/120 is below 2e-21
+//    and the pair is within ~2^-59 of 2^r - 1.
+// Then P = trunc(ph) + trunc(pl), each truncated toward zero to a multiple of
+// 2^-63 (|P| < 2^-11, so P is a multiple of 2^-63 below 2^52 of them: exact
+// in FP64 and in a 64-bit integer), and the result is T (1 + P) rounded to
+// nearest even, T = 2^((k & 2047)/2048) from the 2048-entry table, scaled by
+// 2^(k >> 11) on the exponent field.  Error against 2^a: table and final
+// rounding 0.5 ulp each plus ~0.03 ulp, under 1.05 ulp over the whole range;
+// the blob terms use -58.5 <= a <= 0.
+__device__ __forceinline__ double exp2_tab_fp(double a, const double *__restrict__ T)
+{
+    const Exp2Red e = exp2_reduce(a);
+    const double P = __dadd_rn(widen(trunc63(e.ph)), widen(trunc63(e.pl)));   // exact
+    const double Tj = T[e.k & (kExpTabN - 1)];
+    const double v = fma(Tj, P, Tj);                                         // RN(T (1 + P))
+    const int hi = __double2hiint(v) + ((e.k >> 11) << 20);
     const unsigned ahi = (unsigned)__double2hiint(a);
     // a <= -1021 (sign set, |a| >= 1021: hi word >= that of -1021.0), -inf and
     // NaN with the sign bit set flush to 0
     return ahi >= 0xC08FE800u ? 0.0 : __hiloint2double(hi, __double2loint(v));
+}
+
+// The same value in 64-bit integer arithmetic: with T = S 2^-52 (S its 53-bit
+// significand, T in [1, 2)) and U = 2^63 + P 2^63, T (1 + P) = S U 2^-115
+// exactly; the 117-bit product S U (high and low 64-bit words) is normalised
+// by its leading zeros and rounded to 53 bits, to nearest with ties to even
+// (round bit and sticky bits), as the FMA of exp2_tab_fp rounds it.
+__device__ __forceinline__ double exp2_tab_int(double a, const double *__restrict__ T)
+{
+    const Exp2Red e = exp2_reduce(a);
+    const long long P = fix63(e.ph) + fix63(e.pl);                   // exact, |P| < 2^52
+    const unsigned long long tb = (unsigned long long)__double_as_longlong(T[e.k & (kExpTabN - 1)]);
+    const unsigned long long S = (tb & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+    const unsigned long long U = 0x8000000000000000ull + (unsigned long long)P;
+    const unsigned long long hi = __umul64hi(S, U), lo = S * U;     // S U < 2^117
+    const int lz = __clzll((long long)hi) - 11;                      // 0, 1 or 2
+    const unsigned long long m = lz == 0 ? hi : (hi << lz) | (lo >> (64 - lz));
+    const unsigned long long r = lo << lz;                            // round bit, then sticky bits
+    const unsigned long long up = (r >> 63) & ((r << 1) != 0ull ? 1ull : (m & 1ull));
+    const long long bits = ((long long)(1023 - lz + (e.k >> 11)) << 52) + (long long)(m + up);
+    const unsigned ahi = (unsigned)__double2hiint(a);
+    return ahi >= 0xC08FE800u ? 0.0 : __longlong_as_double(bits);
 }
 
 // 2^a in FP32 with the hardware base-2 exponential (ex2.approx.ftz.f32:
@@ -388,6 +452,7 @@ struct EvalCtx {
     const float *dfb = nullptr;  // double-float blob rows (GF_F64X mode)
     const float *dfT = nullptr;  // double-float 2^(j/64) table (GF_F64X mode)
     int live = 0;                // blob terms evaluated (work counter)
+    bool exp_fp = false;         // blob exponentials by exp2_tab_fp (else exp2_tab_int; same bits)
 };
 
 // Stage the FP32 pre-test rows (sigma, -sigma c).
@@ -427,14 +492,15 @@ __device__ __forceinline__ bool pretest_negligible(const float *__restrict__ bp,
 // adds A G to n2 and (-2 ln2 sigma A) G u (= 2 s A G (x - c)) to g and counts
 // it in live.  Returns G, or 0 for a negligible term.
 __device__ __forceinline__ double blob_term_scaled(const double *__restrict__ b, int stride, const double *x,
-                                                   double &n2, double *g, const double *__restrict__ T, int &live)
+                                                   double &n2, double *g, const double *__restrict__ T, int &live,
+                                                   bool exp_fp)
 {
     const double sg = b[0];
     const double u0 = fma(sg, x[0], b[stride]), u1 = fma(sg, x[1], b[2 * stride]),
                  u2 = fma(sg, x[2], b[3 * stride]);
     const double a = fma(-u2, u2, fma(-u1, u1, -(u0 * u0)));
     if (below_cull(a)) return 0.0;
-    const double G = exp2_tab(a, T);
+    const double G = exp_fp ? exp2_tab_fp(a, T) : exp2_tab_int(a, T);
     n2 = fma(b[4 * stride], G, n2);
     const double c = b[5 * stride] * G;
     g[0] = fma(c, u0, g[0]);
@@ -511,7 +577,7 @@ __device__ __forceinline__ void iso_index(const MediumParams &m, const R *__rest
 #pragma unroll 2
         for (int j = 0; j < nb; ++j) {
             if (px.on && pretest_negligible(cx.pre + 4 * j * cx.pre_stride, cx.pre_stride, px)) continue;
-            blob_term_scaled(sb + kBlobStride * j * stride, stride, x, n2, g, cx.T, cx.live);
+            blob_term_scaled(sb + kBlobStride * j * stride, stride, x, n2, g, cx.T, cx.live, cx.exp_fp);
         }
     } else {
         // the same scaled form in FP32 with the hardware base-2 exponential

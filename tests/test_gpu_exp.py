@@ -48,6 +48,25 @@ def test_exp_error_bound_against_correct_rounding():
     assert (np.abs(lib - cuda) <= 3.0 * np.spacing(np.abs(cuda))).all()
 
 
+def test_exp_integer_and_fma_forms_return_the_same_bits():
+    """The form without FP64 operations (FP64-bound kernels) and the form with
+    the table product as an FP64 FMA (the adjoint's recomputation) must round
+    T (1 + P) identically: dense sweeps of the blob range, table-index and
+    binade boundaries, values near multiples of 2^-11, and the wide range."""
+    rng = np.random.default_rng(11)
+    j = np.arange(-2048 * 64, 1)
+    a = np.concatenate([-rng.uniform(0, 64, 400_000), -rng.uniform(64, 1020.99, 100_000),
+                        j / 2048.0, j / 2048.0 + 2.0 ** -40, j / 2048.0 - 2.0 ** -40,
+                        (j[:-1] + 0.5) / 2048.0, -np.abs(rng.normal(0, 1e-6, 20_000)),
+                        [0.0, -0.0, -1e-300, -5e-324, -2.0 ** -12, -58.5, -1021.0 + 1e-9]])
+    a = a[a <= 0]
+    t = torch.tensor(a, device="cuda")
+    lib, _ = gf.gf_bench_exp(t)
+    fp = gf.gf_bench_exp_fp(t)
+    same = torch.eq(lib.view(torch.int64), fp.view(torch.int64))
+    assert bool(same.all()), a[~same.cpu().numpy()][:8]
+
+
 def test_exp_flush_and_special_values():
     a = torch.tensor([-1021.0, -1021.5, -1075.0, -1e4, -float("inf"), 0.0, -0.0], device="cuda",
                      dtype=torch.float64)
