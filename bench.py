@@ -277,7 +277,7 @@ FLOPS_LIVE_TERM, FLOPS_CULLED_TERM, FLOPS_EVAL, FLOPS_STEP = 18, 9, 51, 18
 # 1,048,576 rays, from an ncu capture of the same launch shape (the kernel
 # loads and stores the ray state once, so the count does not depend on the
 # number of steps).  Valid only for the FP64 GRIN kernel as captured.
-TRAFFIC_BYTES_1M = 75_652_608 + 23_213_312
+TRAFFIC_BYTES_1M = 75_720_448 + 23_289_344
 
 
 def algorithmic_flops(evals: int, live: int, n_blobs: int, ray_steps: int) -> int:
