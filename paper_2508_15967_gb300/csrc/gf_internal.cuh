@@ -400,6 +400,16 @@ __device__ __forceinline__ void stage_blobs(const MediumParams &m, R *sb)
     }
 }
 
+// A 16-byte shared-memory load as one instruction (p 16-byte aligned, in
+// shared memory).
+__device__ __forceinline__ float4 lds128(const float4 *p)
+{
+    float4 v;
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+    return v;
+}
+
 // Packed FP32x2 arithmetic (two lanes of float per instruction on sm_100 and
 // later): d = a b + c, a b, and a + b, each half correctly rounded.
 __device__ __forceinline__ unsigned long long pk2(float2 v)
@@ -591,17 +601,20 @@ __device__ __forceinline__ void iso_index(const MediumParams &m, const R *__rest
         // ulp of n^2 for the amplitudes in use, far inside the FP32 gate.
         const float2 X0 = make_float2(x[0], x[0]), X1 = make_float2(x[1], x[1]), X2 = make_float2(x[2], x[2]);
         float2 N = make_float2(0.f, 0.f), H0 = N, H1 = N, H2 = N;
-        const float2 *rp = reinterpret_cast<const float2 *>(sb);
+        // a pair's six float2 fields are 48 bytes: three 16-byte loads (sb is
+        // a 16-byte aligned shared array)
+        const float4 *rp = reinterpret_cast<const float4 *>(sb);
         const int np = (nb + 1) / 2;
 #pragma unroll 1
         for (int p = 0; p < np; ++p) {
-            const float2 *b = rp + kBlobStride * p;
-            const float2 sg = b[0];
-            const float2 u0 = fma2(sg, X0, b[1]), u1 = fma2(sg, X1, b[2]), u2 = fma2(sg, X2, b[3]);
+            const float4 r0 = lds128(rp + 3 * p), r1 = lds128(rp + 3 * p + 1), r2 = lds128(rp + 3 * p + 2);
+            const float2 sg = make_float2(r0.x, r0.y);
+            const float2 u0 = fma2(sg, X0, make_float2(r0.z, r0.w)), u1 = fma2(sg, X1, make_float2(r1.x, r1.y)),
+                         u2 = fma2(sg, X2, make_float2(r1.z, r1.w));
             const float2 q = fma2(u2, u2, fma2(u1, u1, mul2(u0, u0)));   // |u|^2
             const float2 G = make_float2(exp2_fast(-q.x), exp2_fast(-q.y));
-            N = fma2(b[4], G, N);
-            const float2 c = mul2(b[5], G);
+            N = fma2(make_float2(r2.x, r2.y), G, N);
+            const float2 c = mul2(make_float2(r2.z, r2.w), G);
             H0 = fma2(c, u0, H0);
             H1 = fma2(c, u1, H1);
             H2 = fma2(c, u2, H2);
