@@ -63,6 +63,18 @@ gf_status gf_bench_exp(const double *in, double *out_lib, double *out_cuda, int6
 gf_status gf_bench_exp_fp(const double *in, double *out, int64_t n, void *stream);
 
 /*
+ * gf_bench_blob_gauss -- evaluate the Gaussian of the FP64 evaluator's blob
+ * terms, G = 2^(-(u0^2 + u1^2 + u2^2)), with |u|^2 summed exactly in integer
+ * fixed point, for n points u (device, [3][n] structure of arrays), in both
+ * forms of the table product: out_int (no FP64 operation) and out_fp (one
+ * FP64 FMA), device, n each; the two must be the same bits.  A negligible
+ * term (|u|^2 >= 58.5 or some |u_i| >= 8) gives +0, a non-finite u a NaN.
+ * Stream-ordered on `stream`.
+ * Errors: GF_ERR_INVALID_ARG (n < 0, non-device pointers), GF_ERR_CUDA.
+ */
+gf_status gf_bench_blob_gauss(const double *u, double *out_int, double *out_fp, int64_t n, void *stream);
+
+/*
  * gf_bench_exp_df -- evaluate the double-float base-2 exponential 2^a of the
  * GF_F64X blob evaluator (defined for -63 < a <= 0) on n device doubles
  * (each first split into a float pair), writing hi + lo as doubles to `out`

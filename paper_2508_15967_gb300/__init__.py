@@ -89,6 +89,7 @@ def lib() -> C.CDLL:
             "gf_bench_exp": ([P, P, P, I64, P], I32),
             "gf_bench_exp_df": ([P, P, I64, P], I32),
             "gf_bench_exp_fp": ([P, P, I64, P], I32),
+            "gf_bench_blob_gauss": ([P, P, P, I64, P], I32),
             "gf_bench_recip": ([P, P, P, I64, P], I32),
             "gf_fault_inject": ([I64], I32),
             "gf_bench_live_allocations": ([P], I64),
@@ -479,6 +480,16 @@ def gf_bench_exp_fp(a: torch.Tensor) -> torch.Tensor:
     o = torch.empty_like(a)
     _check("gf_bench_exp_fp", lib().gf_bench_exp_fp(_ptr(a), _ptr(o), a.numel(), _stream(None)))
     return o
+
+
+def gf_bench_blob_gauss(u: torch.Tensor):
+    """(integer-form, FMA-form) blob Gaussians 2^-|u|^2 of a float64 device tensor of shape (3, n)."""
+    u = u.contiguous()
+    n = u.shape[1]
+    o1 = torch.empty(n, dtype=torch.float64, device=u.device)
+    o2 = torch.empty_like(o1)
+    _check("gf_bench_blob_gauss", lib().gf_bench_blob_gauss(_ptr(u), _ptr(o1), _ptr(o2), n, _stream(None)))
+    return o1, o2
 
 
 def gf_bench_exp_df(a: torch.Tensor) -> torch.Tensor:

@@ -146,23 +146,23 @@ __global__ void __launch_bounds__(kAdjBlock, 8) adjoint_kernel(
                 double K[6], acc[6], Y[6], D;
                 double *Ss = S.stage + ((int64_t)(s * 4) * kStageVals) * n + i;
 #pragma unroll
+                for (int c = 0; c < 6; ++c) Y[c] = y[c];
+                // a rolled stage loop: one copy of the evaluator in the code
+#pragma unroll 1
                 for (int st = 0; st < 4; ++st) {
-                    const double *P = st == 0 ? y : Y;
 #pragma unroll
-                    for (int c = 0; c < 6; ++c) Ss[c * n] = P[c];
+                    for (int c = 0; c < 6; ++c) Ss[c * n] = Y[c];
                     double ng[4];
-                    rhs_iso<double, KIND, false>(m, sbs, nb, om, P, K, D, cx, 1, ng);
+                    rhs_iso<double, KIND, false>(m, sbs, nb, om, Y, K, D, cx, 1, ng);
 #pragma unroll
                     for (int c = 0; c < 4; ++c) Ss[(6 + c) * n] = ng[c];
                     Ss += (int64_t)kStageVals * n;
-                    if (st == 0) {
-#pragma unroll
-                        for (int c = 0; c < 6; ++c) { acc[c] = K[c]; Y[c] = rk_axpy(h2, K[c], y[c]); }
-                    } else if (st < 3) {
+                    if (st < 3) {
+                        const double hj = st == 2 ? dt : h2;
 #pragma unroll
                         for (int c = 0; c < 6; ++c) {
-                            acc[c] = rk_acc2(acc[c], K[c]);
-                            Y[c] = rk_axpy(st == 1 ? h2 : dt, K[c], y[c]);
+                            acc[c] = st == 0 ? K[c] : rk_acc2(acc[c], K[c]);
+                            Y[c] = rk_axpy(hj, K[c], y[c]);
                         }
                     } else {
 #pragma unroll

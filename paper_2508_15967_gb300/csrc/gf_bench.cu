@@ -82,6 +82,18 @@ __global__ void exp_fp_check_kernel(const double *in, double *out, int64_t n)
     out[i] = exp2_tab_fp(in[i], sT);
 }
 
+__global__ void blob_gauss_check_kernel(const double *u, double *out_int, double *out_fp, int64_t n)
+{
+    __shared__ double sT[kExpTabN];
+    stage_exp_table(sT);
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double u0 = u[i], u1 = u[n + i], u2 = u[2 * n + i];
+    out_int[i] = blob_gauss(u0, u1, u2, sT, false);
+    out_fp[i] = blob_gauss(u0, u1, u2, sT, true);
+}
+
 __global__ void recip_check_kernel(const double *in, double *out_recip, float *out_narrow, int64_t n)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -164,4 +176,20 @@ extern "C" gf_status gf_bench_fma_peak(gf_precision prec, int64_t iters, int32_t
     if (prec == GF_F32) return gf::run_peak<float>(iters, blocks_per_sm, out_tflops, out_ms);
     gf::set_error("gf_bench_fma_peak: unknown precision");
     return GF_ERR_INVALID_ARG;
+}
+
+extern "C" gf_status gf_bench_blob_gauss(const double *u, double *out_int, double *out_fp, int64_t n, void *stream)
+{
+    if (n < 0) {
+        gf::set_error("gf_bench_blob_gauss: n < 0");
+        return GF_ERR_INVALID_ARG;
+    }
+    if (n == 0) return GF_OK;
+    gf_status s;
+    if ((s = gf::check_device_ptr(u, "u")) != GF_OK || (s = gf::check_device_ptr(out_int, "out_int")) != GF_OK ||
+        (s = gf::check_device_ptr(out_fp, "out_fp")) != GF_OK)
+        return s;
+    gf::blob_gauss_check_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(u, out_int, out_fp,
+                                                                                              n);
+    return gf::cuda_status(cudaGetLastError(), "gf_bench_blob_gauss launch");
 }

@@ -244,9 +244,8 @@ __device__ __forceinline__ void coop_blob_sums(const Lane &L, bool part, const d
         if (p < total) {
             const double sg = b[0];
             const double u0 = fma(sg, x0, b[1]), u1 = fma(sg, x1, b[2]), u2 = fma(sg, x2, b[3]);
-            const double a = fma(-u2, u2, fma(-u1, u1, -(u0 * u0)));
             double *r = cw.res + 4 * p;
-            r[0] = below_cull(a) ? 0.0 : exp2_tab_int(a, T);
+            r[0] = blob_gauss(u0, u1, u2, T, false);
             r[1] = u0;
             r[2] = u1;
             r[3] = u2;

@@ -225,6 +225,24 @@ struct Exp2Red {
     float ph, pl;
 };
 
+// e^t - 1 = ph + pl for t = r ln2, r = rh + rl given as a float pair
+// (|r| <= 2^-12 + 2^-23 |a|, |rl| below 2^-34 or one ulp of rh).
+__device__ __forceinline__ Exp2Red exp2_poly(int k, float rh, float rl)
+{
+    // t = r ln2 = th + tl
+    const float th = __fmul_rn(rh, kLn2FHi);
+    const float tl = fmaf(rl, kLn2FHi, fmaf(rh, kLn2FLo, fmaf(rh, kLn2FHi, -th)));
+    // e^t - 1 = ph + pl
+    const float p2 = __fmul_rn(th, th);
+    const float e2 = fmaf(th, th, -p2);                           // th^2 = p2 + e2 exactly
+    const float h = __fmul_rn(0.5f, p2);
+    const float ph = __fadd_rn(th, h);
+    const float l0 = __fsub_rn(h, __fsub_rn(ph, th));             // fast two-sum, |th| >= |h|
+    const float c34 = __fmul_rn(p2, fmaf(th, kInv6F, __fmul_rn(p2, kInv24F)));   // t^3/6 + t^4/24
+    const float pl = __fadd_rn(l0, __fadd_rn(tl, fmaf(0.5f, e2, fmaf(th, tl, c34))));
+    return Exp2Red{k, ph, pl};
+}
+
 __device__ __forceinline__ Exp2Red exp2_reduce(double a)
 {
     const float a0 = narrow_trunc(a);
@@ -238,18 +256,7 @@ __device__ __forceinline__ Exp2Red exp2_reduce(double a)
     const float rh = __fadd_rn(s, a1);
     const float bb = __fsub_rn(rh, s);
     const float rl = __fadd_rn(__fadd_rn(__fsub_rn(s, __fsub_rn(rh, bb)), __fsub_rn(a1, bb)), a2);
-    // t = r ln2 = th + tl
-    const float th = __fmul_rn(rh, kLn2FHi);
-    const float tl = fmaf(rl, kLn2FHi, fmaf(rh, kLn2FLo, fmaf(rh, kLn2FHi, -th)));
-    // e^t - 1 = ph + pl
-    const float p2 = __fmul_rn(th, th);
-    const float e2 = fmaf(th, th, -p2);                           // th^2 = p2 + e2 exactly
-    const float h = __fmul_rn(0.5f, p2);
-    const float ph = __fadd_rn(th, h);
-    const float l0 = __fsub_rn(h, __fsub_rn(ph, th));             // fast two-sum, |th| >= |h|
-    const float c34 = __fmul_rn(p2, fmaf(th, kInv6F, __fmul_rn(p2, kInv24F)));   // t^3/6 + t^4/24
-    const float pl = __fadd_rn(l0, __fadd_rn(tl, fmaf(0.5f, e2, fmaf(th, tl, c34))));
-    return Exp2Red{k, ph, pl};
+    return exp2_poly(k, rh, rl);
 }
 
 // 2^a for a <= 0 (finite or -inf; a <= -1021 returns 0, below four times the
@@ -278,17 +285,23 @@ __device__ __forceinline__ Exp2Red exp2_reduce(double a)
 // 2^(k >> 11) on the exponent field.  Error against 2^a: table and final
 // rounding 0.5 ulp each plus ~0.03 ulp, under 1.05 ulp over the whole range;
 // the blob terms use -58.5 <= a <= 0.
-__device__ __forceinline__ double exp2_tab_fp(double a, const double *__restrict__ T)
+// 2^(k/2048) (1 + ph + pl) for a reduction e with k >> 11 >= -1021: one FP64
+// addition (exact) and one FMA.
+__device__ __forceinline__ double exp2_scale_fp(const Exp2Red &e, const double *__restrict__ T)
 {
-    const Exp2Red e = exp2_reduce(a);
     const double P = __dadd_rn(widen(trunc63(e.ph)), widen(trunc63(e.pl)));   // exact
     const double Tj = T[e.k & (kExpTabN - 1)];
     const double v = fma(Tj, P, Tj);                                         // RN(T (1 + P))
-    const int hi = __double2hiint(v) + ((e.k >> 11) << 20);
+    return __hiloint2double(__double2hiint(v) + ((e.k >> 11) << 20), __double2loint(v));
+}
+
+__device__ __forceinline__ double exp2_tab_fp(double a, const double *__restrict__ T)
+{
+    const double v = exp2_scale_fp(exp2_reduce(a), T);
     const unsigned ahi = (unsigned)__double2hiint(a);
     // a <= -1021 (sign set, |a| >= 1021: hi word >= that of -1021.0), -inf and
     // NaN with the sign bit set flush to 0
-    return ahi >= 0xC08FE800u ? 0.0 : __hiloint2double(hi, __double2loint(v));
+    return ahi >= 0xC08FE800u ? 0.0 : v;
 }
 
 // The same value in 64-bit integer arithmetic: with T = S 2^-52 (S its 53-bit
@@ -296,9 +309,8 @@ __device__ __forceinline__ double exp2_tab_fp(double a, const double *__restrict
 // exactly; the 117-bit product S U (high and low 64-bit words) is normalised
 // by its leading zeros and rounded to 53 bits, to nearest with ties to even
 // (round bit and sticky bits), as the FMA of exp2_tab_fp rounds it.
-__device__ __forceinline__ double exp2_tab_int(double a, const double *__restrict__ T)
+__device__ __forceinline__ double exp2_scale_int(const Exp2Red &e, const double *__restrict__ T)
 {
-    const Exp2Red e = exp2_reduce(a);
     const long long P = fix63(e.ph) + fix63(e.pl);                   // exact, |P| < 2^52
     const unsigned long long tb = (unsigned long long)__double_as_longlong(T[e.k & (kExpTabN - 1)]);
     const unsigned long long S = (tb & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
@@ -309,8 +321,68 @@ __device__ __forceinline__ double exp2_tab_int(double a, const double *__restric
     const unsigned long long r = lo << lz;                            // round bit, then sticky bits
     const unsigned long long up = (r >> 63) & ((r << 1) != 0ull ? 1ull : (m & 1ull));
     const long long bits = ((long long)(1023 - lz + (e.k >> 11)) << 52) + (long long)(m + up);
+    return __longlong_as_double(bits);
+}
+
+__device__ __forceinline__ double exp2_tab_int(double a, const double *__restrict__ T)
+{
+    const double v = exp2_scale_int(exp2_reduce(a), T);
     const unsigned ahi = (unsigned)__double2hiint(a);
-    return ahi >= 0xC08FE800u ? 0.0 : __longlong_as_double(bits);
+    return ahi >= 0xC08FE800u ? 0.0 : v;
+}
+
+// u^2 for |u| < 8 in 64-bit fixed point, in units of 2^-56, within one unit,
+// and the largest biased exponent seen in emax.  U = |u| 2^60 is formed from
+// u's significand M by a shift, M 2^(e - 1015) (exact for |u| >= 2^-8; below
+// that truncated by less than 2^-60, which moves u^2 by less than 2^-67), and
+// split as U = H 2^32 + L (H < 2^31); then U^2 2^-64 = H^2 + (H L + L^2
+// 2^-33) 2^-31 + (under 2^-32), the middle term rounded to nearest: two
+// 32 x 32 -> 64-bit products and one high half.  Larger e only raise emax
+// (the caller culls them); the sum of three such squares stays below 2^64.
+__device__ __forceinline__ unsigned long long sq_fix56(double u, unsigned &emax)
+{
+    const unsigned hi = (unsigned)__double2hiint(u), lo = (unsigned)__double2loint(u);
+    const unsigned e = (hi >> 20) & 0x7FFu;
+    const unsigned long long M = ((unsigned long long)((hi & 0xFFFFFu) | 0x100000u) << 32) | lo;
+    const int sh = (int)e - 1015;
+    const unsigned long long U = sh >= 0 ? M << min(sh, 10) : M >> min(-sh, 63);   // zero, subnormal: 0
+    const unsigned H = (unsigned)(U >> 32), L = (unsigned)U;
+    const unsigned long long HL = (unsigned long long)H * L + (__umulhi(L, L) >> 1) + (1ull << 30);
+    emax = max(emax, e);
+    return (unsigned long long)H * H + (HL >> 31);
+}
+
+// |u|^2 = 58.5 (the cull threshold kBlobCull2) in units of 2^-56.
+constexpr unsigned long long kBlobCullQ56 = 0x3A80000000000000ull;
+
+// The Gaussian of a blob term, G = 2^(-|u|^2) for FP64 u = (u0, u1, u2),
+// with the exponent formed without FP64 operations: |u|^2 is summed in
+// 64-bit fixed point (sq_fix56, within 2^-55.4 of the exact sum of the
+// squares of the given u, where the FP64 form rounds |u|^2 to 53 bits, up
+// to 2^-47 for |u|^2 near 58); k = round(2048 |u|^2) and r = k/2048 - |u|^2
+// (|r| <= 2^-12) come from its bits, r as a float pair (its bits down to
+// 2^-34 and the rest, both exact), and 2^r, the table entry and the scaling
+// follow exp2_poly and exp2_scale_int (or exp2_scale_fp: the same bits).
+// Error against the exact 2^(-|u|^2) of the given u below 1.05 ulp (CPU
+// emulation of these steps against exact rationals, and the GPU test).
+// Returns +0 for a negligible term (|u|^2 >= 58.5, or some |u_i| >= 8) and a
+// NaN if some u_i is infinite or NaN.
+__device__ __forceinline__ double blob_gauss(double u0, double u1, double u2, const double *__restrict__ T,
+                                             bool exp_fp)
+{
+    unsigned emax = 0u;
+    const unsigned long long q = sq_fix56(u0, emax) + sq_fix56(u1, emax) + sq_fix56(u2, emax);
+    if (emax >= 1026u) return emax == 2047u ? __longlong_as_double(0x7FF8000000000000ll) : 0.0;
+    if (q >= kBlobCullQ56) return 0.0;
+    const long long K = (long long)((q + (1ull << 44)) >> 45);      // round(2048 |u|^2)
+    const long long ra = (K << 45) - (long long)q;                  // r in units of 2^-56, |ra| <= 2^44
+    const int vh = (int)(ra >> 22);                                 // |vh| <= 2^22
+    const unsigned vl = (unsigned)ra & 0x3FFFFFu;
+    // small integers as floats by the bias trick (exact), then scaled
+    const float rh = __fmul_rn(__fsub_rn(__int_as_float(0x4B400000 + vh), 12582912.0f), 0x1p-34f);
+    const float rl = __fmul_rn(__fsub_rn(__uint_as_float(0x4B000000u | vl), 8388608.0f), 0x1p-56f);
+    const Exp2Red e = exp2_poly(-(int)K, rh, rl);
+    return exp_fp ? exp2_scale_fp(e, T) : exp2_scale_int(e, T);
 }
 
 // 2^a in FP32 with the hardware base-2 exponential (ex2.approx.ftz.f32:
@@ -361,15 +433,6 @@ template <>
 __device__ __forceinline__ float recip<float>(float v)
 {
     return __frcp_rn(v);
-}
-
-// a < -58.5 (kBlobCull2) for a double, decided on the bit pattern with
-// integer compares (for negative a, larger magnitude means a larger unsigned
-// pattern; NaN with the sign bit set also counts as negligible).  Same
-// decision as the FP64 comparison, without an FP64 instruction.
-__device__ __forceinline__ bool below_cull(double a)
-{
-    return (unsigned long long)__double_as_longlong(a) > 0xC04D400000000000ull;   // bits of -58.5
 }
 
 template <typename R>
@@ -508,9 +571,8 @@ __device__ __forceinline__ double blob_term_scaled(const double *__restrict__ b,
     const double sg = b[0];
     const double u0 = fma(sg, x[0], b[stride]), u1 = fma(sg, x[1], b[2 * stride]),
                  u2 = fma(sg, x[2], b[3 * stride]);
-    const double a = fma(-u2, u2, fma(-u1, u1, -(u0 * u0)));
-    if (below_cull(a)) return 0.0;
-    const double G = exp_fp ? exp2_tab_fp(a, T) : exp2_tab_int(a, T);
+    const double G = blob_gauss(u0, u1, u2, T, exp_fp);
+    if (__double_as_longlong(G) == 0ll) return 0.0;
     n2 = fma(b[4 * stride], G, n2);
     const double c = b[5 * stride] * G;
     g[0] = fma(c, u0, g[0]);
@@ -581,10 +643,13 @@ __device__ __forceinline__ void iso_index(const MediumParams &m, const R *__rest
     }
     if constexpr (sizeof(R) == 8) {
         // scaled rows: u = sigma x - sigma c, G = 2^(-|u|^2),
-        // n^2 += A G, grad n^2 += (-2 ln2 sigma A) G u   (16 FP64 operations per live term)
+        // n^2 += A G, grad n^2 += (-2 ln2 sigma A) G u   (8 FP64 operations per live term:
+        // u 3, n^2 1, the weight 1, grad n^2 3; G on the integer and FP32 pipes)
         PreX px = {0.f, 0.f, 0.f, false};
         if (cx.pre != nullptr) px = pretest_point(m, x);
-#pragma unroll 2
+        // one term per iteration: the trace kernels inline this loop once per
+        // stage, and a longer body makes the instruction cache miss
+#pragma unroll 1
         for (int j = 0; j < nb; ++j) {
             if (px.on && pretest_negligible(cx.pre + 4 * j * cx.pre_stride, cx.pre_stride, px)) continue;
             blob_term_scaled(sb + kBlobStride * j * stride, stride, x, n2, g, cx.T, cx.live, cx.exp_fp);

@@ -102,3 +102,63 @@ def test_reciprocal_and_truncation_helpers():
     assert (np.abs(f[body]) <= np.abs(x[body])).all() and (np.sign(f[body]) == np.sign(x[body])).all()
     assert (np.abs(f[body] - x[body]) / np.abs(x[body])).max() < 2.0 ** -23
     assert np.isinf(f[-2]) and np.isinf(f[-1]) and f[-1] < 0 and f[-6] == 0.0
+
+
+def _gauss_exact(u) -> Decimal:
+    """2^-(u0^2 + u1^2 + u2^2) of the given doubles, the exponent exact."""
+    getcontext().prec = 50
+    q = sum(Fraction(float(c)) ** 2 for c in u)
+    return (-(Decimal(q.numerator) / Decimal(q.denominator)) * Decimal(2).ln()).exp()
+
+
+def _blob_points(rng, n):
+    d = rng.normal(0, 1, (n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    pts = [rng.uniform(-7.6, 7.6, (n, 3)),                                 # culled and live
+           d * np.sqrt(rng.uniform(0, 58.5, (n, 1))),                      # live, any exponent
+           d * np.sqrt(rng.integers(0, 58 * 2048, (n, 1)) / 2048.0),       # exponent on the k/2048 grid
+           rng.normal(0, 1, (n, 3)) * 10.0 ** rng.uniform(-12, 0.5, (n, 3)),   # mixed magnitudes
+           rng.uniform(-1e-3, 1e-3, (n, 3))]                               # near the centre
+    return np.concatenate(pts)
+
+
+def test_blob_gaussian_against_the_exact_gaussian():
+    """The FP64 evaluator's blob Gaussian sums |u|^2 exactly in integer fixed
+    point: within 1.05 ulp of 2^-|u|^2 for the given u (no rounding of the
+    exponent), +0 exactly for the negligible terms (|u|^2 >= 58.5), and the
+    same bits in its integer and FMA forms."""
+    rng = np.random.default_rng(21)
+    u = _blob_points(rng, 1200)
+    u = np.concatenate([u, [[0.0, 0.0, 0.0], [-0.0, 5e-324, 0.0], [2.0 ** -30, 2.0 ** -40, 0.0],
+                            [7.6, 0.0, 0.0], [1.0, 1.0, 1.0], [np.sqrt(58.5) * (1 - 1e-15), 0.0, 0.0]]])
+    gi, gfp = (t.cpu().numpy() for t in gf.gf_bench_blob_gauss(torch.tensor(u.T.copy(), device="cuda")))
+    assert (gi.view(np.int64) == gfp.view(np.int64)).all()
+    q = np.array([float(sum(Fraction(float(c)) ** 2 for c in p)) for p in u])
+    live = q < 58.5 - 1e-9
+    dead = q >= 58.5 + 1e-9
+    assert (gi[dead] == 0).all() and not np.signbit(gi[dead]).any()
+    err = np.array([float(abs(Decimal(float(g)) - ex) / Decimal(math.ulp(float(ex))))
+                    for g, ex in ((g, _gauss_exact(p)) for g, p in zip(gi[live], u[live]))])
+    assert err.max() < 1.05, (err.max(), u[live][np.argmax(err)])
+    assert err.mean() < 0.4
+    assert gi[len(u) - 6] == 1.0 and gi[len(u) - 5] == 1.0
+
+
+def test_blob_gaussian_forms_agree_and_special_values():
+    rng = np.random.default_rng(22)
+    u = _blob_points(rng, 200_000)
+    t = torch.tensor(u.T.copy(), device="cuda")
+    gi, gfp = gf.gf_bench_blob_gauss(t)
+    assert torch.equal(gi.view(torch.int64), gfp.view(torch.int64))
+    # against CUDA's exp2 of the FP64-rounded exponent: the only gap is that rounding
+    q = (t * t).sum(0)
+    ref = torch.exp2(-q)
+    live = q < 58.0
+    rel = ((gi - ref).abs() / ref)[live]
+    assert float(rel.max()) < 64 * 2.0 ** -52
+    # |u_i| >= 8 is negligible whatever the others; inf and NaN give NaN
+    s = torch.tensor([[8.0, 0.0, 0.0], [-9.5, 0.0, 0.0], [1e300, 0.0, 0.0], [float("inf"), 0.0, 0.0],
+                      [float("nan"), 0.0, 0.0], [0.0, -float("inf"), 1.0]], device="cuda", dtype=torch.float64)
+    gs, _ = gf.gf_bench_blob_gauss(s.T.contiguous())
+    gs = gs.cpu().numpy()
+    assert (gs[:3] == 0).all() and np.isnan(gs[3:]).all()
