@@ -474,27 +474,11 @@ __device__ __forceinline__ float4 lds128(const float4 *p)
 }
 
 // Packed FP32x2 arithmetic (two lanes of float per instruction on sm_100 and
-// later): d = a b + c, a b, and a + b, each half correctly rounded.
-__device__ __forceinline__ unsigned long long pk2(float2 v)
-{
-    return ((unsigned long long)__float_as_uint(v.y) << 32) | __float_as_uint(v.x);
-}
-__device__ __forceinline__ float2 upk2(unsigned long long v)
-{
-    return make_float2(__uint_as_float((unsigned)v), __uint_as_float((unsigned)(v >> 32)));
-}
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
-{
-    unsigned long long d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)), "l"(pk2(c)));
-    return upk2(d);
-}
-__device__ __forceinline__ float2 mul2(float2 a, float2 b)
-{
-    unsigned long long d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
-    return upk2(d);
-}
+// later, the compiler's builtins): d = a b + c and a b, each half correctly
+// rounded; neg2 negates both halves.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 
 // Blob terms whose exponent is below this are skipped.  The FP64, FP32 and
 // double-float evaluators' rows carry the exponent in base 2 (sigma =
@@ -670,14 +654,14 @@ __device__ __forceinline__ void iso_index(const MediumParams &m, const R *__rest
         // a 16-byte aligned shared array)
         const float4 *rp = reinterpret_cast<const float4 *>(sb);
         const int np = (nb + 1) / 2;
-#pragma unroll 1
+#pragma unroll 2
         for (int p = 0; p < np; ++p) {
             const float4 r0 = lds128(rp + 3 * p), r1 = lds128(rp + 3 * p + 1), r2 = lds128(rp + 3 * p + 2);
             const float2 sg = make_float2(r0.x, r0.y);
             const float2 u0 = fma2(sg, X0, make_float2(r0.z, r0.w)), u1 = fma2(sg, X1, make_float2(r1.x, r1.y)),
                          u2 = fma2(sg, X2, make_float2(r1.z, r1.w));
-            const float2 q = fma2(u2, u2, fma2(u1, u1, mul2(u0, u0)));   // |u|^2
-            const float2 G = make_float2(exp2_fast(-q.x), exp2_fast(-q.y));
+            const float2 nq = fma2(neg2(u2), u2, fma2(neg2(u1), u1, mul2(neg2(u0), u0)));   // -|u|^2
+            const float2 G = make_float2(exp2_fast(nq.x), exp2_fast(nq.y));
             N = fma2(make_float2(r2.x, r2.y), G, N);
             const float2 c = mul2(make_float2(r2.z, r2.w), G);
             H0 = fma2(c, u0, H0);
